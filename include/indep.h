@@ -1,0 +1,239 @@
+/*
+ * indep.h -- C ABI of the B300 (sm_103a) implementation of the Independent
+ * algorithm for neutral biodiversity models (Langenstein 2021,
+ * "Communication-free and Parallel Simulation of Neutral Biodiversity
+ * Models").
+ *
+ * Every sampled individual's lineage is traced backwards in time on its own
+ * (section "The Independent Algorithm"), driven by a counter-based RNG primed
+ * on (seed, indexed location, time) (sections "Environmental RNG Priming" and
+ * "Aligning the RNGs of Colliding Individuals"), with exponential inter-event
+ * times drawn as memoryless sums inside re-prime intervals (section
+ * "Memoryless sums of exponentials").  Lineages that meet draw identical
+ * randomness afterwards; a device hash table culls the copies at common time
+ * horizons (a device-side form of section "Deduplicating Redundant
+ * Individuals" and of the water-level rounds of the appendix "The Independent
+ * Water-Level Algorithm").  The species of an individual is the speciation
+ * event its lineage ends in (section "A Neutral Coalescence-based
+ * Simulation"); identities are dense ranks of the speciation keys
+ * (location, IEEE-754 bits of the time) in ascending order.
+ *
+ * Conventions
+ *  - Every entry point returns an ind_status; nothing throws or aborts.
+ *  - The library owns all device state of a simulation; it allocates it on
+ *    the simulation's stream through the process-wide allocator hook
+ *    (ind_set_allocator), by default cudaMallocAsync.  The caller owns every
+ *    buffer it passes in; input buffers are copied before the call returns.
+ *  - All device work is issued on the stream given to sim_create (NULL = the
+ *    legacy default stream).  Calls that return results to the host
+ *    synchronise that stream.
+ *  - Pointers documented as "host or device" may be either (unified virtual
+ *    addressing); results are written with cudaMemcpyDefault.
+ *  - Results are bit-identical for a given (landscape, dispersal, nu, seed,
+ *    sample): they do not depend on tuning, batching, dedup cadence or the
+ *    order in which the GPU executes lineages.
+ */
+#ifndef INDEP_H
+#define INDEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ind_sim ind_sim;
+
+typedef enum {
+    IND_OK = 0,
+    IND_ERR_ARG = -1,    /* invalid argument; nothing was changed */
+    IND_ERR_OOM = -2,    /* the allocator failed; the object is unchanged */
+    IND_ERR_CUDA = -3,   /* a CUDA runtime call failed (see ind_last_cuda_error) */
+    IND_ERR_BUDGET = -4, /* sim_run used its round budget; call it again to resume */
+    IND_ERR_STATE = -5,  /* call out of order (e.g. species before the run ended) */
+    IND_ERR_DEVICE = -6  /* a device-side limit was hit (see DESIGN: re-prime
+                            interval draw limit); results are not valid */
+} ind_status;
+
+/* landscape kinds */
+enum { IND_NONSPATIAL = 0, IND_TORUS = 1, IND_MAP = 2 };
+/* dispersal kinds */
+enum { IND_DISPERSAL_UNIFORM = 0, IND_DISPERSAL_GAUSSIAN = 1, IND_DISPERSAL_ALIAS_GAUSSIAN = 2 };
+
+/* Landscape (section "Three Neutral scenarios").
+ *  IND_NONSPATIAL: one deme of J = deme individuals (width = height = 1),
+ *    dispersal uniform over all J indexed locations, the parent's own
+ *    included; requires IND_DISPERSAL_UNIFORM.
+ *  IND_TORUS: width x height cells of deme individuals each, wrapped;
+ *    requires IND_DISPERSAL_GAUSSIAN.
+ *  IND_MAP: width x height cells, deme_map[y * width + x] individuals in each
+ *    (0 = not habitable), wrapped; requires IND_DISPERSAL_ALIAS_GAUSSIAN.
+ * Limits: width, height <= 2^20; deme <= 2^23 - 1 (non-spatial J likewise);
+ * width * height * deme < 2^32 (map: width * height * 255); lambda > 0 and
+ * finite; delta_t a power of two in [2^-20, 2^20]; lambda * delta_t >= 2^-20.
+ * A search that crosses 2^26 empty re-prime intervals, or draws 2^20 times in
+ * one interval, stops the run with IND_ERR_DEVICE. */
+typedef struct {
+    int32_t kind;
+    uint32_t width, height;
+    uint32_t deme;
+    const uint8_t* deme_map; /* IND_MAP only: host or device pointer, copied */
+    double lambda;           /* turnover rate: events per unit time per lineage */
+    double delta_t;          /* re-prime interval length */
+} ind_landscape;
+
+/* Dispersal (DispersalSampler of section "The Statically Checked Component
+ * System"; the intra-deme index is uniform, CoalescenceSampler).
+ *  IND_DISPERSAL_GAUSSIAN: each axis moves by round(sigma z), z ~ N(0, 1),
+ *    sampled by inversion of the discretised normal CDF quantised to 2^-64;
+ *    0 < sigma <= 64.
+ *  IND_DISPERSAL_ALIAS_GAUSSIAN: per habitable cell, an alias table over the
+ *    disk dx^2 + dy^2 <= radius^2 with weights
+ *    round(2^32 exp(-(dx^2 + dy^2)/(2 sigma^2))) * deme(target); 1 <= radius
+ *    <= 40. */
+typedef struct {
+    int32_t kind;
+    double sigma;
+    uint32_t radius;
+} ind_dispersal;
+
+typedef struct {
+    uint64_t rounds;        /* horizon rounds executed so far */
+    uint64_t raw_events;    /* events executed on the GPU, duplicates included */
+    uint64_t unique_events; /* distinct (location, time) events; exact only when
+                               counting was enabled (ind_tuning.count_unique) */
+    uint64_t culled;        /* lineages removed by the horizon dedup */
+    uint64_t n_sampled;     /* lineages started */
+    uint64_t n_species;     /* species count (after sim_species) */
+    uint64_t n_roots;       /* lineages that ended in a speciation event */
+    double ms_total;        /* wall time of the sim_run calls (host clock) */
+    double advance_ms;      /* summed advance-kernel time (profile = 1 only) */
+    uint64_t advance_launches; /* advance-kernel launches timed (profile = 1 only) */
+} ind_run_stats;
+
+/* Tuning of the engine.  None of it changes results (bit-identical). */
+typedef struct {
+    uint32_t block_threads;     /* advance-kernel threads per block: 64..512, multiple of 32 */
+    uint32_t blocks_per_sm;     /* persistent grid = blocks_per_sm x SM count, 1..32 */
+    uint32_t lineages_per_lane; /* lineages a warp claims per lane at a time, 1..64 */
+    uint32_t rounds_per_check;  /* horizon rounds between host completion checks, 1..4096 */
+    uint32_t use_graph;         /* 1: replay each chunk of rounds as a captured CUDA graph */
+    uint32_t dedup;             /* 1: horizon dedup (default); 0: none */
+    uint32_t count_unique;      /* 1: count distinct events exactly (slower, for measurement) */
+    uint32_t profile;           /* 1: time every advance-kernel launch with CUDA events */
+    /* horizon step of a simulation with n active lineages over S indexed
+     * locations: lambda * step = max(floor, min(occupancy_step * S / n,
+     * events_per_round / n)), floor = tail_events while n < busy_lineages
+     * (the GPU is latency-bound and duplicates cost no time), else
+     * min_events_per_lineage */
+    double events_per_round;       /* water level: target events per simulation per round */
+    double min_events_per_lineage; /* lower bound of lambda x horizon step */
+    double occupancy_step;         /* alpha: duplicate work per round stays near alpha / 2 */
+    double tail_events;            /* lower bound of lambda x horizon step below busy_lineages */
+    double busy_lineages;          /* active lineages that fill the GPU */
+} ind_tuning;
+
+typedef struct {
+    /* returns a device allocation of at least bytes, ordered on stream, or NULL */
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*release)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} ind_allocator;
+
+/* Process-wide device allocator hook, used for all later allocations
+ * (NULL restores cudaMallocAsync / cudaFreeAsync).  Not thread-safe with
+ * concurrent library calls. */
+ind_status ind_set_allocator(const ind_allocator* allocator);
+
+/* Defaults of the tuning. */
+void ind_default_tuning(ind_tuning* out);
+
+/* Create a simulation: validates the arguments, copies the deme map,
+ * derives the stream key from seed, and builds the dispersal tables on the
+ * device (for IND_MAP: one alias row per habitable cell, 8 bytes per disk
+ * offset).  nu is the speciation probability per event, 0 < nu <= 1.
+ * cuda_stream is a cudaStream_t (NULL: legacy default stream). */
+ind_status sim_create(const ind_landscape* landscape, const ind_dispersal* dispersal, double nu,
+                      uint64_t seed, void* cuda_stream, ind_sim** out);
+
+/* Choose the sampled individuals and reset all lineages to the present:
+ * individual (cell, i) is sampled iff fraction >= 1 or the top 53 bits of its
+ * sample draw (stream key of sample_seed, tag SAMPLE) are below
+ * ceil(fraction 2^53).  Individuals are numbered in (cell row-major, i)
+ * order.  0 < fraction <= 1.  *n_sampled receives the count (may be NULL). */
+ind_status sim_sample(ind_sim* sim, double fraction, uint64_t sample_seed, uint64_t* n_sampled);
+
+/* Run horizon rounds until every lineage has speciated or round_budget
+ * rounds were executed in this call (0 = unlimited); IND_ERR_BUDGET means
+ * "not finished yet" and the next call resumes.  out may be NULL. */
+ind_status sim_run(ind_sim* sim, uint64_t round_budget, ind_run_stats* out);
+
+/* After a finished run: species identity per sampled individual (dense rank
+ * of its speciation key, 0 .. n_species-1) into species_id_out[n_sampled]
+ * (host or device; may be NULL), and the count into *n_species_out (may be
+ * NULL). */
+ind_status sim_species(ind_sim* sim, uint64_t* species_id_out, uint64_t* n_species_out);
+
+/* After a finished run: the speciation key of every sampled individual:
+ * location loc = x | y << 20 | i << 40 and the IEEE-754 bits of the
+ * speciation time, into arrays of n_sampled entries (host or device). */
+ind_status sim_species_keys(ind_sim* sim, uint64_t* key_loc_out, uint64_t* key_time_out);
+
+/* Tuning of a simulation (copied); NULL restores the defaults. */
+ind_status sim_set_tuning(ind_sim* sim, const ind_tuning* tuning);
+
+/* Cumulative statistics of a simulation. */
+ind_status sim_stats(const ind_sim* sim, ind_run_stats* out);
+
+/* Upper bound of the device bytes a simulation of this shape holds after
+ * sim_create + sim_sample(fraction) + sim_run (admission control);
+ * 0 for invalid arguments. */
+size_t sim_mem_estimate(const ind_landscape* landscape, const ind_dispersal* dispersal,
+                        double fraction);
+
+/* Free a simulation and its device state (stream-ordered). NULL is a no-op. */
+void sim_destroy(ind_sim* sim);
+
+/* Run n sampled simulations together in one persistent advance kernel per
+ * round until all have finished, then resolve their species.  Each sim must
+ * be sampled and not yet run; they may have different landscapes, sizes,
+ * nu and dispersal.  Work is issued on the stream of sims[0]; tuning NULL =
+ * sims[0]'s tuning.  per_sim (n entries, may be NULL) receives each
+ * simulation's statistics.  Afterwards sim_species works on each sim. */
+ind_status sim_batch_run(ind_sim** sims, uint32_t n, const ind_tuning* tuning,
+                         ind_run_stats* per_sim);
+
+/* Synthetic habitat map (seeded site percolation): cell (x, y) is habitable
+ * iff the top 53 bits of the first draw of its map stream (stream key of
+ * map_seed, location x | y << 20, time 0, tag MAP) are below
+ * ceil(p_habitable 2^53); its deme is then 1 + mulhi64(second draw,
+ * max_deme).  deme_out: width * height bytes, row-major, host or device;
+ * 1 <= max_deme <= 255.  Work runs on cuda_stream; returns after it ends. */
+ind_status ind_habitat(uint64_t map_seed, uint32_t width, uint32_t height, double p_habitable,
+                       uint32_t max_deme, uint8_t* deme_out, void* cuda_stream);
+
+/* Conformance probe of the device arithmetic (no counterpart in the paper;
+ * used by the tests): for each 64-bit input v[i], exp_q58_out[i] receives the
+ * fixed-point -ln U of U = ((v[i] >> 11) + 1) 2^-53 in units of 2^-58, and
+ * philox_out[4i..4i+3] the Philox4x32-10 block with key (lo, hi of v[i]) and
+ * counter (lo, hi of v[i+1 mod n], lo, hi of v[i+2 mod n]).  Either output may
+ * be NULL; all pointers host or device; 1 <= n <= 2^30. */
+ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, uint32_t* philox_out,
+                        void* cuda_stream);
+
+/* Human-readable status name; never NULL. */
+const char* ind_status_string(ind_status status);
+
+/* The last CUDA error code seen by the library (cudaError_t as int). */
+int ind_last_cuda_error(void);
+
+/* Number of library kernel launches since the process started (for
+ * accounting). */
+uint64_t ind_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* INDEP_H */

@@ -1,0 +1,1974 @@
+// engine.cu -- kernels and C ABI of the Independent-algorithm engine.
+//
+// One engine serves a single simulation and a batch of uneven simulations
+// alike: the lineages of all simulations of a batch share structure-of-arrays
+// buffers, each simulation keeps its own horizon (water level, appendix "The
+// Independent Water-Level Algorithm"), and one persistent advance kernel per
+// round moves every active lineage of every simulation to its simulation's
+// horizon.  Per round:
+//   advance  -- events (speciation or dispersal) until the next event lies
+//               beyond the horizon; then insert the lineage's indexed
+//               location into the round's dedup table (min lineage id wins);
+//   compact  -- drop finished lineages, cull the losers of the dedup
+//               (parent[loser] = winner), write the survivors to the other
+//               buffer; its last block advances every simulation's horizon.
+// Lineages at the same indexed location at a horizon T are exact duplicates:
+// the next event of both is the first point of that location's event
+// process after T, and everything after depends only on (location, time).
+// Culling either copy is exact, so results do not depend on the dedup, its
+// cadence, the tuning or the GPU's execution order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "indep.h"
+#include "device.cuh"
+
+namespace indep {
+void host_ln_tables(uint64_t L[256], uint32_t R[256], uint64_t* ln2_q64, int64_t c[7]);
+int host_gauss_half(double sigma);
+std::vector<uint64_t> host_gauss_cdf(double sigma);
+std::vector<uint64_t> host_kernel_weights(double sigma, int radius);
+}  // namespace indep
+
+using namespace indep;
+
+// ---------------------------------------------------------------------------
+// process state
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_last_cuda_error{0};
+static std::atomic<uint64_t> g_launches{0};
+static ind_allocator g_alloc = {nullptr, nullptr, nullptr};
+
+#define CK(expr)                                           \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) {                           \
+            g_last_cuda_error.store((int)e_);              \
+            return IND_ERR_CUDA;                           \
+        }                                                  \
+    } while (0)
+
+#define CKL()                                              \
+    do {                                                   \
+        g_launches.fetch_add(1);                           \
+        cudaError_t e_ = cudaGetLastError();               \
+        if (e_ != cudaSuccess) {                           \
+            g_last_cuda_error.store((int)e_);              \
+            return IND_ERR_CUDA;                           \
+        }                                                  \
+    } while (0)
+
+struct Alloc {
+    void* p;
+    size_t bytes;
+};
+
+static void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (g_alloc.alloc) return g_alloc.alloc(bytes, (void*)s, g_alloc.ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dev_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (g_alloc.release) {
+        g_alloc.release(p, bytes, (void*)s, g_alloc.ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+// owner of a set of device allocations on one stream
+struct Pool {
+    cudaStream_t stream = nullptr;
+    std::vector<Alloc> allocs;
+    template <class T>
+    T* get(size_t count) {
+        size_t bytes = count * sizeof(T);
+        void* p = dev_alloc(bytes, stream);
+        if (p) allocs.push_back({p, bytes});
+        return (T*)p;
+    }
+    void release_all() {
+        for (auto& a : allocs) dev_free(a.p, a.bytes, stream);
+        allocs.clear();
+    }
+    size_t total() const {
+        size_t t = 0;
+        for (auto& a : allocs) t += a.bytes;
+        return t;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// device data
+// ---------------------------------------------------------------------------
+__device__ LnTables g_ln;  // read-only tables of the inverse-transform logarithm
+static std::mutex g_ln_mutex;
+static std::vector<int> g_ln_ready;  // per device
+
+static ind_status ensure_ln_tables(cudaStream_t s) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_ln_mutex);
+    if ((int)g_ln_ready.size() <= dev) g_ln_ready.resize(dev + 1, 0);
+    if (g_ln_ready[dev]) return IND_OK;
+    static LnTables host;
+    host_ln_tables(host.L, host.R, &host.ln2_q64, host.c);
+    CK(cudaMemcpyToSymbolAsync(g_ln, &host, sizeof(LnTables), 0, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    g_ln_ready[dev] = 1;
+    return IND_OK;
+}
+
+constexpr uint32_t DONE_BIT = 0x80000000u;
+constexpr uint64_t EMPTY_KEY = ~0ull;
+constexpr uint32_t INTERVAL_BLOCK_LIMIT = 1u << 19;  // 2^20 draws per re-prime interval
+constexpr uint32_t INTERVAL_LIMIT = 1u << 26;        // empty intervals crossed in one search
+
+struct SimParams {
+    int32_t kind;
+    uint32_t W, H, D;          // D: individuals per cell (non-spatial: J)
+    uint32_t slot_deme;        // individuals per cell in the slot numbering (map: max deme)
+    int32_t dt_log2;
+    uint64_t nu_thr;           // ceil(nu 2^53)
+    double lambda;
+    uint32_t sk0, sk1;         // stream key of the seed
+    int32_t gauss_half;
+    uint32_t gauss_n;
+    const uint64_t* gauss;     // 2 half discretised-normal CDF thresholds
+    const uint8_t* deme_map;   // W*H
+    const uint32_t* row_of;    // W*H alias row of a cell
+    const uint64_t* alias;     // rows x n_off entries: q | alias << 32 | full << 63
+    const int8_t* off;         // n_off (dx, dy)
+    uint32_t n_off;
+    uint32_t n_lineages;
+    uint64_t slot_base;        // first global slot index of this simulation
+    uint32_t gid_base;         // first global lineage id of this simulation
+    uint32_t pad;
+    const uint64_t* sample_loc;  // n_lineages sampled locations
+    double events_per_round;
+    double min_events;
+    double occupancy_step;
+    double tail_events;
+    double busy_lineages;
+    double n_slots;            // indexed locations of the landscape
+};
+
+struct SimState {
+    double horizon;
+    uint64_t raw_events;
+    uint64_t unique_events;
+    uint64_t culled;
+    uint64_t rounds;
+    uint32_t n_active;
+    uint32_t n_next;
+    uint32_t culled_round;
+    uint32_t done;
+    uint32_t error;
+    uint32_t pad;
+};
+
+struct Globals {
+    uint32_t n_total;       // lineages in the current input buffer
+    uint32_t n_total_next;  // survivors written by the running compaction
+    uint32_t work_ctr;      // claim counter of the advance kernel
+    uint32_t blocks_done;   // finished blocks of the running compaction
+    uint32_t round;         // rounds completed (parity selects buffers)
+    uint32_t mask[2];       // probe mask of the dedup tables
+    uint32_t used[2];       // occupied-slot counts of the dedup tables
+    uint32_t ev_used[2];    // occupied-slot counts of the event-count tables
+    uint32_t error;
+    uint32_t n_live_sims;
+};
+
+struct __align__(16) EvSlot {
+    unsigned long long a, b;
+};
+
+struct LinPtrs {
+    uint64_t* loc;
+    double* tn;
+    uint32_t* gid;
+    uint32_t* sim;
+};
+
+struct BatchDev {
+    LinPtrs lin[2];
+    uint32_t* parent;
+    uint64_t* key_loc;
+    uint64_t* key_time;
+    unsigned long long* ht_key[2];
+    uint32_t* ht_val[2];
+    uint32_t* ht_used[2];
+    EvSlot* ev[2];
+    uint32_t* ev_used[2];
+    uint32_t ev_mask;
+    uint32_t ht_cap;
+    const SimParams* P;
+    SimState* S;
+    Globals* G;
+    uint32_t n_sims;
+    uint32_t lpl;
+    int dedup;
+    int count_unique;
+};
+
+// ---------------------------------------------------------------------------
+// per-lineage event arithmetic
+// ---------------------------------------------------------------------------
+struct LaneSim {
+    uint32_t sim;
+    int kind;
+    uint32_t W, H, D;
+    uint64_t nu_thr;
+    uint32_t sk0, sk1;
+    double dt, inv_dt;
+    double lam;
+    bool lam1;
+    double horizon;
+};
+
+__device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
+                                             const SimState* S, uint32_t sim) {
+    const SimParams* p = P + sim;
+    c.sim = sim;
+    c.kind = __ldg(&p->kind);
+    c.W = __ldg(&p->W);
+    c.H = __ldg(&p->H);
+    c.D = __ldg(&p->D);
+    c.nu_thr = __ldg(&p->nu_thr);
+    c.sk0 = __ldg(&p->sk0);
+    c.sk1 = __ldg(&p->sk1);
+    int dl = __ldg(&p->dt_log2);
+    c.dt = ldexp(1.0, dl);
+    c.inv_dt = ldexp(1.0, -dl);
+    c.lam = __ldg(&p->lambda);
+    c.lam1 = (c.lam == 1.0);
+    c.horizon = *(volatile const double*)&S[sim].horizon;
+}
+
+struct LnSh {
+    const uint64_t* L;
+    const uint32_t* R;
+    uint64_t ln2;
+    int64_t c[7];
+};
+
+__device__ __forceinline__ double exp_draw(uint64_t v, const LnSh& ln, const LaneSim& c) {
+    uint64_t q = exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c);
+    double x = __dmul_rn(__ull2double_rn(q), 0x1p-58);
+    return c.lam1 ? x : __ddiv_rn(x, c.lam);
+}
+
+// first point of loc's event process strictly after tau; negative on overflow
+__device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnSh& ln) {
+    uint64_t k = __double2ull_rd(__dmul_rn(tau, c.inv_dt));
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
+        double p = __dmul_rn(__ull2double_rn(k), c.dt);
+        const double end = __dmul_rn(__ull2double_rn(k + 1ull), c.dt);
+        bool next_interval = false;
+        for (uint32_t j = 0; j < INTERVAL_BLOCK_LIMIT; ++j) {
+            const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+            p = __dadd_rn(p, exp_draw(b.lo, ln, c));
+            if (p >= end) {
+                next_interval = true;
+                break;
+            }
+            if (p > tau) return p;
+            p = __dadd_rn(p, exp_draw(b.hi, ln, c));
+            if (p >= end) {
+                next_interval = true;
+                break;
+            }
+            if (p > tau) return p;
+        }
+        if (!next_interval) return -1.0;
+        ++k;
+    }
+    return -1.0;
+}
+
+__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, uint32_t n, int32_t half,
+                                              uint64_t r) {
+    return (int32_t)upper_bound_u64(t, n, r) - half;
+}
+
+// one event at (loc, tau); returns true if the lineage speciated, else
+// moves loc to the dispersal target
+__device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
+                                         double tau) {
+    const uint64_t tk = (uint64_t)__double_as_longlong(tau);
+    const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
+    if (c.kind == KIND_NONSPATIAL) {
+        if ((b0.lo >> 11) < c.nu_thr) return true;
+        loc = pack_loc(0, 0, umulhi64(b0.hi, c.D));
+        return false;
+    }
+    const u64x2 b1 = stream_block(c.sk0, c.sk1, loc, tk, 1, TAG_EVENT);
+    if ((b0.lo >> 11) < c.nu_thr) return true;
+    const SimParams* p = P + c.sim;
+    const uint32_t x = loc_x(loc), y = loc_y(loc);
+    if (c.kind == KIND_TORUS) {
+        const uint64_t* g = p->gauss;
+        const uint32_t gn = __ldg(&p->gauss_n);
+        const int32_t gh = __ldg(&p->gauss_half);
+        const uint32_t tx = wrap_add(x, gauss_step(g, gn, gh, b0.hi), c.W);
+        const uint32_t ty = wrap_add(y, gauss_step(g, gn, gh, b1.lo), c.H);
+        const uint64_t ti = c.D > 1 ? umulhi64(b1.hi, c.D) : 0ull;
+        loc = pack_loc(tx, ty, ti);
+        return false;
+    }
+    // habitat map: alias row of the origin cell
+    const uint32_t n_off = __ldg(&p->n_off);
+    const uint32_t row = __ldg(p->row_of + (size_t)y * c.W + x);
+    const uint32_t col = (uint32_t)(((b0.hi >> 32) * (uint64_t)n_off) >> 32);
+    const uint64_t e = __ldg(p->alias + (size_t)row * n_off + col);
+    const uint32_t u = (uint32_t)b0.hi;
+    const uint32_t o = ((e >> 63) != 0 || u < (uint32_t)e) ? col : (uint32_t)((e >> 32) & 0xFFFFu);
+    const int8_t* off = p->off;
+    const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+    const uint32_t tx = wrap_add(x, dx, c.W);
+    const uint32_t ty = wrap_add(y, dy, c.H);
+    const uint32_t d = __ldg(p->deme_map + (size_t)ty * c.W + tx);
+    loc = pack_loc(tx, ty, umulhi64(b1.lo, d));
+    return false;
+}
+
+__device__ __forceinline__ uint64_t slot_key(const SimParams* __restrict__ P, const LaneSim& c, uint64_t loc) {
+    const uint64_t cell = (uint64_t)loc_y(loc) * c.W + loc_x(loc);
+    return __ldg(&P[c.sim].slot_base) + cell * __ldg(&P[c.sim].slot_deme) + loc_i(loc);
+}
+
+// exact distinct-event counting: insert (slot, time bits); true if new
+__device__ __forceinline__ bool count_event(const BatchDev& B, uint32_t t, uint64_t skey, double tau) {
+    EvSlot mine;
+    mine.a = skey;
+    mine.b = (unsigned long long)__double_as_longlong(tau);
+    EvSlot empty;
+    empty.a = EMPTY_KEY;
+    empty.b = EMPTY_KEY;
+    uint32_t h = (uint32_t)mix64(skey ^ (mine.b * 0x9E3779B97F4A7C15ull)) & B.ev_mask;
+    for (uint32_t probe = 0; probe <= B.ev_mask; ++probe) {
+        EvSlot old = atomicCAS(&B.ev[t][h], empty, mine);
+        if (old.a == EMPTY_KEY && old.b == EMPTY_KEY) {
+            uint32_t k = atomicAdd(&B.G->ev_used[t], 1u);
+            B.ev_used[t][k] = h;
+            return true;
+        }
+        if (old.a == mine.a && old.b == mine.b) return false;
+        h = (h + 1u) & B.ev_mask;
+    }
+    atomicOr(&B.G->error, 2u);
+    return false;
+}
+
+__device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint64_t skey, uint32_t gid) {
+    const uint32_t mask = B.G->mask[t];
+    uint32_t h = (uint32_t)mix64(skey) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long old = atomicCAS(&B.ht_key[t][h], EMPTY_KEY, (unsigned long long)skey);
+        if (old == EMPTY_KEY) {
+            uint32_t k = atomicAdd(&B.G->used[t], 1u);
+            B.ht_used[t][k] = h;
+            atomicMin(&B.ht_val[t][h], gid);
+            return;
+        }
+        if (old == skey) {
+            atomicMin(&B.ht_val[t][h], gid);
+            return;
+        }
+        h = (h + 1u) & mask;
+    }
+    atomicOr(&B.G->error, 4u);
+}
+
+__device__ __forceinline__ uint32_t dedup_lookup(const BatchDev& B, uint32_t t, uint64_t skey) {
+    const uint32_t mask = B.G->mask[t];
+    uint32_t h = (uint32_t)mix64(skey) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = B.ht_key[t][h];
+        if (k == skey) return B.ht_val[t][h];
+        if (k == EMPTY_KEY) break;
+        h = (h + 1u) & mask;
+    }
+    return 0xFFFFFFFFu;
+}
+
+// warp-aggregated add of v to ctr[sim] over the lanes of mask
+__device__ __forceinline__ void warp_add_by_sim(unsigned mask, uint32_t sim, uint64_t v, uint64_t* base,
+                                                size_t stride_bytes) {
+    if (!mask) return;
+    const unsigned grp = __match_any_sync(mask, sim);
+    const int leader = __ffs(grp) - 1;
+    uint64_t sum = 0;
+    // reduce within the group: every lane contributes, the leader adds
+    for (int l = 0; l < 32; ++l) {
+        if (!((mask >> l) & 1u)) continue;
+        uint64_t x = __shfl_sync(mask, v, l);
+        if ((grp >> l) & 1u) sum += x;
+    }
+    if ((int)(threadIdx.x & 31) == leader && sum)
+        atomicAdd((unsigned long long*)((char*)base + stride_bytes * sim), (unsigned long long)sum);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32_t n_lin) {
+    __shared__ uint64_t sL[256];
+    __shared__ uint32_t sR[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        sL[i] = g_ln.L[i];
+        sR[i] = g_ln.R[i];
+    }
+    __syncthreads();
+    LnSh ln{sL, sR, g_ln.ln2_q64, {g_ln.c[0], g_ln.c[1], g_ln.c[2], g_ln.c[3], g_ln.c[4], g_ln.c[5], g_ln.c[6]}};
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_lin; g += gridDim.x * blockDim.x) {
+        // simulation of lineage g: last s with gid_base[s] <= g
+        uint32_t lo = 0, hi = B.n_sims;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (gid_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        LaneSim c;
+        load_lanesim(c, B.P, B.S, lo);
+        const uint64_t loc = B.P[lo].sample_loc[g - gid_base[lo]];
+        double t = next_event_time(c, loc, 0.0, ln);
+        if (t < 0.0) {
+            atomicOr(&B.S[lo].error, 1u);
+            atomicOr(&B.G->error, 1u);
+            t = INFINITY;
+        }
+        B.lin[0].loc[g] = loc;
+        B.lin[0].tn[g] = t;
+        B.lin[0].gid[g] = g;
+        B.lin[0].sim[g] = lo;
+        B.parent[g] = g;
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(512) k_advance(BatchDev B) {
+    __shared__ uint64_t sL[256];
+    __shared__ uint32_t sR[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        sL[i] = g_ln.L[i];
+        sR[i] = g_ln.R[i];
+    }
+    __syncthreads();
+    const LnSh ln{sL, sR, g_ln.ln2_q64, {g_ln.c[0], g_ln.c[1], g_ln.c[2], g_ln.c[3], g_ln.c[4], g_ln.c[5], g_ln.c[6]}};
+
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t n = B.G->n_total;
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t chunk = 32u * B.lpl;
+
+    uint32_t chunk_next = 0, chunk_end = 0;  // warp-uniform
+    bool exhausted = false;
+
+    bool has = false;
+    uint32_t idx = 0, gid = 0;
+    uint64_t loc = 0;
+    double tn = 0.0;
+    LaneSim c;
+    c.sim = 0xFFFFFFFFu;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+
+    for (;;) {
+        unsigned need = __ballot_sync(0xFFFFFFFFu, !has);
+        if (need) {
+            if (chunk_next >= chunk_end && !exhausted) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&B.G->work_ctr, chunk);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base >= n) {
+                    exhausted = true;
+                } else {
+                    chunk_next = base;
+                    chunk_end = min(base + chunk, n);
+                }
+            }
+            if (chunk_next < chunk_end) {
+                const uint32_t avail = chunk_end - chunk_next;
+                const uint32_t rank = __popc(need & lt_mask);
+                if (!has && rank < avail) {
+                    idx = chunk_next + rank;
+                    gid = L.gid[idx];
+                    loc = L.loc[idx];
+                    tn = L.tn[idx];
+                    const uint32_t s = L.sim[idx];
+                    if (s != c.sim) {
+                        if (cnt_sim != 0xFFFFFFFFu && (ev_raw | ev_unique)) {
+                            atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                            if (COUNT)
+                                atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events,
+                                          (unsigned long long)ev_unique);
+                            ev_raw = ev_unique = 0;
+                        }
+                        load_lanesim(c, B.P, B.S, s);
+                        cnt_sim = s;
+                    }
+                    has = true;
+                }
+                chunk_next += min(avail, (uint32_t)__popc(need));
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, has)) {
+            if (exhausted) break;
+            continue;
+        }
+        if (has) {
+            if (!(tn <= c.horizon)) {
+                // at the horizon: write back and enter the dedup
+                L.loc[idx] = loc;
+                L.tn[idx] = tn;
+                if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                has = false;
+            } else {
+                ++ev_raw;
+                if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+                if (do_event(c, B.P, loc, tn)) {
+                    B.key_loc[gid] = loc;
+                    B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                    L.gid[idx] = gid | DONE_BIT;
+                    has = false;
+                } else {
+                    const double nt = next_event_time(c, loc, tn, ln);
+                    if (nt < 0.0) {
+                        atomicOr(&B.S[c.sim].error, 1u);
+                        atomicOr(&B.G->error, 1u);
+                        B.key_loc[gid] = ~0ull;
+                        B.key_time[gid] = ~0ull;
+                        L.gid[idx] = gid | DONE_BIT;
+                        has = false;
+                    } else {
+                        tn = nt;
+                    }
+                }
+            }
+        }
+    }
+    // flush the event counters, aggregated over lanes of the same simulation
+    const bool valid = cnt_sim != 0xFFFFFFFFu;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+        warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
+        if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
+    }
+}
+
+// horizon step (time) of a simulation with n active lineages
+__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n) {
+    const double dn = (double)n;
+    const double floor_ev = dn < p->busy_lineages ? p->tail_events : p->min_events;
+    const double per = fmax(floor_ev, fmin(p->occupancy_step * p->n_slots / dn, p->events_per_round / dn));
+    return per / p->lambda;
+}
+
+__global__ void k_compact(BatchDev B) {
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs in = B.lin[t];
+    const LinPtrs out = B.lin[t ^ 1u];
+    const uint32_t n = B.G->n_total;
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+
+    for (uint32_t base = warp_global * 32u; base < n; base += n_warps * 32u) {
+        const uint32_t i = base + lane;
+        bool survive = false, culled = false;
+        uint32_t s = 0xFFFFFFFFu, g = 0;
+        uint64_t loc = 0;
+        double tn = 0.0;
+        if (i < n) {
+            g = in.gid[i];
+            if (!(g & DONE_BIT)) {
+                s = in.sim[i];
+                loc = in.loc[i];
+                tn = in.tn[i];
+                survive = true;
+                if (B.dedup) {
+                    const SimParams* p = B.P + s;
+                    const uint64_t cell = (uint64_t)loc_y(loc) * p->W + loc_x(loc);
+                    const uint64_t sk = p->slot_base + cell * p->slot_deme + loc_i(loc);
+                    const uint32_t w = dedup_lookup(B, t, sk);
+                    if (w != g && w != 0xFFFFFFFFu) {
+                        B.parent[g] = w;
+                        survive = false;
+                        culled = true;
+                    }
+                }
+            }
+        }
+        const unsigned sm = __ballot_sync(0xFFFFFFFFu, survive);
+        const unsigned cm = __ballot_sync(0xFFFFFFFFu, culled);
+        uint32_t pos0 = 0;
+        if (lane == 0 && sm) pos0 = atomicAdd(&B.G->n_total_next, (uint32_t)__popc(sm));
+        pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
+        if (survive) {
+            const uint32_t pos = pos0 + __popc(sm & lt_mask);
+            out.loc[pos] = loc;
+            out.tn[pos] = tn;
+            out.gid[pos] = g;
+            out.sim[pos] = s;
+        }
+        if (sm) {
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, survive ? s : 0xFFFFFFFFu);
+            if (survive && lane == (uint32_t)(__ffs(grp) - 1))
+                atomicAdd(&B.S[s].n_next, (uint32_t)__popc(grp));
+        }
+        if (cm) {
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, culled ? s : 0xFFFFFFFFu);
+            if (culled && lane == (uint32_t)(__ffs(grp) - 1))
+                atomicAdd(&B.S[s].culled_round, (uint32_t)__popc(grp));
+        }
+    }
+    // clear the dedup / event tables of the previous round (no longer read)
+    const uint32_t tp = t ^ 1u;
+    const uint32_t nu = B.G->used[tp];
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += gridDim.x * blockDim.x) {
+        const uint32_t h = B.ht_used[tp][k];
+        B.ht_key[tp][h] = EMPTY_KEY;
+        B.ht_val[tp][h] = 0xFFFFFFFFu;
+    }
+    if (B.count_unique) {
+        const uint32_t ne = B.G->ev_used[tp];
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
+            const uint32_t h = B.ev_used[tp][k];
+            B.ev[tp][h].a = EMPTY_KEY;
+            B.ev[tp][h].b = EMPTY_KEY;
+        }
+    }
+
+    // the last block to finish advances the round
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&B.G->blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ uint32_t live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
+        SimState* st = B.S + s;
+        const uint32_t na = atomicAdd(&st->n_next, 0u);
+        const uint32_t nc = atomicAdd(&st->culled_round, 0u);
+        st->culled += nc;
+        st->culled_round = 0;
+        st->n_next = 0;
+        if (st->done) continue;
+        st->n_active = na;
+        st->rounds += 1;
+        if (na == 0) {
+            st->done = 1;
+            continue;
+        }
+        atomicAdd(&live, 1u);
+        st->horizon = st->horizon + horizon_step(B.P + s, na);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Globals* G = B.G;
+        const uint32_t nt = atomicAdd(&G->n_total_next, 0u);
+        G->n_total = nt;
+        G->n_total_next = 0;
+        G->work_ctr = 0;
+        G->blocks_done = 0;
+        G->used[tp] = 0;
+        G->ev_used[tp] = 0;
+        G->n_live_sims = live;
+        uint32_t cap = 2u;
+        while (cap < 2u * nt && cap < B.ht_cap) cap <<= 1;
+        G->mask[tp] = cap - 1u;  // the next round uses table tp
+        G->round += 1;
+        __threadfence();
+    }
+}
+
+// initial horizons and counters of a fresh batch
+__global__ void k_start(BatchDev B, uint32_t n_lin) {
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
+        const SimParams* p = B.P + s;
+        SimState* st = B.S + s;
+        const uint32_t na = p->n_lineages;
+        st->n_active = na;
+        st->done = na == 0 ? 1u : 0u;
+        st->horizon = horizon_step(p, max(na, 1u));
+    }
+    if (threadIdx.x == 0) {
+        Globals* G = B.G;
+        G->n_total = n_lin;
+        uint32_t cap = 2u;
+        while (cap < 2u * n_lin && cap < B.ht_cap) cap <<= 1;
+        G->mask[0] = cap - 1u;
+        G->mask[1] = cap - 1u;
+    }
+}
+
+// root of every lineage (pointer chase over parent) and collection of roots
+struct SortItem {
+    unsigned long long a, b, c, d;  // sim, key location, key time bits, lineage id
+};
+
+__global__ void k_roots(BatchDev B, uint32_t n_lin, uint32_t* root, SortItem* items, uint32_t* n_items,
+                        const uint32_t* __restrict__ gid_base) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_lin; g += gridDim.x * blockDim.x) {
+        uint32_t r = g;
+        for (uint32_t hops = 0; hops < n_lin; ++hops) {
+            const uint32_t p = B.parent[r];
+            if (p == r) break;
+            r = p;
+        }
+        root[g] = r;
+        if (r == g) {
+            uint32_t lo = 0, hi = B.n_sims;
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (gid_base[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t k = atomicAdd(n_items, 1u);
+            items[k] = SortItem{lo, B.key_loc[g], B.key_time[g], g};
+        }
+    }
+}
+
+__device__ __forceinline__ bool item_less(const SortItem& x, const SortItem& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    return x.c < y.c;
+}
+
+__global__ void k_pad_items(SortItem* items, const uint32_t* n_items, uint32_t n_pad) {
+    const uint32_t n = *n_items;
+    for (uint32_t i = n + blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
+        items[i] = SortItem{~0ull, ~0ull, ~0ull, ~0ull};
+}
+
+__global__ void k_bitonic_global(SortItem* x, uint32_t n, uint32_t j, uint32_t k) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t l = i ^ j;
+    if (l <= i) return;
+    const SortItem A = x[i], Bv = x[l];
+    const bool up = (i & k) == 0;
+    if (item_less(Bv, A) == up) {
+        x[i] = Bv;
+        x[l] = A;
+    }
+}
+
+// all stages with j < 2 * blockDim.x for one k, in shared memory
+__global__ void k_bitonic_shared(SortItem* x, uint32_t n, uint32_t k, uint32_t j_start) {
+    extern __shared__ SortItem sh[];
+    const uint32_t span = 2u * blockDim.x;
+    const uint32_t base = blockIdx.x * span;
+    for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) sh[i] = x[base + i];
+    __syncthreads();
+    for (uint32_t j = j_start; j > 0; j >>= 1) {
+        for (uint32_t ii = threadIdx.x; ii < span; ii += blockDim.x) {
+            const uint32_t l = ii ^ j;
+            if (l > ii) {
+                const uint32_t gi = base + ii;
+                const bool up = (gi & k) == 0;
+                const SortItem A = sh[ii], Bv = sh[l];
+                if (item_less(Bv, A) == up) {
+                    sh[ii] = Bv;
+                    sh[l] = A;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < span; i += blockDim.x) x[base + i] = sh[i];
+}
+
+// heads of distinct keys and of simulations
+__global__ void k_heads(const SortItem* x, const uint32_t* n_items, uint32_t* head) {
+    const uint32_t n = *n_items;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        bool h = i == 0 || x[i].a != x[i - 1].a || x[i].b != x[i - 1].b || x[i].c != x[i - 1].c;
+        head[i] = h ? 1u : 0u;
+    }
+}
+
+// distinct index (inclusive scan - 1) -> rank within the simulation
+__global__ void k_sim_first(const SortItem* x, const uint32_t* n_items, const uint32_t* incl,
+                            uint32_t* sim_first, uint64_t* sim_count) {
+    const uint32_t n = *n_items;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i == 0 || x[i].a != x[i - 1].a) sim_first[x[i].a] = incl[i] - 1u;
+        if (i == n - 1 || x[i].a != x[i + 1].a) sim_count[x[i].a] = incl[i];  // fixed up below
+    }
+}
+
+__global__ void k_sim_count_fix(const uint32_t* sim_first, uint64_t* sim_count, uint32_t n_sims,
+                                const uint32_t* n_items) {
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sims; s += gridDim.x * blockDim.x)
+        if (sim_count[s] != 0) sim_count[s] -= sim_first[s];
+}
+
+__global__ void k_rank(const SortItem* x, const uint32_t* n_items, const uint32_t* incl,
+                       const uint32_t* sim_first, uint32_t* rank_of_root) {
+    const uint32_t n = *n_items;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        rank_of_root[x[i].d] = incl[i] - 1u - sim_first[x[i].a];
+}
+
+// per-individual outputs of one simulation
+__global__ void k_outputs(const uint32_t* root, const uint32_t* rank_of_root, const uint64_t* key_loc,
+                          const uint64_t* key_time, uint32_t gid_base, uint32_t n, uint64_t* species,
+                          uint64_t* out_loc, uint64_t* out_time) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t r = root[gid_base + i];
+        species[i] = rank_of_root[r];
+        out_loc[i] = key_loc[r];
+        out_time[i] = key_time[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of u32 (block scan, recursive over block sums)
+// ---------------------------------------------------------------------------
+constexpr uint32_t SCAN_BLOCK = 1024;
+constexpr uint32_t SCAN_ITEMS = 4;
+constexpr uint32_t SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t ws = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, ws, o);
+            if (lane >= (uint32_t)o) ws += y;
+        }
+        warp_sums[lane] = ws;
+    }
+    __syncthreads();
+    const uint32_t before = w > 0 ? warp_sums[w - 1] : 0u;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// exclusive (inclusive if incl) scan of a tile; tile totals into sums
+__global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, uint32_t* sums, uint32_t n, int inclusive) {
+    const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t local = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        local += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(local, &total);
+#pragma unroll
+    for (uint32_t k = 0; k < SCAN_ITEMS; ++k) {
+        if (inclusive) run += v[k];
+        if (base + k < n) out[base + k] = run;
+        if (!inclusive) run += v[k];
+    }
+    if (threadIdx.x == 0 && sums) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(uint32_t* out, const uint32_t* sums_excl, uint32_t n) {
+    const uint32_t base = blockIdx.x * SCAN_TILE;
+    const uint32_t add = sums_excl[blockIdx.x];
+    for (uint32_t k = threadIdx.x; k < SCAN_TILE; k += blockDim.x)
+        if (base + k < n) out[base + k] += add;
+}
+
+static ind_status scan_u32(Pool& pool, const uint32_t* in, uint32_t* out, uint32_t n, bool inclusive,
+                           cudaStream_t s) {
+    if (n == 0) return IND_OK;
+    const uint32_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        k_scan_tiles<<<1, SCAN_BLOCK, 0, s>>>(in, out, nullptr, n, inclusive ? 1 : 0);
+        CKL();
+        return IND_OK;
+    }
+    uint32_t* sums = pool.get<uint32_t>(tiles);
+    uint32_t* sums_ex = pool.get<uint32_t>(tiles);
+    if (!sums || !sums_ex) return IND_ERR_OOM;
+    k_scan_tiles<<<tiles, SCAN_BLOCK, 0, s>>>(in, out, sums, n, inclusive ? 1 : 0);
+    CKL();
+    ind_status st = scan_u32(pool, sums, sums_ex, tiles, false, s);
+    if (st != IND_OK) return st;
+    k_scan_add<<<tiles, SCAN_BLOCK, 0, s>>>(out, sums_ex, n);
+    CKL();
+    return IND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// inputs: habitat map, alias rows, sampling
+// ---------------------------------------------------------------------------
+__global__ void k_habitat(uint8_t* out, uint32_t W, uint32_t H, uint32_t sk0, uint32_t sk1, uint64_t thr,
+                          uint32_t max_deme) {
+    const uint64_t n = (uint64_t)W * H;
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(c % W), y = (uint32_t)(c / W);
+        const u64x2 b = stream_block(sk0, sk1, pack_loc(x, y, 0), 0, 0, TAG_MAP);
+        out[c] = (b.lo >> 11) < thr ? (uint8_t)(1u + umulhi64(b.hi, max_deme)) : (uint8_t)0;
+    }
+}
+
+// one warp per habitable cell: weights, then integer Vose on lane 0
+__global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint32_t H,
+                              const uint32_t* __restrict__ cells, uint32_t n_rows, const int8_t* __restrict__ off,
+                              uint32_t n_off, const uint64_t* __restrict__ kw, uint64_t* __restrict__ alias) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const size_t per_warp = ((size_t)n_off * 12 + 15) & ~(size_t)15;  // 16-byte aligned regions
+    uint64_t* s = (uint64_t*)(smem + per_warp * w);
+    uint16_t* small_ = (uint16_t*)(s + n_off);
+    uint16_t* large_ = small_ + n_off;
+    for (uint32_t row = blockIdx.x * warps + w; row < n_rows; row += gridDim.x * warps) {
+        const uint32_t cell = cells[row];
+        const uint32_t cx = cell % W, cy = cell / W;
+        unsigned long long part = 0;
+        for (uint32_t o = lane; o < n_off; o += 32) {
+            const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+            const uint32_t tx = wrap_add(cx, dx, W), ty = wrap_add(cy, dy, H);
+            const uint64_t wgt = kw[dx * dx + dy * dy] * (uint64_t)deme[(size_t)ty * W + tx];
+            s[o] = (uint64_t)n_off * wgt;
+            part += wgt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        __syncwarp();
+        if (lane == 0) {
+            const uint64_t Wt = part;
+            uint64_t* e = alias + (size_t)row * n_off;
+            uint32_t ns = 0, nl = 0;
+            for (uint32_t o = 0; o < n_off; ++o) {
+                if (s[o] < Wt) small_[ns++] = (uint16_t)o;
+                else large_[nl++] = (uint16_t)o;
+            }
+            while (ns > 0 && nl > 0) {
+                const uint32_t a = small_[--ns];
+                const uint32_t b = large_[--nl];
+                // q = floor(s_a 2^32 / W) by restoring division (s_a < W < 2^56)
+                uint64_t rem = s[a], q = 0;
+                for (int bit = 0; bit < 32; ++bit) {
+                    rem <<= 1;
+                    q <<= 1;
+                    if (rem >= Wt) {
+                        rem -= Wt;
+                        q |= 1ull;
+                    }
+                }
+                e[a] = q | ((uint64_t)b << 32);
+                s[b] = s[b] + s[a] - Wt;
+                if (s[b] < Wt) small_[ns++] = (uint16_t)b;
+                else large_[nl++] = (uint16_t)b;
+            }
+            while (nl > 0) {
+                const uint32_t b = large_[--nl];
+                e[b] = 0xFFFFFFFFull | ((uint64_t)b << 32) | (1ull << 63);
+            }
+            while (ns > 0) {
+                const uint32_t a = small_[--ns];
+                e[a] = 0xFFFFFFFFull | ((uint64_t)a << 32) | (1ull << 63);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_sample_flags(uint32_t* flags, uint64_t n_slots, int kind, uint32_t W, uint32_t D,
+                               uint32_t slot_deme, const uint8_t* deme, int all, uint32_t sk0, uint32_t sk1,
+                               uint64_t thr) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t cell = s / slot_deme;
+        const uint32_t i = (uint32_t)(s % slot_deme);
+        const uint32_t d = kind == KIND_MAP ? deme[cell] : D;
+        bool keep = i < d;
+        if (keep && !all) {
+            const uint64_t loc = pack_loc(cell % W, cell / W, i);
+            keep = (stream_block(sk0, sk1, loc, 0, 0, TAG_SAMPLE).lo >> 11) < thr;
+        }
+        flags[s] = keep ? 1u : 0u;
+    }
+}
+
+__global__ void k_sample_write(const uint32_t* flags, const uint32_t* pos, uint64_t n_slots, uint32_t W,
+                               uint32_t slot_deme, uint64_t* out) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        if (!flags[s]) continue;
+        const uint64_t cell = s / slot_deme;
+        out[pos[s]] = pack_loc(cell % W, cell / W, s % slot_deme);
+    }
+}
+
+// device arithmetic probes for the conformance tests
+__global__ void k_selftest(const uint64_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ exp_q58,
+                           uint32_t* __restrict__ philox_out) {
+    __shared__ uint64_t sL[256];
+    __shared__ uint32_t sR[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        sL[i] = g_ln.L[i];
+        sR[i] = g_ln.R[i];
+    }
+    __syncthreads();
+    int64_t c[7];
+    for (int k = 0; k < 7; ++k) c[k] = g_ln.c[k];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = in[i];
+        if (exp_q58) exp_q58[i] = exp1_q58(v >> 11, sL, sR, g_ln.ln2_q64, c);
+        if (philox_out) {
+            const uint64_t w = in[(i + 1) % n], z = in[(i + 2) % n];
+            const u32x4 o = philox10((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)w, (uint32_t)(w >> 32),
+                                     (uint32_t)z, (uint32_t)(z >> 32));
+            philox_out[4 * i + 0] = o.x;
+            philox_out[4 * i + 1] = o.y;
+            philox_out[4 * i + 2] = o.z;
+            philox_out[4 * i + 3] = o.w;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host objects
+// ---------------------------------------------------------------------------
+struct Batch;
+
+struct ind_sim {
+    ind_landscape land{};
+    ind_dispersal disp{};
+    double nu = 0.0;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;
+    ind_tuning tuning{};
+    uint32_t sk0 = 0, sk1 = 0;
+    uint64_t nu_thr = 0;
+    int dt_log2 = 0;
+    uint32_t slot_deme = 1;
+    uint64_t n_slots = 0;  // indexed locations (individuals of a full landscape)
+    Pool tables;   // dispersal tables, map
+    Pool sample;   // sampled locations
+    Pool results;  // outputs
+    uint64_t* d_gauss = nullptr;
+    uint32_t gauss_n = 0;
+    int gauss_half = 0;
+    uint8_t* d_deme = nullptr;
+    uint32_t* d_row_of = nullptr;
+    uint64_t* d_alias = nullptr;
+    int8_t* d_off = nullptr;
+    uint32_t n_off = 0, n_rows = 0;
+    uint64_t* d_sample = nullptr;
+    uint64_t n_sampled = 0;
+    bool sampled = false;
+    bool finished = false;
+    uint64_t* d_species = nullptr;
+    uint64_t* d_key_loc = nullptr;
+    uint64_t* d_key_time = nullptr;
+    uint64_t n_species = 0;
+    Batch* batch = nullptr;
+    ind_run_stats stats{};
+};
+
+static void seed_key(uint64_t seed, uint32_t* k0, uint32_t* k1) {
+    u32x4 o = philox10((uint32_t)seed, (uint32_t)(seed >> 32), 0, 0, 0, 0);
+    *k0 = o.x;
+    *k1 = o.y;
+}
+
+static uint32_t sm_count() {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return (uint32_t)n;
+}
+
+static uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t max_blocks) {
+    uint64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return (uint32_t)b;
+}
+
+struct Batch {
+    std::vector<ind_sim*> sims;
+    uint32_t n_sims = 0;
+    uint32_t n_lin = 0;
+    cudaStream_t stream = nullptr;
+    ind_tuning tun{};
+    Pool pool;
+    Pool scratch;
+    SimParams* d_params = nullptr;
+    SimState* d_state = nullptr;
+    Globals* d_g = nullptr;
+    uint32_t* d_gid_base = nullptr;
+    BatchDev dev{};
+    Globals* h_g = nullptr;  // pinned
+    std::vector<SimState> h_state;
+    bool started = false;
+    bool finished = false;
+    uint64_t rounds = 0;
+    cudaGraphExec_t graph = nullptr;
+    uint32_t graph_rounds = 0;
+    cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
+    std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
+    double advance_ms = 0.0;
+    uint64_t advance_launches = 0;
+    uint32_t adv_blocks = 0, adv_threads = 0, cmp_blocks = 0;
+    double ms = 0.0;
+
+    ~Batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (auto e : ev_start) cudaEventDestroy(e);
+        for (auto e : ev_end) cudaEventDestroy(e);
+        if (h_g) cudaFreeHost(h_g);
+        scratch.release_all();
+        pool.release_all();
+    }
+};
+
+static ind_status batch_build(Batch& b) {
+    b.pool.stream = b.scratch.stream = b.stream;
+    b.n_sims = (uint32_t)b.sims.size();
+    std::vector<SimParams> hp(b.n_sims);
+    std::vector<uint32_t> gid_base(b.n_sims);
+    uint64_t lin = 0, slots = 0;
+    for (uint32_t s = 0; s < b.n_sims; ++s) {
+        ind_sim* m = b.sims[s];
+        SimParams& p = hp[s];
+        memset(&p, 0, sizeof(p));
+        p.kind = m->land.kind;
+        p.W = m->land.width;
+        p.H = m->land.height;
+        p.D = m->land.kind == IND_MAP ? 0 : m->land.deme;
+        p.slot_deme = m->slot_deme;
+        p.dt_log2 = m->dt_log2;
+        p.nu_thr = m->nu_thr;
+        p.lambda = m->land.lambda;
+        p.sk0 = m->sk0;
+        p.sk1 = m->sk1;
+        p.gauss_half = m->gauss_half;
+        p.gauss_n = m->gauss_n;
+        p.gauss = m->d_gauss;
+        p.deme_map = m->d_deme;
+        p.row_of = m->d_row_of;
+        p.alias = m->d_alias;
+        p.off = m->d_off;
+        p.n_off = m->n_off;
+        p.n_lineages = (uint32_t)m->n_sampled;
+        p.slot_base = slots;
+        p.gid_base = (uint32_t)lin;
+        p.sample_loc = m->d_sample;
+        p.events_per_round = b.tun.events_per_round;
+        p.min_events = b.tun.min_events_per_lineage;
+        p.occupancy_step = b.tun.occupancy_step;
+        p.tail_events = b.tun.tail_events;
+        p.busy_lineages = b.tun.busy_lineages;
+        p.n_slots = (double)m->n_slots;
+        gid_base[s] = (uint32_t)lin;
+        lin += m->n_sampled;
+        slots += (uint64_t)m->land.width * m->land.height * m->slot_deme;
+    }
+    if (lin >= (1ull << 31)) return IND_ERR_ARG;
+    b.n_lin = (uint32_t)lin;
+    const uint32_t n = std::max<uint32_t>(b.n_lin, 1u);
+    Pool& P = b.pool;
+    b.d_params = P.get<SimParams>(b.n_sims);
+    b.d_state = P.get<SimState>(b.n_sims);
+    b.d_g = P.get<Globals>(1);
+    b.d_gid_base = P.get<uint32_t>(b.n_sims);
+    BatchDev& d = b.dev;
+    for (int t = 0; t < 2; ++t) {
+        d.lin[t].loc = P.get<uint64_t>(n);
+        d.lin[t].tn = P.get<double>(n);
+        d.lin[t].gid = P.get<uint32_t>(n);
+        d.lin[t].sim = P.get<uint32_t>(n);
+    }
+    d.parent = P.get<uint32_t>(n);
+    d.key_loc = P.get<uint64_t>(n);
+    d.key_time = P.get<uint64_t>(n);
+    uint32_t cap = 2;
+    while (cap < 2u * n) cap <<= 1;
+    d.ht_cap = cap;
+    for (int t = 0; t < 2; ++t) {
+        d.ht_key[t] = P.get<unsigned long long>(cap);
+        d.ht_val[t] = P.get<uint32_t>(cap);
+        d.ht_used[t] = P.get<uint32_t>(n);
+    }
+    d.count_unique = b.tun.count_unique ? 1 : 0;
+    if (d.count_unique) {
+        double est = 0;
+        for (uint32_t s = 0; s < b.n_sims; ++s)
+            est += std::max(b.tun.events_per_round, b.tun.min_events_per_lineage * (double)hp[s].n_lineages) + 64.0;
+        uint64_t ec = 2;
+        while ((double)ec < 3.0 * est && ec < (1ull << 30)) ec <<= 1;
+        d.ev_mask = (uint32_t)(ec - 1);
+        for (int t = 0; t < 2; ++t) {
+            d.ev[t] = P.get<EvSlot>(ec);
+            d.ev_used[t] = P.get<uint32_t>(ec);
+        }
+    }
+    for (int t = 0; t < 2; ++t)
+        if (!d.lin[t].loc || !d.lin[t].tn || !d.lin[t].gid || !d.lin[t].sim || !d.ht_key[t] || !d.ht_val[t] ||
+            !d.ht_used[t] || (d.count_unique && (!d.ev[t] || !d.ev_used[t])))
+            return IND_ERR_OOM;
+    if (!b.d_params || !b.d_state || !b.d_g || !b.d_gid_base || !d.parent || !d.key_loc || !d.key_time)
+        return IND_ERR_OOM;
+    d.P = b.d_params;
+    d.S = b.d_state;
+    d.G = b.d_g;
+    d.n_sims = b.n_sims;
+    d.lpl = b.tun.lineages_per_lane;
+    d.dedup = b.tun.dedup ? 1 : 0;
+    cudaStream_t s = b.stream;
+    CK(cudaMemcpyAsync(b.d_params, hp.data(), sizeof(SimParams) * b.n_sims, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(b.d_gid_base, gid_base.data(), sizeof(uint32_t) * b.n_sims, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(b.d_state, 0, sizeof(SimState) * b.n_sims, s));
+    CK(cudaMemsetAsync(b.d_g, 0, sizeof(Globals), s));
+    for (int t = 0; t < 2; ++t) {
+        CK(cudaMemsetAsync(d.ht_key[t], 0xFF, sizeof(unsigned long long) * cap, s));
+        CK(cudaMemsetAsync(d.ht_val[t], 0xFF, sizeof(uint32_t) * cap, s));
+        if (d.count_unique) CK(cudaMemsetAsync(d.ev[t], 0xFF, sizeof(EvSlot) * ((size_t)d.ev_mask + 1), s));
+    }
+    CK(cudaMallocHost(&b.h_g, sizeof(Globals)));
+    b.h_state.resize(b.n_sims);
+    if (b.tun.profile) {
+        b.ev_start.resize(b.tun.rounds_per_check);
+        b.ev_end.resize(b.tun.rounds_per_check);
+        for (uint32_t r = 0; r < b.tun.rounds_per_check; ++r) {
+            CK(cudaEventCreate(&b.ev_start[r]));
+            CK(cudaEventCreate(&b.ev_end[r]));
+        }
+    }
+    const uint32_t sms = sm_count();
+    b.adv_threads = b.tun.block_threads;
+    b.adv_blocks = sms * b.tun.blocks_per_sm;
+    b.cmp_blocks = sms * 4;
+    // starting states
+    k_start<<<1, 256, 0, s>>>(d, b.n_lin);
+    CKL();
+    if (b.n_lin) {
+        k_init<<<grid_for(b.n_lin, 256, sms * 16), 256, 0, s>>>(d, b.d_gid_base, b.n_lin);
+        CKL();
+    }
+    b.started = true;
+    return IND_OK;
+}
+
+static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
+    cudaStream_t s = capturing ? b.cap_stream : b.stream;
+    const bool prof = b.tun.profile && r < b.ev_start.size();
+    const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
+    if (b.dev.count_unique) k_advance<true><<<b.adv_blocks, b.adv_threads, 0, s>>>(b.dev);
+    else k_advance<false><<<b.adv_blocks, b.adv_threads, 0, s>>>(b.dev);
+    CKL();
+    if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));
+    k_compact<<<b.cmp_blocks, 256, 0, s>>>(b.dev);
+    CKL();
+    return IND_OK;
+}
+
+static ind_status batch_rounds(Batch& b, uint32_t rounds) {
+    if (b.tun.use_graph) {
+        if (!b.graph || b.graph_rounds != rounds) {
+            if (b.graph) {
+                cudaGraphExecDestroy(b.graph);
+                b.graph = nullptr;
+            }
+            cudaGraph_t g;
+            if (!b.cap_stream) CK(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
+            CK(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (uint32_t r = 0; r < rounds; ++r) {
+                ind_status st = launch_round(b, r, true);
+                if (st != IND_OK) {
+                    cudaStreamEndCapture(b.cap_stream, &g);
+                    return st;
+                }
+            }
+            CK(cudaStreamEndCapture(b.cap_stream, &g));
+            CK(cudaGraphInstantiate(&b.graph, g, 0));
+            cudaGraphDestroy(g);
+            b.graph_rounds = rounds;
+        }
+        CK(cudaGraphLaunch(b.graph, b.stream));
+        g_launches.fetch_add(2ull * rounds);
+        return IND_OK;
+    }
+    for (uint32_t r = 0; r < rounds; ++r) {
+        ind_status st = launch_round(b, r, false);
+        if (st != IND_OK) return st;
+    }
+    return IND_OK;
+}
+
+// after a synchronised chunk: add up the timed advance launches
+static void collect_profile(Batch& b, uint32_t rounds) {
+    if (!b.tun.profile) return;
+    for (uint32_t r = 0; r < rounds && r < b.ev_start.size(); ++r) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b.ev_start[r], b.ev_end[r]) == cudaSuccess) {
+            b.advance_ms += ms;
+            b.advance_launches += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+}
+
+// resolve roots, sort/unique species keys, write per-sim outputs
+static ind_status batch_finish(Batch& b) {
+    cudaStream_t s = b.stream;
+    Pool& T = b.scratch;
+    const uint32_t n = std::max<uint32_t>(b.n_lin, 1u);
+    const uint32_t sms = sm_count();
+    uint32_t* root = T.get<uint32_t>(n);
+    uint32_t* n_items = T.get<uint32_t>(1);
+    uint32_t n_pad = 1;
+    while (n_pad < n) n_pad <<= 1;
+    if (n_pad < 2048) n_pad = 2048;
+    SortItem* items = T.get<SortItem>(n_pad);
+    uint32_t* head = T.get<uint32_t>(n);
+    uint32_t* incl = T.get<uint32_t>(n);
+    uint32_t* sim_first = T.get<uint32_t>(b.n_sims);
+    uint64_t* sim_count = T.get<uint64_t>(b.n_sims);
+    uint32_t* rank = T.get<uint32_t>(n);
+    if (!root || !n_items || !items || !head || !incl || !sim_first || !sim_count || !rank) return IND_ERR_OOM;
+    CK(cudaMemsetAsync(n_items, 0, sizeof(uint32_t), s));
+    CK(cudaMemsetAsync(sim_count, 0, sizeof(uint64_t) * b.n_sims, s));
+    CK(cudaMemsetAsync(sim_first, 0, sizeof(uint32_t) * b.n_sims, s));
+    const uint32_t gb = grid_for(n, 256, sms * 16);
+    k_roots<<<gb, 256, 0, s>>>(b.dev, b.n_lin, root, items, n_items, b.d_gid_base);
+    CKL();
+    uint32_t h_items = 0;
+    CK(cudaMemcpyAsync(&h_items, n_items, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    uint32_t np = 2048;
+    while (np < h_items) np <<= 1;
+    k_pad_items<<<grid_for(np, 256, sms * 16), 256, 0, s>>>(items, n_items, np);
+    CKL();
+    // bitonic sort of np items: global stages for j >= 2048, shared for the rest
+    const uint32_t sh_threads = 1024;
+    const uint32_t span = 2 * sh_threads;
+    const size_t sh_bytes = sizeof(SortItem) * span;
+    static bool attr_set = false;
+    if (!attr_set) {
+        CK(cudaFuncSetAttribute(k_bitonic_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_bytes));
+        attr_set = true;
+    }
+    for (uint32_t k = 2; k <= np; k <<= 1) {
+        uint32_t j = k >> 1;
+        for (; j >= span; j >>= 1) {
+            k_bitonic_global<<<(np + 255) / 256, 256, 0, s>>>(items, np, j, k);
+            CKL();
+        }
+        k_bitonic_shared<<<np / span, sh_threads, sh_bytes, s>>>(items, np, k, j);
+        CKL();
+    }
+    k_heads<<<grid_for(h_items, 256, sms * 16), 256, 0, s>>>(items, n_items, head);
+    CKL();
+    ind_status st = scan_u32(T, head, incl, h_items, true, s);
+    if (st != IND_OK) return st;
+    if (h_items) {
+        k_sim_first<<<grid_for(h_items, 256, sms * 16), 256, 0, s>>>(items, n_items, incl, sim_first, sim_count);
+        CKL();
+        k_sim_count_fix<<<grid_for(b.n_sims, 256, sms), 256, 0, s>>>(sim_first, sim_count, b.n_sims, n_items);
+        CKL();
+        k_rank<<<grid_for(h_items, 256, sms * 16), 256, 0, s>>>(items, n_items, incl, sim_first, rank);
+        CKL();
+    }
+    std::vector<uint64_t> counts(b.n_sims);
+    for (uint32_t si = 0; si < b.n_sims; ++si) {
+        ind_sim* m = b.sims[si];
+        if (m->n_sampled == 0) continue;
+        if (!m->d_species) {
+            m->results.stream = m->stream;
+            m->d_species = m->results.get<uint64_t>(m->n_sampled);
+            m->d_key_loc = m->results.get<uint64_t>(m->n_sampled);
+            m->d_key_time = m->results.get<uint64_t>(m->n_sampled);
+            if (!m->d_species || !m->d_key_loc || !m->d_key_time) return IND_ERR_OOM;
+        }
+        uint32_t base = 0;
+        for (uint32_t k = 0; k < si; ++k) base += (uint32_t)b.sims[k]->n_sampled;
+        k_outputs<<<grid_for(m->n_sampled, 256, sms * 16), 256, 0, s>>>(
+            root, rank, b.dev.key_loc, b.dev.key_time, base, (uint32_t)m->n_sampled, m->d_species, m->d_key_loc,
+            m->d_key_time);
+        CKL();
+    }
+    CK(cudaMemcpyAsync(counts.data(), sim_count, sizeof(uint64_t) * b.n_sims, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b.h_state.data(), b.d_state, sizeof(SimState) * b.n_sims, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (uint32_t si = 0; si < b.n_sims; ++si) {
+        ind_sim* m = b.sims[si];
+        m->n_species = counts[si];
+        m->finished = true;
+        m->stats.n_species = counts[si];
+    }
+    b.scratch.release_all();
+    return IND_OK;
+}
+
+static void collect_stats(Batch& b, uint64_t n_roots_unknown) {
+    (void)n_roots_unknown;
+    for (uint32_t si = 0; si < b.n_sims; ++si) {
+        ind_sim* m = b.sims[si];
+        const SimState& st = b.h_state[si];
+        m->stats.rounds = st.rounds;
+        m->stats.raw_events = st.raw_events;
+        m->stats.unique_events = st.unique_events;
+        m->stats.culled = st.culled;
+        m->stats.n_sampled = m->n_sampled;
+        m->stats.n_roots = m->n_sampled - st.culled;
+    }
+}
+
+// run rounds until finished or budget; IND_ERR_BUDGET if not finished
+static ind_status batch_run(Batch& b, uint64_t round_budget) {
+    auto t0 = std::chrono::steady_clock::now();
+    ind_status result = IND_OK;
+    uint64_t done_rounds = 0;
+    for (;;) {
+        uint32_t chunk = b.tun.rounds_per_check;
+        if (round_budget) {
+            if (done_rounds >= round_budget) {
+                result = IND_ERR_BUDGET;
+                break;
+            }
+            chunk = (uint32_t)std::min<uint64_t>(chunk, round_budget - done_rounds);
+        }
+        ind_status st = batch_rounds(b, chunk);
+        if (st != IND_OK) return st;
+        done_rounds += chunk;
+        b.rounds += chunk;
+        CK(cudaMemcpyAsync(b.h_g, b.d_g, sizeof(Globals), cudaMemcpyDeviceToHost, b.stream));
+        CK(cudaStreamSynchronize(b.stream));
+        collect_profile(b, chunk);
+        if (b.h_g->error) {
+            CK(cudaMemcpyAsync(b.h_state.data(), b.d_state, sizeof(SimState) * b.n_sims, cudaMemcpyDeviceToHost,
+                               b.stream));
+            CK(cudaStreamSynchronize(b.stream));
+            collect_stats(b, 0);
+            return IND_ERR_DEVICE;
+        }
+        if (b.h_g->n_total == 0) break;
+    }
+    if (result == IND_OK) {
+        ind_status st = batch_finish(b);
+        if (st != IND_OK) return st;
+        b.finished = true;
+    } else {
+        CK(cudaMemcpyAsync(b.h_state.data(), b.d_state, sizeof(SimState) * b.n_sims, cudaMemcpyDeviceToHost,
+                           b.stream));
+        CK(cudaStreamSynchronize(b.stream));
+    }
+    collect_stats(b, 0);
+    auto t1 = std::chrono::steady_clock::now();
+    b.ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    for (auto* m : b.sims) {
+        m->stats.ms_total = b.ms;
+        m->stats.advance_ms = b.advance_ms;
+        m->stats.advance_launches = b.advance_launches;
+    }
+    return result;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* ind_status_string(ind_status s) {
+    switch (s) {
+        case IND_OK: return "IND_OK";
+        case IND_ERR_ARG: return "IND_ERR_ARG";
+        case IND_ERR_OOM: return "IND_ERR_OOM";
+        case IND_ERR_CUDA: return "IND_ERR_CUDA";
+        case IND_ERR_BUDGET: return "IND_ERR_BUDGET";
+        case IND_ERR_STATE: return "IND_ERR_STATE";
+        case IND_ERR_DEVICE: return "IND_ERR_DEVICE";
+    }
+    return "IND_UNKNOWN";
+}
+
+int ind_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+uint64_t ind_kernel_launches(void) { return g_launches.load(); }
+
+ind_status ind_set_allocator(const ind_allocator* a) {
+    if (a && (!a->alloc || !a->release)) return IND_ERR_ARG;
+    if (a) g_alloc = *a;
+    else g_alloc = ind_allocator{nullptr, nullptr, nullptr};
+    return IND_OK;
+}
+
+void ind_default_tuning(ind_tuning* t) {
+    if (!t) return;
+    memset(t, 0, sizeof(*t));
+    t->block_threads = 256;
+    t->blocks_per_sm = 8;
+    t->lineages_per_lane = 4;
+    t->rounds_per_check = 16;
+    t->use_graph = 1;
+    t->dedup = 1;
+    t->count_unique = 0;
+    t->profile = 0;
+    t->events_per_round = 4194304.0;
+    t->min_events_per_lineage = 0.25;
+    t->occupancy_step = 0.25;
+    t->tail_events = 128.0;
+    t->busy_lineages = 32768.0;
+}
+
+static bool tuning_ok(const ind_tuning* t) {
+    return t->block_threads >= 64 && t->block_threads <= 512 && t->block_threads % 32 == 0 &&
+           t->blocks_per_sm >= 1 && t->blocks_per_sm <= 32 && t->lineages_per_lane >= 1 &&
+           t->lineages_per_lane <= 64 && t->rounds_per_check >= 1 && t->rounds_per_check <= 4096 &&
+           t->events_per_round >= 1.0 && t->min_events_per_lineage > 0.0 && t->occupancy_step > 0.0 &&
+           t->tail_events > 0.0 && t->busy_lineages >= 0.0 && std::isfinite(t->tail_events) &&
+           std::isfinite(t->busy_lineages) &&
+           std::isfinite(t->events_per_round) && std::isfinite(t->min_events_per_lineage) &&
+           std::isfinite(t->occupancy_step);
+}
+
+static int pow2_log2(double v, bool* ok) {
+    int e = 0;
+    double m = std::frexp(v, &e);
+    *ok = (m == 0.5) && e - 1 >= -20 && e - 1 <= 20;
+    return e - 1;
+}
+
+static ind_status validate(const ind_landscape* L, const ind_dispersal* D, double nu, int* dt_log2) {
+    if (!L || !D) return IND_ERR_ARG;
+    if (!(nu > 0.0 && nu <= 1.0)) return IND_ERR_ARG;
+    if (!(L->lambda > 0.0) || !std::isfinite(L->lambda)) return IND_ERR_ARG;
+    bool ok = false;
+    *dt_log2 = pow2_log2(L->delta_t, &ok);
+    if (!ok || !(L->delta_t > 0.0)) return IND_ERR_ARG;
+    if (!(L->lambda * L->delta_t >= 0x1p-20)) return IND_ERR_ARG;  // bounded interval search
+    if (L->width < 1 || L->height < 1 || L->width > (1u << 20) || L->height > (1u << 20)) return IND_ERR_ARG;
+    if (L->kind == IND_NONSPATIAL) {
+        if (L->width != 1 || L->height != 1 || L->deme < 1 || L->deme >= (1u << 23)) return IND_ERR_ARG;
+        if (D->kind != IND_DISPERSAL_UNIFORM) return IND_ERR_ARG;
+    } else if (L->kind == IND_TORUS) {
+        if (L->deme < 1 || L->deme >= (1u << 23)) return IND_ERR_ARG;
+        if (D->kind != IND_DISPERSAL_GAUSSIAN) return IND_ERR_ARG;
+        if (!(D->sigma > 0.0 && D->sigma <= 64.0)) return IND_ERR_ARG;
+    } else if (L->kind == IND_MAP) {
+        if (!L->deme_map) return IND_ERR_ARG;
+        if (D->kind != IND_DISPERSAL_ALIAS_GAUSSIAN) return IND_ERR_ARG;
+        if (!(D->sigma > 0.0 && D->sigma <= 64.0) || D->radius < 1 || D->radius > 40) return IND_ERR_ARG;
+    } else {
+        return IND_ERR_ARG;
+    }
+    const uint64_t dmax = L->kind == IND_MAP ? 255u : L->deme;
+    if ((uint64_t)L->width * L->height * dmax > (1ull << 32) - 1) return IND_ERR_ARG;
+    return IND_OK;
+}
+
+ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu, uint64_t seed, void* cuda_stream,
+                      ind_sim** out) {
+    if (!out) return IND_ERR_ARG;
+    *out = nullptr;
+    int dt_log2 = 0;
+    ind_status st = validate(L, D, nu, &dt_log2);
+    if (st != IND_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    st = ensure_ln_tables(s);
+    if (st != IND_OK) return st;
+    ind_sim* m = new (std::nothrow) ind_sim();
+    if (!m) return IND_ERR_OOM;
+    m->land = *L;
+    m->land.deme_map = nullptr;
+    m->disp = *D;
+    m->nu = nu;
+    m->seed = seed;
+    m->stream = s;
+    m->tables.stream = m->sample.stream = m->results.stream = s;
+    ind_default_tuning(&m->tuning);
+    m->dt_log2 = dt_log2;
+    seed_key(seed, &m->sk0, &m->sk1);
+    m->nu_thr = (uint64_t)std::ceil(nu * 0x1p53);
+    m->slot_deme = L->kind == IND_MAP ? 0 : L->deme;
+    m->n_slots = (uint64_t)L->width * L->height * L->deme;
+    auto fail = [&](ind_status e) {
+        m->tables.release_all();
+        delete m;
+        return e;
+    };
+    if (L->kind == IND_TORUS) {
+        std::vector<uint64_t> cdf = host_gauss_cdf(D->sigma);
+        m->gauss_half = host_gauss_half(D->sigma);
+        m->gauss_n = (uint32_t)cdf.size();
+        m->d_gauss = m->tables.get<uint64_t>(cdf.size());
+        if (!m->d_gauss) return fail(IND_ERR_OOM);
+        if (cudaMemcpyAsync(m->d_gauss, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+    }
+    if (L->kind == IND_MAP) {
+        const size_t ncell = (size_t)L->width * L->height;
+        std::vector<uint8_t> dm(ncell);
+        if (cudaMemcpy(dm.data(), L->deme_map, ncell, cudaMemcpyDefault) != cudaSuccess) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+        uint32_t maxd = 0;
+        m->n_slots = 0;
+        std::vector<uint32_t> cells, row_of(ncell, 0xFFFFFFFFu);
+        for (size_t c = 0; c < ncell; ++c) {
+            maxd = std::max<uint32_t>(maxd, dm[c]);
+            m->n_slots += dm[c];
+            if (dm[c]) {
+                row_of[c] = (uint32_t)cells.size();
+                cells.push_back((uint32_t)c);
+            }
+        }
+        if (cells.empty()) return fail(IND_ERR_ARG);
+        m->slot_deme = maxd;
+        const int R = (int)D->radius;
+        std::vector<int8_t> off;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx)
+                if (dx * dx + dy * dy <= R * R) {
+                    off.push_back((int8_t)dx);
+                    off.push_back((int8_t)dy);
+                }
+        m->n_off = (uint32_t)(off.size() / 2);
+        m->n_rows = (uint32_t)cells.size();
+        std::vector<uint64_t> kw = host_kernel_weights(D->sigma, R);
+        m->d_deme = m->tables.get<uint8_t>(ncell);
+        m->d_row_of = m->tables.get<uint32_t>(ncell);
+        m->d_off = m->tables.get<int8_t>(off.size());
+        uint64_t* d_kw = m->tables.get<uint64_t>(kw.size());
+        uint32_t* d_cells = m->tables.get<uint32_t>(cells.size());
+        m->d_alias = m->tables.get<uint64_t>((size_t)m->n_rows * m->n_off);
+        if (!m->d_deme || !m->d_row_of || !m->d_off || !d_kw || !d_cells || !m->d_alias) return fail(IND_ERR_OOM);
+        bool okc = cudaMemcpyAsync(m->d_deme, dm.data(), ncell, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                   cudaMemcpyAsync(m->d_row_of, row_of.data(), ncell * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                   cudaMemcpyAsync(m->d_off, off.data(), off.size(), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                   cudaMemcpyAsync(d_kw, kw.data(), kw.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+                   cudaMemcpyAsync(d_cells, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+        if (!okc) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+        const size_t per_warp = ((size_t)m->n_off * 12 + 15) & ~(size_t)15;
+        int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
+        const size_t shb = per_warp * warps;
+        if (cudaFuncSetAttribute(k_alias_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb) != cudaSuccess) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+        const uint32_t blocks = std::min<uint32_t>((m->n_rows + warps - 1) / warps, sm_count() * 8);
+        k_alias_build<<<blocks, 32 * warps, shb, s>>>(m->d_deme, L->width, L->height, d_cells, m->n_rows, m->d_off,
+                                                      m->n_off, d_kw, m->d_alias);
+        g_launches.fetch_add(1);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+    }
+    *out = m;
+    return IND_OK;
+}
+
+ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_t* n_sampled) {
+    if (!m || !(fraction > 0.0 && fraction <= 1.0)) return IND_ERR_ARG;
+    if (m->batch) {
+        delete m->batch;
+        m->batch = nullptr;
+    }
+    m->sample.release_all();
+    m->results.release_all();
+    m->d_species = m->d_key_loc = m->d_key_time = nullptr;
+    m->finished = false;
+    m->sampled = false;
+    m->stats = ind_run_stats{};
+    cudaStream_t s = m->stream;
+    const uint64_t n_slots = (uint64_t)m->land.width * m->land.height * m->slot_deme;
+    Pool tmp;
+    tmp.stream = s;
+    uint32_t* flags = tmp.get<uint32_t>(n_slots);
+    uint32_t* pos = tmp.get<uint32_t>(n_slots);
+    if (!flags || !pos) {
+        tmp.release_all();
+        return IND_ERR_OOM;
+    }
+    uint32_t sk0, sk1;
+    seed_key(sample_seed, &sk0, &sk1);
+    const uint64_t thr = (uint64_t)std::ceil(fraction * 0x1p53);
+    const uint32_t sms = sm_count();
+    k_sample_flags<<<grid_for(n_slots, 256, sms * 32), 256, 0, s>>>(flags, n_slots, m->land.kind, m->land.width,
+                                                                   m->land.deme, m->slot_deme, m->d_deme,
+                                                                   fraction >= 1.0 ? 1 : 0, sk0, sk1, thr);
+    g_launches.fetch_add(1);
+    ind_status st = scan_u32(tmp, flags, pos, (uint32_t)n_slots, false, s);
+    if (st != IND_OK) {
+        tmp.release_all();
+        return st;
+    }
+    uint32_t last_pos = 0, last_flag = 0;
+    if (cudaMemcpyAsync(&last_pos, pos + n_slots - 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&last_flag, flags + n_slots - 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        g_last_cuda_error.store((int)cudaGetLastError());
+        tmp.release_all();
+        return IND_ERR_CUDA;
+    }
+    const uint64_t count = (uint64_t)last_pos + last_flag;
+    m->d_sample = m->sample.get<uint64_t>(std::max<uint64_t>(count, 1));
+    if (!m->d_sample) {
+        tmp.release_all();
+        return IND_ERR_OOM;
+    }
+    k_sample_write<<<grid_for(n_slots, 256, sms * 32), 256, 0, s>>>(flags, pos, n_slots, m->land.width,
+                                                                   m->slot_deme, m->d_sample);
+    g_launches.fetch_add(1);
+    tmp.release_all();
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        g_last_cuda_error.store((int)cudaGetLastError());
+        return IND_ERR_CUDA;
+    }
+    m->n_sampled = count;
+    m->sampled = true;
+    m->stats.n_sampled = count;
+    if (n_sampled) *n_sampled = count;
+    return IND_OK;
+}
+
+ind_status sim_set_tuning(ind_sim* m, const ind_tuning* t) {
+    if (!m) return IND_ERR_ARG;
+    if (!t) {
+        ind_default_tuning(&m->tuning);
+        return IND_OK;
+    }
+    if (!tuning_ok(t)) return IND_ERR_ARG;
+    m->tuning = *t;
+    return IND_OK;
+}
+
+ind_status sim_stats(const ind_sim* m, ind_run_stats* out) {
+    if (!m || !out) return IND_ERR_ARG;
+    *out = m->stats;
+    return IND_OK;
+}
+
+ind_status sim_run(ind_sim* m, uint64_t round_budget, ind_run_stats* out) {
+    if (!m) return IND_ERR_ARG;
+    if (!m->sampled) return IND_ERR_STATE;
+    if (m->finished) {
+        if (out) *out = m->stats;
+        return IND_OK;
+    }
+    if (!m->batch) {
+        Batch* b = new (std::nothrow) Batch();
+        if (!b) return IND_ERR_OOM;
+        b->sims.push_back(m);
+        b->stream = m->stream;
+        b->tun = m->tuning;
+        ind_status st = batch_build(*b);
+        if (st != IND_OK) {
+            delete b;
+            return st;
+        }
+        m->batch = b;
+    }
+    ind_status st = batch_run(*m->batch, round_budget);
+    if (out) *out = m->stats;
+    if (st == IND_OK) {
+        delete m->batch;
+        m->batch = nullptr;
+    }
+    return st;
+}
+
+ind_status sim_batch_run(ind_sim** sims, uint32_t n, const ind_tuning* tuning, ind_run_stats* per_sim) {
+    if (!sims || n == 0) return IND_ERR_ARG;
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!sims[i]) return IND_ERR_ARG;
+        if (!sims[i]->sampled || sims[i]->finished || sims[i]->batch) return IND_ERR_STATE;
+        for (uint32_t j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return IND_ERR_ARG;
+    }
+    if (tuning && !tuning_ok(tuning)) return IND_ERR_ARG;
+    Batch b;
+    b.sims.assign(sims, sims + n);
+    b.stream = sims[0]->stream;
+    b.tun = tuning ? *tuning : sims[0]->tuning;
+    // other streams' work (sampling) must be complete
+    for (uint32_t i = 1; i < n; ++i)
+        if (sims[i]->stream != b.stream) CK(cudaStreamSynchronize(sims[i]->stream));
+    ind_status st = batch_build(b);
+    if (st == IND_OK) st = batch_run(b, 0);
+    if (per_sim)
+        for (uint32_t i = 0; i < n; ++i) per_sim[i] = sims[i]->stats;
+    return st;
+}
+
+ind_status sim_species(ind_sim* m, uint64_t* species_out, uint64_t* n_species_out) {
+    if (!m) return IND_ERR_ARG;
+    if (!m->finished) return IND_ERR_STATE;
+    if (species_out && m->n_sampled) {
+        CK(cudaMemcpyAsync(species_out, m->d_species, m->n_sampled * 8, cudaMemcpyDefault, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    if (n_species_out) *n_species_out = m->n_species;
+    return IND_OK;
+}
+
+ind_status sim_species_keys(ind_sim* m, uint64_t* key_loc, uint64_t* key_time) {
+    if (!m) return IND_ERR_ARG;
+    if (!m->finished) return IND_ERR_STATE;
+    if (m->n_sampled) {
+        if (key_loc) CK(cudaMemcpyAsync(key_loc, m->d_key_loc, m->n_sampled * 8, cudaMemcpyDefault, m->stream));
+        if (key_time) CK(cudaMemcpyAsync(key_time, m->d_key_time, m->n_sampled * 8, cudaMemcpyDefault, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    return IND_OK;
+}
+
+size_t sim_mem_estimate(const ind_landscape* L, const ind_dispersal* D, double fraction) {
+    int dtl = 0;
+    if (validate(L, D, 0.5, &dtl) != IND_OK || !(fraction > 0.0 && fraction <= 1.0)) return 0;
+    const uint64_t ncell = (uint64_t)L->width * L->height;
+    double individuals;
+    size_t tables = 0;
+    if (L->kind == IND_MAP) {
+        // without reading the map: the largest possible deme everywhere
+        individuals = (double)ncell * 255.0;
+        uint64_t n_off = 0;
+        const int R = (int)D->radius;
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx)
+                if (dx * dx + dy * dy <= R * R) ++n_off;
+        tables = ncell * (1 + 4 + 4 + n_off * 8) + 2 * n_off + 8 * (size_t)(R * R + 1);
+    } else {
+        individuals = (double)ncell * L->deme;
+        if (L->kind == IND_TORUS) tables = 16 * (size_t)host_gauss_half(D->sigma);
+    }
+    const double sampled = std::ceil(individuals * fraction * 1.02) + 64;
+    // sampling scratch (8 B per slot) is freed before the run
+    const double slots = (L->kind == IND_MAP ? (double)ncell * 255.0 : individuals);
+    // per lineage: 2 x 24 (buffers) + 20 (parent, keys) + 24 (outputs) + 8 (sample)
+    // + 2 x 4 x 12 (dedup tables of twice the size) + 8 (used lists) + 32 x 2 (species sort)
+    const double per = 48 + 20 + 24 + 8 + 96 + 8 + 64 + 16;
+    const double bytes = tables + std::max(sampled * per, slots * 8.0) + (1 << 20);
+    return (size_t)bytes;
+}
+
+void sim_destroy(ind_sim* m) {
+    if (!m) return;
+    if (m->batch) delete m->batch;
+    m->results.release_all();
+    m->sample.release_all();
+    m->tables.release_all();
+    delete m;
+}
+
+ind_status ind_habitat(uint64_t map_seed, uint32_t width, uint32_t height, double p_habitable, uint32_t max_deme,
+                       uint8_t* deme_out, void* cuda_stream) {
+    if (!deme_out || width < 1 || height < 1 || width > (1u << 20) || height > (1u << 20)) return IND_ERR_ARG;
+    if (!(p_habitable >= 0.0 && p_habitable <= 1.0) || max_deme < 1 || max_deme > 255) return IND_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t sk0, sk1;
+    seed_key(map_seed, &sk0, &sk1);
+    const uint64_t thr = (uint64_t)std::ceil(p_habitable * 0x1p53);
+    const uint64_t n = (uint64_t)width * height;
+    cudaPointerAttributes attr{};
+    bool on_device = cudaPointerGetAttributes(&attr, deme_out) == cudaSuccess && attr.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    uint8_t* dst = deme_out;
+    Pool tmp;
+    tmp.stream = s;
+    if (!on_device) {
+        dst = tmp.get<uint8_t>(n);
+        if (!dst) return IND_ERR_OOM;
+    }
+    k_habitat<<<grid_for(n, 256, sm_count() * 32), 256, 0, s>>>(dst, width, height, sk0, sk1, thr, max_deme);
+    g_launches.fetch_add(1);
+    if (cudaGetLastError() != cudaSuccess) {
+        tmp.release_all();
+        return IND_ERR_CUDA;
+    }
+    if (!on_device) {
+        if (cudaMemcpyAsync(deme_out, dst, n, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            tmp.release_all();
+            return IND_ERR_CUDA;
+        }
+    }
+    tmp.release_all();
+    CK(cudaStreamSynchronize(s));
+    return IND_OK;
+}
+
+ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, uint32_t* philox_out,
+                        void* cuda_stream) {
+    if (!in || n == 0 || n > (1ull << 30)) return IND_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    ind_status st = ensure_ln_tables(s);
+    if (st != IND_OK) return st;
+    Pool tmp;
+    tmp.stream = s;
+    uint64_t* d_in = tmp.get<uint64_t>(n);
+    uint64_t* d_exp = exp_q58_out ? tmp.get<uint64_t>(n) : nullptr;
+    uint32_t* d_ph = philox_out ? tmp.get<uint32_t>(4 * n) : nullptr;
+    if (!d_in || (exp_q58_out && !d_exp) || (philox_out && !d_ph)) {
+        tmp.release_all();
+        return IND_ERR_OOM;
+    }
+    bool ok = cudaMemcpyAsync(d_in, in, n * 8, cudaMemcpyDefault, s) == cudaSuccess;
+    if (ok) {
+        k_selftest<<<grid_for(n, 256, sm_count() * 16), 256, 0, s>>>(d_in, n, d_exp, d_ph);
+        g_launches.fetch_add(1);
+        ok = cudaGetLastError() == cudaSuccess;
+    }
+    if (ok && exp_q58_out) ok = cudaMemcpyAsync(exp_q58_out, d_exp, n * 8, cudaMemcpyDefault, s) == cudaSuccess;
+    if (ok && philox_out) ok = cudaMemcpyAsync(philox_out, d_ph, n * 16, cudaMemcpyDefault, s) == cudaSuccess;
+    tmp.release_all();
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+        g_last_cuda_error.store((int)cudaGetLastError());
+        return IND_ERR_CUDA;
+    }
+    return IND_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,67 @@
+// tables.cpp -- host-side integer tables of the library, computed in binary128
+// (libquadmath).  They are roundings of real-valued definitions:
+//   ln tables   L_j = round(2^62 ln(2^16 / R_j)), R_j = round(2^25/(513+2j)),
+//               ln2 = round(2^64 ln 2), c_k = round(2^62 / k)  (inverse
+//               transform -ln U of the appendix "Inverse Transform: Uniform
+//               and Exponential")
+//   Gaussian    C_k = round(2^64 Phi((k - half + 1/2) / sigma)), clamped to
+//               [0, 2^64 - 1], half = ceil(10 sigma) in binary64: the
+//               per-axis discretised normal of section "Normal Dispersal"
+//   kernel      K[d2] = round(2^32 exp(-d2 / (2 sigma^2))): Gaussian weights
+//               of the habitat-map dispersal
+// binary128 carries about 113 bits, far more than the 64 needed, so ties of
+// the rounding cannot flip (the tables' distance to the rounding boundary is
+// asserted in the test suite).
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+extern "C" {
+#include <quadmath.h>
+}
+
+namespace indep {
+
+static uint64_t round_q(__float128 x) {
+    __float128 f = floorq(x + (__float128)0.5);
+    if (f <= 0) return 0;
+    if (f >= ldexpq((__float128)1, 64) - 1) return ~0ull;
+    return (uint64_t)f;
+}
+
+void host_ln_tables(uint64_t L[256], uint32_t R[256], uint64_t* ln2_q64, int64_t c[7]) {
+    for (uint32_t j = 0; j < 256; ++j) {
+        uint64_t d = 513u + 2u * (uint64_t)j;
+        R[j] = (uint32_t)(((1ull << 26) + d) / (2u * d));
+        __float128 v = logq((__float128)65536 / (__float128)R[j]);
+        L[j] = round_q(ldexpq(v, 62));
+    }
+    *ln2_q64 = round_q(ldexpq(logq((__float128)2), 64));
+    c[0] = 0;
+    for (int k = 1; k <= 6; ++k) c[k] = (int64_t)(((1ull << 63) + (uint64_t)k) / (2ull * (uint64_t)k));
+}
+
+int host_gauss_half(double sigma) { return (int)std::ceil(10.0 * sigma); }
+
+std::vector<uint64_t> host_gauss_cdf(double sigma) {
+    int half = host_gauss_half(sigma);
+    std::vector<uint64_t> out(2 * (size_t)half);
+    __float128 s = (__float128)sigma;
+    __float128 rt2 = sqrtq((__float128)2);
+    for (int k = 0; k < 2 * half; ++k) {
+        __float128 z = ((__float128)(k - half) + (__float128)0.5) / s;
+        __float128 phi = erfcq(-z / rt2) / 2;
+        out[k] = round_q(ldexpq(phi, 64));
+    }
+    return out;
+}
+
+std::vector<uint64_t> host_kernel_weights(double sigma, int radius) {
+    std::vector<uint64_t> out((size_t)radius * radius + 1);
+    __float128 s = (__float128)sigma;
+    for (int d2 = 0; d2 <= radius * radius; ++d2)
+        out[d2] = round_q(ldexpq(expq(-(__float128)d2 / (2 * s * s)), 32));
+    return out;
+}
+
+}  // namespace indep

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle.
+
+Every comparison is bit-exact: speciation keys (location, IEEE bits of the
+time), dense species identities and species counts are integers, so the
+tolerance is zero.  Inputs are seeded and synthetic (see workloads.py).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2108_05815_b300 as ind
+from paper_2108_05815_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2108_05815_b300 import build
+    build.build()
+    yield
+
+
+def gpu_sim(cfg, deme_map=None, tuning=None):
+    kw = dict(width=cfg.get("width", 1), height=cfg.get("height", 1), deme=cfg.get("deme", 1),
+              sigma=cfg.get("sigma", 0.0), radius=cfg.get("radius", 0), lam=cfg.get("lam", 1.0),
+              delta_t=cfg.get("delta_t", 1.0), tuning=tuning)
+    if cfg["kind"] == W.MAP:
+        kw["deme_map"] = deme_map
+    return ind.Simulation(cfg["kind"], cfg["nu"], cfg["seed"], **kw)
+
+
+def oracle_model(cfg, deme_map=None):
+    return O.Model(cfg["kind"], cfg.get("width", 1), cfg.get("height", 1), cfg.get("deme", 1), cfg["nu"],
+                   cfg["seed"], lam=cfg.get("lam", 1.0), delta_t=cfg.get("delta_t", 1.0),
+                   sigma=cfg.get("sigma"), radius=cfg.get("radius"), deme_map=deme_map)
+
+
+def run_gpu(cfg, deme_map=None, tuning=None, fraction=1.0, sample_seed=0):
+    s = gpu_sim(cfg, deme_map, tuning)
+    n = s.sample(fraction, sample_seed)
+    assert s.run()
+    ids, K = s.species()
+    kl, kt = s.species_keys()
+    st = s.stats()
+    s.close()
+    return dict(n=n, ids=ids, K=K, kl=kl, kt=kt, stats=st)
+
+
+def run_oracle(cfg, deme_map=None, fraction=1.0, sample_seed=0):
+    m = oracle_model(cfg, deme_map)
+    locs = m.sample(fraction, sample_seed)
+    kl, kt, U = m.run_merge(locs)
+    ids, K = O.species_ids(kl, kt)
+    return dict(n=len(locs), ids=ids, K=K, kl=kl, kt=kt, U=U, locs=locs, model=m)
+
+
+def assert_same(g, o):
+    assert g["n"] == o["n"]
+    assert np.array_equal(g["kl"], o["kl"])
+    assert np.array_equal(g["kt"], o["kt"])
+    assert g["K"] == o["K"]
+    assert np.array_equal(g["ids"], o["ids"])
+
+
+# --------------------------------------------------------------------------
+# device arithmetic, bit for bit
+# --------------------------------------------------------------------------
+def test_device_exp_and_philox_bitexact():
+    rng = np.random.default_rng(123)
+    v = rng.integers(0, np.iinfo(np.int64).max, size=200000, dtype=np.int64).astype(np.uint64)
+    v[:54] = [(np.uint64(1) << np.uint64(k)) << np.uint64(11) for k in range(54)]
+    v[54] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    v[55] = np.uint64(0)
+    e, p = ind.selftest(v)
+    for i in range(0, len(v), 97):
+        assert int(e[i]) == O.exp1_q58(int(v[i]) >> 11), i
+    for i in range(0, len(v), 211):
+        w, z = int(v[(i + 1) % len(v)]), int(v[(i + 2) % len(v)])
+        key = [int(v[i]) & 0xFFFFFFFF, int(v[i]) >> 32]
+        ctr = [w & 0xFFFFFFFF, w >> 32, z & 0xFFFFFFFF, z >> 32]
+        assert O.philox4x32_10(key, ctr) == [int(x) for x in p[i]]
+
+
+def test_device_habitat_matches_oracle():
+    for (seed, Wd, Hd, p, md) in [(7, 300, 200, 0.6, 8), (3, 64, 1, 0.25, 3), (11, 1, 1, 1.0, 255)]:
+        g = ind.habitat(seed, Wd, Hd, p, md)
+        o = O.habitat(seed, Wd, Hd, p, md)
+        assert np.array_equal(g, o)
+
+
+# --------------------------------------------------------------------------
+# whole simulations: full parity on small and mid-size workloads
+# --------------------------------------------------------------------------
+def test_config1_nonspatial_full_parity():
+    cfg = W.config1()
+    o = run_oracle(cfg)
+    g = run_gpu(cfg)
+    assert_same(g, o)
+    assert g["stats"]["raw_events"] >= o["U"]
+    assert g["stats"]["n_sampled"] == 10000
+
+
+def test_config2_torus_full_parity():
+    cfg = W.config2()
+    o = run_oracle(cfg)
+    g = run_gpu(cfg)
+    assert_same(g, o)
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(kind=W.TORUS, width=64, height=48, deme=2, sigma=1.5, nu=1e-3, seed=5),
+    dict(kind=W.TORUS, width=37, height=23, deme=3, sigma=6.3, nu=3e-3, seed=6),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=777, nu=2e-2, seed=9),
+])
+def test_small_models_full_parity(cfg):
+    assert_same(run_gpu(cfg), run_oracle(cfg))
+
+
+@pytest.mark.parametrize("side,nu,sigma,radius", [(96, 1e-2, 4.0, 16), (50, 3e-3, 2.5, 7), (40, 5e-2, 9.0, 20)])
+def test_map_full_parity(side, nu, sigma, radius):
+    dm = O.habitat(13, side, side)
+    cfg = dict(kind=W.MAP, width=side, height=side, sigma=sigma, radius=radius, nu=nu, seed=17)
+    assert_same(run_gpu(cfg, deme_map=dm), run_oracle(cfg, deme_map=dm))
+
+
+def test_sampled_fraction_parity():
+    cfg = dict(kind=W.TORUS, width=80, height=60, deme=4, sigma=2.0, nu=2e-3, seed=21)
+    o = run_oracle(cfg, fraction=0.3, sample_seed=77)
+    g = run_gpu(cfg, fraction=0.3, sample_seed=77)
+    assert_same(g, o)
+    dm = O.habitat(4, 70, 50)
+    cfgm = dict(kind=W.MAP, width=70, height=50, sigma=3.0, radius=10, nu=4e-3, seed=22)
+    assert_same(run_gpu(cfgm, dm, fraction=0.45, sample_seed=5), run_oracle(cfgm, dm, fraction=0.45, sample_seed=5))
+
+
+# --------------------------------------------------------------------------
+# unique-event counting is exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [W.config1(),
+                                 dict(kind=W.TORUS, width=64, height=64, deme=1, sigma=2.0, nu=1e-3, seed=3)])
+def test_unique_event_count_matches_oracle(cfg):
+    o = run_oracle(cfg)
+    g = run_gpu(cfg, tuning=dict(count_unique=1))
+    assert_same(g, o)
+    assert g["stats"]["unique_events"] == o["U"]
+
+
+# --------------------------------------------------------------------------
+# invariants: tuning, dedup, graphs, batching, resumption
+# --------------------------------------------------------------------------
+TUNINGS = [
+    dict(dedup=0),
+    dict(use_graph=0, rounds_per_check=3),
+    dict(block_threads=64, blocks_per_sm=1, lineages_per_lane=1),
+    dict(block_threads=512, blocks_per_sm=2, lineages_per_lane=16),
+    dict(events_per_round=500.0, min_events_per_lineage=0.5, tail_events=0.5, occupancy_step=0.05),
+    dict(events_per_round=1e9, min_events_per_lineage=1e6),
+]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
+def test_results_do_not_depend_on_tuning(tuning):
+    cfg = dict(kind=W.TORUS, width=48, height=40, deme=2, sigma=2.0, nu=2e-3, seed=31)
+    ref = run_gpu(cfg)
+    assert_same(run_gpu(cfg, tuning=tuning), ref)
+
+
+def test_round_budget_resumes():
+    cfg = dict(kind=W.TORUS, width=48, height=48, deme=1, sigma=2.0, nu=1e-3, seed=8)
+    ref = run_gpu(cfg)
+    s = gpu_sim(cfg, tuning=dict(events_per_round=2000.0, min_events_per_lineage=1.0, tail_events=1.0,
+                                  rounds_per_check=2))
+    s.sample()
+    calls = 0
+    while not s.run(round_budget=3):
+        calls += 1
+        assert calls < 100000
+    assert calls > 1
+    ids, K = s.species()
+    kl, kt = s.species_keys()
+    assert np.array_equal(kl, ref["kl"]) and np.array_equal(kt, ref["kt"]) and K == ref["K"]
+    s.close()
+
+
+def test_batch_equals_alone():
+    dm = O.habitat(2, 60, 60)
+    cfgs = [W.config1(),
+            dict(kind=W.TORUS, width=100, height=90, deme=1, sigma=3.0, nu=1e-3, seed=4),
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=3, nu=0.5, seed=5),
+            dict(kind=W.MAP, width=60, height=60, sigma=4.0, radius=16, nu=1e-2, seed=6),
+            dict(kind=W.TORUS, width=20, height=20, deme=4, sigma=1.0, nu=1e-1, seed=7),
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=1, nu=1e-4, seed=8)]
+    alone = [run_gpu(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
+    sims = [gpu_sim(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
+    for s in sims:
+        s.sample()
+    stats = ind.batch_run(sims)
+    for s, a, st in zip(sims, alone, stats):
+        ids, K = s.species()
+        kl, kt = s.species_keys()
+        assert np.array_equal(kl, a["kl"]) and np.array_equal(kt, a["kt"])
+        assert K == a["K"] and np.array_equal(ids, a["ids"])
+        assert st["raw_events"] == a["stats"]["raw_events"]
+        s.close()
+
+
+# --------------------------------------------------------------------------
+# edge and degenerate cases
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=500, nu=1.0, seed=1),      # nu = 1: K = n
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=1, nu=1e-3, seed=2),       # J = 1: K = 1
+    dict(kind=W.TORUS, width=1, height=1, deme=1, sigma=3.0, nu=1e-2, seed=3), # a single cell
+    dict(kind=W.TORUS, width=31, height=17, deme=1, sigma=1e-3, nu=0.05, seed=4),  # no movement: K = n
+    dict(kind=W.TORUS, width=40, height=30, deme=2, sigma=2.0, nu=3e-3, seed=5, lam=2.5, delta_t=0.5),
+    dict(kind=W.TORUS, width=40, height=30, deme=2, sigma=2.0, nu=3e-3, seed=6, lam=0.3, delta_t=4.0),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=2000, nu=1e-2, seed=7, lam=7.0, delta_t=0.125),
+])
+def test_edge_cases_parity(cfg):
+    o = run_oracle(cfg)
+    g = run_gpu(cfg)
+    assert_same(g, o)
+    if cfg["nu"] == 1.0 or cfg.get("sigma") == 1e-3:
+        assert g["K"] == g["n"]
+    if cfg.get("deme") == 1 and cfg["kind"] == W.NONSPATIAL:
+        assert g["K"] == 1
+
+
+# --------------------------------------------------------------------------
+# full-size habitat map (config 3): sampled individuals + properties
+# --------------------------------------------------------------------------
+def test_config3_full_size_sampled_parity():
+    cfg = W.config3()
+    dm = ind.habitat(cfg["map_seed"], cfg["width"], cfg["height"], cfg["p_habitable"], cfg["max_deme"])
+    assert np.array_equal(dm, O.habitat(cfg["map_seed"], cfg["width"], cfg["height"], cfg["p_habitable"],
+                                        cfg["max_deme"]))
+    g = run_gpu(cfg, deme_map=dm)
+    assert g["n"] == int(dm.astype(np.int64).sum())
+    # properties that hold at any size
+    keys = list(zip(g["kl"].tolist(), g["kt"].tolist()))
+    distinct = sorted(set(keys))
+    assert g["K"] == len(distinct)
+    rank = {k: r for r, k in enumerate(distinct)}
+    sub = np.arange(0, g["n"], 9973)
+    assert all(g["ids"][i] == rank[keys[i]] for i in sub)
+    # sampled individuals traced one by one by the oracle (mode P)
+    m = oracle_model(cfg, dm)
+    locs = m.sample()
+    pick = np.random.default_rng(0).choice(g["n"], size=6, replace=False)
+    kl, kt, _ = m.trace(locs[pick])
+    assert np.array_equal(kl, g["kl"][pick]) and np.array_equal(kt, g["kt"][pick])
