@@ -222,6 +222,29 @@ ind_status ind_habitat(uint64_t map_seed, uint32_t width, uint32_t height, doubl
 ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, uint32_t* philox_out,
                         void* cuda_stream);
 
+/* Species ranking that allocates nothing (the paper has no counterpart: it
+ * exists for callers that must not allocate device memory while they run,
+ * e.g. a process that plans all of its device memory at start-up, or code
+ * running inside an allocator of its own that it cannot re-enter).
+ * Computes, for n individuals with speciation keys (key_loc[i],
+ * key_time[i]), the dense species identity of each (rank of its key among
+ * the distinct keys in ascending (location, time bits) order) into
+ * species_out[i] and the number of distinct keys into *n_species_out: the
+ * same values sim_species gives for those keys.
+ *  - key_loc, key_time, species_out: device-accessible pointers of n entries;
+ *    n_species_out: host or device pointer (may be NULL).
+ *  - n <= 65536; larger n returns IND_ERR_ARG without doing anything.
+ *  - Its scratch is one fixed device array of about 2.5 MiB that every GPU
+ *    loading this library holds until the process exits; no cudaMalloc,
+ *    cudaFree or allocating library routine is called.
+ *  - The first call on a device looks up that array's device address (with
+ *    the device current); make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents: calls
+ *    whose work overlaps on the GPU race and give wrong results.
+ *  - Work runs on cuda_stream; returns after it ends if n_species_out is set. */
+ind_status ind_species_rank_static(const uint64_t* key_loc, const uint64_t* key_time, uint64_t n,
+                                   uint64_t* species_out, uint64_t* n_species_out, void* cuda_stream);
+
 /* Human-readable status name; never NULL. */
 const char* ind_status_string(ind_status status);
 

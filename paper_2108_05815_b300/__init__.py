@@ -92,6 +92,8 @@ EXPORTS = {
                                    ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "ind_selftest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    "ind_species_rank_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p]),
     "ind_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ind_last_cuda_error": (ctypes.c_int, []),
     "ind_kernel_launches": (ctypes.c_uint64, []),
@@ -302,6 +304,16 @@ def selftest(values, want_exp=True, want_philox=True, stream=None):
                               ctypes.c_void_p(p.ctypes.data) if p is not None else None, _stream(stream)),
            "ind_selftest")
     return e, p
+
+
+def species_rank_static(key_loc, key_time, out, stream=None):
+    """ind_species_rank_static: dense species ids of device key tensors into the
+    device tensor `out` (nothing is allocated); returns the species count"""
+    n = ctypes.c_uint64(0)
+    _check(lib().ind_species_rank_static(ctypes.c_void_p(key_loc.data_ptr()), ctypes.c_void_p(key_time.data_ptr()),
+                                         int(key_loc.numel()), ctypes.c_void_p(out.data_ptr()), ctypes.byref(n),
+                                         _stream(stream)), "ind_species_rank_static")
+    return int(n.value)
 
 
 def kernel_launches():
