@@ -53,8 +53,8 @@ def build(force=False):
 
 
 class _LnTables(ctypes.Structure):
-    _fields_ = [("ln_tab", ctypes.c_uint64 * 256), ("ln2_q64", ctypes.c_uint64),
-                ("coef", ctypes.c_int64 * 7)]
+    _fields_ = [("ln_tab", ctypes.c_uint64 * (1 << tables.LN_TABLE_BITS)), ("ln2_q64", ctypes.c_uint64),
+                ("c3", ctypes.c_int64)]
 
 
 class _Model(ctypes.Structure):
@@ -111,13 +111,12 @@ _ln_struct = None
 def _ln():
     global _ln_struct
     if _ln_struct is None:
-        tab, ln2, coef, _ = tables.ln_tables()
+        tab, ln2, c3, _ = tables.ln_tables()
         s = _LnTables()
-        for j in range(256):
-            s.ln_tab[j] = tab[j]
+        for j, v in enumerate(tab):
+            s.ln_tab[j] = v
         s.ln2_q64 = ln2
-        for k in range(7):
-            s.coef[k] = coef[k]
+        s.c3 = c3
         _ln_struct = s
     return _ln_struct
 

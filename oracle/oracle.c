@@ -120,32 +120,34 @@ static uint64_t mulhi64(uint64_t a, uint64_t b)
  * r = the top 53 bits of a draw.  ln is evaluated in fixed point:
  *   n = r + 1 = 2^e * m,  m in [1, 2)
  *   -ln U = (53 - e) ln 2 - ln m
- *   ln m = ln(2^16 / R_j) + ln(1 + rr),  1 + rr = m R_j / 2^16
- * with the 8 fraction bits after the leading one of m selecting j, a 16-bit
- * reciprocal R_j of the bucket midpoint, a table L_j of ln(2^16/R_j) and the
- * series ln(1+rr) = rr - rr^2/2 + ... + rr^6/6 (|rr| < 2^-8.9) in signed
- * Q2.62 arithmetic.  The result is rounded to Q6.58 and converted to double.
- * The tables are inputs: L_j = round(2^62 ln(2^16/R_j)), ln2_64 =
- * round(2^64 ln 2), coef[k] = round(2^62/k), k = 1..6.
+ *   ln m = ln(2^32 / R_j) + ln(1 + s),  1 + s = m R_j / 2^32
+ * where the 12 fraction bits after the leading one of m select j, R_j is a
+ * 32-bit reciprocal of the bucket midpoint (so |s| < 2^-12.9), L_j =
+ * ln(2^32/R_j) comes from a table, and
+ *   ln(1 + s) = s - s^2 (1/2 - s/3 + s^2/4)
+ * (the series to s^4; the s^5/5 term is below 2^-66) is evaluated with s in
+ * signed Q0.64 and the bracket in Q2.62.  The result is rounded half up to
+ * Q6.58 and converted to double.  Tables (inputs): L_j = round(2^62 ln(2^32 /
+ * R_j)), ln2_q64 = round(2^64 ln 2), c3 = round(2^64 / 3).
  * ------------------------------------------------------------------------ */
+#define OR_LN_BITS 12
 typedef struct {
-    uint64_t ln_tab[256];
+    uint64_t ln_tab[1 << OR_LN_BITS];
     uint64_t ln2_q64;
-    int64_t coef[7];
+    int64_t c3;
 } or_ln_tables;
 
 uint32_t or_ln_recip(uint32_t j)
 {
-    /* round(2^25 / (513 + 2j)), ties up: 2^16 over the bucket midpoint
-     * (513 + 2j) / 512 */
-    uint64_t d = 513u + 2u * (uint64_t)j;
-    return (uint32_t)(((1ull << 26) + d) / (2u * d));
+    /* round(2^45 / (8193 + 2j)), ties up */
+    uint64_t d = 8193u + 2u * (uint64_t)j;
+    return (uint32_t)(((1ull << 46) + d) / (2u * d));
 }
 
-static int64_t q62_mul(int64_t a, int64_t b)
+/* floor(a b / 2^64) for signed a, b */
+static int64_t mulhi_s(int64_t a, int64_t b)
 {
-    i128 p = (i128)a * (i128)b;
-    return (int64_t)(p >> 62); /* floor division by 2^62 */
+    return (int64_t)(((i128)a * (i128)b) >> 64);
 }
 
 /* the fixed-point value of -ln((r + 1) 2^-53) in units of 2^-58 */
@@ -154,15 +156,15 @@ uint64_t or_exp1_q58(uint64_t r53, const or_ln_tables* T)
     uint64_t n = r53 + 1u;                 /* 1 .. 2^53 */
     int e = 63 - __builtin_clzll(n);       /* floor(log2 n) */
     uint64_t M = n << (63 - e);            /* m * 2^63 */
-    uint32_t j = (uint32_t)((M >> 55) & 0xFFu);
-    uint32_t R = or_ln_recip(j);
-    u128 t = (u128)M * (u128)R;            /* (1 + rr) * 2^79 */
-    int64_t rr = (int64_t)(uint64_t)(t >> 17) - (int64_t)(1ull << 62);
-    int64_t P = T->coef[6];
-    for (int k = 5; k >= 1; k--)
-        P = T->coef[k] - q62_mul(rr, P);
-    int64_t ln1p = q62_mul(rr, P);         /* ln(1 + rr), Q62 */
-    int64_t lnm = (int64_t)T->ln_tab[j] + ln1p; /* ln m, Q62 */
+    uint32_t j = (uint32_t)((M >> (63 - OR_LN_BITS)) & ((1u << OR_LN_BITS) - 1u));
+    u128 P = (u128)M * (u128)or_ln_recip(j);             /* (1 + s) 2^95 */
+    int64_t s = (int64_t)(uint64_t)(P >> 31);            /* Q0.64, wraps to s */
+    int64_t s2 = mulhi_s(s, s);                           /* s^2, Q0.64 */
+    int64_t s3 = mulhi_s(s, T->c3);                       /* s/3, Q0.64 */
+    int64_t t = ((int64_t)1 << 61) - (s3 >> 2) + (s2 >> 4); /* 1/2 - s/3 + s^2/4, Q2.62 */
+    int64_t q = (int64_t)(((u128)(uint64_t)s2 * (u128)(uint64_t)t) >> 64); /* s^2 t, Q2.62 */
+    int64_t ln1p = s - q * 4;                             /* ln(1 + s), Q0.64 */
+    int64_t lnm = (int64_t)T->ln_tab[j] + (ln1p >> 2);    /* ln m, Q2.62 */
     i128 x64 = (i128)(53 - e) * (i128)T->ln2_q64 - (i128)lnm * 4;
     if (x64 < 0)
         x64 = 0;

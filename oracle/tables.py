@@ -7,9 +7,9 @@ Every table is a rounding of a real-valued definition to integers:
 
 * ``ln_tables`` -- the fixed-point natural logarithm behind the inverse
   transform Exp(1) = -ln U (appendix "Inverse Transform: Uniform and
-  Exponential"): L_j = round(2^62 ln(2^16 / R_j)) with
-  R_j = round(2^25 / (513 + 2j)), ln2_q64 = round(2^64 ln 2) and the series
-  coefficients round(2^62 / k).
+  Exponential"): L_j = round(2^62 ln(2^32 / R_j)) with
+  R_j = round(2^45 / (8193 + 2j)), ln2_q64 = round(2^64 ln 2) and
+  round(2^64 / 3).
 * ``gauss_cdf`` -- the per-axis discretised normal N(0, sigma^2) used for
   Gaussian dispersal (section "Normal Dispersal" compares against exactly
   this discretisation): entry k is round(2^64 Phi((k - half + 1/2) / sigma)),
@@ -37,25 +37,31 @@ def _round_with_margin(x):
     return value, float(abs(frac - mpmath.mpf("0.5")))
 
 
+LN_TABLE_BITS = 12
+
+
 def ln_recip(j):
-    """R_j = round(2^25 / (513 + 2 j)), ties up (integer arithmetic)"""
-    d = 513 + 2 * j
-    return ((1 << 26) + d) // (2 * d)
+    """R_j = round(2^45 / (8193 + 2 j)), ties up (integer arithmetic): 2^32
+    over the midpoint (8193 + 2j) / 8192 of bucket j of m in [1, 2)"""
+    d = 8193 + 2 * j
+    return ((1 << 46) + d) // (2 * d)
 
 
 @functools.lru_cache(maxsize=None)
 def ln_tables():
-    """(ln_tab[256], ln2_q64, coef[0..6], min_margin)"""
+    """(ln_tab[4096], ln2_q64, c3_q64, min_margin):
+    ln_tab[j] = round(2^62 ln(2^32 / R_j)), ln2_q64 = round(2^64 ln 2),
+    c3_q64 = round(2^64 / 3)"""
     with mpmath.workdps(_DPS):
         tab, margins = [], []
-        for j in range(256):
-            v, mg = _round_with_margin(mpmath.ldexp(mpmath.log(mpmath.mpf(1 << 16) / ln_recip(j)), 62))
+        for j in range(1 << LN_TABLE_BITS):
+            v, mg = _round_with_margin(mpmath.ldexp(mpmath.log(mpmath.mpf(2) ** 32 / ln_recip(j)), 62))
             tab.append(v)
             margins.append(mg)
         ln2, mg = _round_with_margin(mpmath.ldexp(mpmath.log(2), 64))
         margins.append(mg)
-    coef = [0] + [((1 << 63) + k) // (2 * k) for k in range(1, 7)]
-    return tuple(tab), ln2, tuple(coef), min(margins)
+    c3 = ((1 << 65) + 3) // 6  # round(2^64 / 3)
+    return tuple(tab), ln2, c3, min(margins)
 
 
 def gauss_half(sigma):

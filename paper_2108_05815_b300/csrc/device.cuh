@@ -82,56 +82,90 @@ __host__ __device__ __forceinline__ uint64_t umulhi64(uint64_t a, uint64_t b) {
 // ---------------------------------------------------------------------------
 // Exp(1) by inverse transform of U = (r + 1) 2^-53, r the top 53 bits of a
 // draw: -ln U = (53 - e) ln 2 - ln m for r + 1 = m 2^e, m in [1, 2).
-// ln m = ln(2^16 / R_j) + ln(1 + s), with j the 8 bits after the leading one
-// of m, R_j = round(2^25 / (513 + 2 j)) and 1 + s = m R_j / 2^16
-// (|s| < 2^-8.9), the series to s^6 evaluated in signed Q2.62.  Result in
-// Q6.58, rounded half up, then converted to binary64.
+// ln m = ln(2^32 / R_j) + ln(1 + s), with j the 12 bits after the leading one
+// of m, R_j = round(2^45 / (8193 + 2 j)) and 1 + s = m R_j / 2^32
+// (|s| < 2^-12.9); ln(1 + s) = s - s^2 (1/2 - s/3 + s^2/4) with s in signed
+// Q0.64 and the bracket in Q2.62.  Result in Q6.58, rounded half up.
+// The chain is built for latency: the two 64-bit high products that feed
+// the bracket run in parallel, and (53 - e) ln 2 is formed off the chain.
 // ---------------------------------------------------------------------------
-struct LnTables {
-    uint64_t L[256];     // round(2^62 ln(2^16 / R_j))
-    uint32_t R[256];     // R_j
+constexpr int LN_BITS = 12;
+constexpr uint32_t LN_N = 1u << LN_BITS;
+
+struct __align__(16) LnTables {
+    uint64_t L[LN_N];    // round(2^62 ln(2^32 / R_j))
+    uint32_t R[LN_N];    // R_j
     uint64_t ln2_q64;    // round(2^64 ln 2)
-    int64_t c[7];        // round(2^62 / k), k = 1..6
+    int64_t c3;          // round(2^64 / 3)
 };
 
-// floor(a b / 2^62) for signed a, b whose product fits in 2^125
-__device__ __forceinline__ int64_t q62_mul(int64_t a, int64_t b) {
-    uint64_t lo = (uint64_t)a * (uint64_t)b;
-    int64_t hi = __mul64hi(a, b);
-    return (int64_t)(((uint64_t)hi << 2) | (lo >> 62));
-}
-
 __device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64_t* __restrict__ Ltab,
-                                             const uint32_t* __restrict__ Rtab, uint64_t ln2_q64,
-                                             const int64_t* c) {
+                                             const uint32_t* __restrict__ Rtab, uint64_t ln2_q64, int64_t c3) {
     const uint64_t n = r53 + 1ull;
     const int lz = __clzll((long long)n);            // 10 .. 63
     const uint64_t M = n << lz;                      // m 2^63
-    const uint32_t j = (uint32_t)(M >> 55) & 0xFFu;
-    const uint64_t R = Rtab[j];
-    const uint64_t plo = M * R;
-    const uint64_t phi = __umul64hi(M, R);           // (1 + s) 2^79 = phi:plo
-    const int64_t s = (int64_t)((phi << 47) | (plo >> 17)) - (int64_t)(1ull << 62);
-    int64_t P = c[6];
-    P = c[5] - q62_mul(s, P);
-    P = c[4] - q62_mul(s, P);
-    P = c[3] - q62_mul(s, P);
-    P = c[2] - q62_mul(s, P);
-    P = c[1] - q62_mul(s, P);
-    const int64_t lnm = (int64_t)Ltab[j] + q62_mul(s, P);    // Q62, |lnm| < 1
-    // x = k ln2 (Q64, 128-bit) - 4 lnm, k = 53 - e = lz - 10
+    const uint32_t j = (uint32_t)(M >> (63 - LN_BITS)) & (LN_N - 1u);
+    const uint32_t R = Rtab[j];   // plain loads: the tables may sit in shared or global memory
+    const uint64_t Lj = Ltab[j];
+    // (53 - e) ln 2 in Q0.64, 128-bit, independent of the table lookups
     const uint64_t k = (uint64_t)(lz - 10);
-    uint64_t xlo = k * ln2_q64;
-    uint64_t xhi = __umul64hi(k, ln2_q64);
+    const uint64_t klo = k * ln2_q64;
+    const uint64_t khi = __umul64hi(k, ln2_q64);
+    // P = M R = (Mh R) 2^32 + Ml R; s = low 64 bits of P >> 31
+    const uint64_t pl = (uint64_t)(uint32_t)M * R;
+    const uint64_t ph = (uint64_t)(uint32_t)(M >> 32) * R;
+    const int64_t s = (int64_t)((ph << 1) + (pl >> 31));
+    const int64_t s2 = __mul64hi(s, s);
+    const int64_t s3 = __mul64hi(s, c3);
+    const int64_t t = (1ll << 61) - (s3 >> 2) + (s2 >> 4);
+    const int64_t q = (int64_t)__umul64hi((uint64_t)s2, (uint64_t)t);
+    const int64_t ln1p = s - (q << 2);
+    const int64_t lnm = (int64_t)Lj + (ln1p >> 2);  // Q2.62
+    // x = k ln2 - 4 lnm (128-bit), clamp at 0, round half up to Q6.58
     const uint64_t slo = (uint64_t)lnm << 2;
-    const uint64_t shi = (uint64_t)(lnm >> 62);      // sign extension of 4 lnm
-    const uint64_t borrow = xlo < slo ? 1ull : 0ull;
-    xlo -= slo;
-    xhi = xhi - shi - borrow;
+    const uint64_t shi = (uint64_t)(lnm >> 62);
+    const uint64_t borrow = klo < slo ? 1ull : 0ull;
+    const uint64_t xlo = klo - slo;
+    const uint64_t xhi = khi - shi - borrow;
     if ((int64_t)xhi < 0) return 0ull;
     const uint64_t rlo = xlo + 32ull;
     const uint64_t rhi = xhi + (rlo < xlo ? 1ull : 0ull);
     return (rhi << 58) | (rlo >> 6);
+}
+
+// round-to-nearest-even binary64 of q 2^-58 (q < 2^64), by integer assembly
+__device__ __forceinline__ double q58_to_double(uint64_t q) {
+    if (q == 0ull) return 0.0;
+    const int lz = __clzll((long long)q);
+    const uint64_t m = q << lz;                       // bit 63 set
+    uint64_t mant = m >> 11;                          // 53 bits
+    const uint64_t rem = m & 0x7FFull;
+    mant += (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    int64_t E = 5 - lz;                               // q 2^-58 = (m / 2^63) 2^(5 - lz)
+    if (mant >> 53) {
+        mant >>= 1;
+        E += 1;
+    }
+    return __longlong_as_double((long long)(((uint64_t)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
+// ---------------------------------------------------------------------------
+// exact integer forms of the event-time bookkeeping (delta_t = 2^d)
+// ---------------------------------------------------------------------------
+// floor(tau / 2^d) for tau >= 0 given by its bits; tau < 2^(53 + d)
+__device__ __forceinline__ uint64_t floor_div_pow2(uint64_t tau_bits, int d) {
+    const int E = (int)((tau_bits >> 52) & 0x7FF) - 1023 - d;
+    if (E < 0) return 0ull;
+    const uint64_t mant = (tau_bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    return E >= 52 ? mant << (E - 52) : mant >> (52 - E);
+}
+
+// bits of the binary64 value k 2^d (exact for k < 2^53)
+__device__ __forceinline__ uint64_t k_times_pow2_bits(uint64_t k, int d) {
+    if (k == 0ull) return 0ull;
+    const int lz = __clzll((long long)k);
+    const uint64_t mant = (k << lz) >> 11;            // exact: k < 2^53
+    return ((uint64_t)(63 - lz + d + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
 }
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,7 @@
 #include "device.cuh"
 
 namespace indep {
-void host_ln_tables(uint64_t L[256], uint32_t R[256], uint64_t* ln2_q64, int64_t c[7]);
+void host_ln_tables(uint64_t* L, uint32_t* R, int n, uint64_t* ln2_q64, int64_t* c3);
 int host_gauss_half(double sigma);
 std::vector<uint64_t> host_gauss_cdf(double sigma);
 std::vector<uint64_t> host_kernel_weights(double sigma, int radius);
@@ -130,7 +130,7 @@ static ind_status ensure_ln_tables(cudaStream_t s) {
     if ((int)g_ln_ready.size() <= dev) g_ln_ready.resize(dev + 1, 0);
     if (g_ln_ready[dev]) return IND_OK;
     static LnTables host;
-    host_ln_tables(host.L, host.R, &host.ln2_q64, host.c);
+    host_ln_tables(host.L, host.R, (int)LN_N, &host.ln2_q64, &host.c3);
     CK(cudaMemcpyToSymbolAsync(g_ln, &host, sizeof(LnTables), 0, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
     g_ln_ready[dev] = 1;
@@ -153,6 +153,7 @@ struct SimParams {
     int32_t gauss_half;
     uint32_t gauss_n;
     const uint64_t* gauss;     // 2 half discretised-normal CDF thresholds
+    const uint16_t* gauss_guide;  // 256 entries: thresholds below (g << 56)
     const uint8_t* deme_map;   // W*H
     const uint32_t* row_of;    // W*H alias row of a cell
     const uint64_t* alias;     // rows x n_off entries: q | alias << 32 | full << 63
@@ -239,7 +240,7 @@ struct LaneSim {
     uint32_t W, H, D;
     uint64_t nu_thr;
     uint32_t sk0, sk1;
-    double dt, inv_dt;
+    int dt_log2;
     double lam;
     bool lam1;
     double horizon;
@@ -256,48 +257,82 @@ __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __rest
     c.nu_thr = __ldg(&p->nu_thr);
     c.sk0 = __ldg(&p->sk0);
     c.sk1 = __ldg(&p->sk1);
-    int dl = __ldg(&p->dt_log2);
-    c.dt = ldexp(1.0, dl);
-    c.inv_dt = ldexp(1.0, -dl);
+    c.dt_log2 = __ldg(&p->dt_log2);
     c.lam = __ldg(&p->lambda);
     c.lam1 = (c.lam == 1.0);
     c.horizon = *(volatile const double*)&S[sim].horizon;
 }
 
-struct LnSh {
+// the logarithm tables (global, read through L1, or a block's shared copy)
+struct LnC {
     const uint64_t* L;
     const uint32_t* R;
     uint64_t ln2;
-    int64_t c[7];
+    int64_t c3;
 };
 
-__device__ __forceinline__ double exp_draw(uint64_t v, const LnSh& ln, const LaneSim& c) {
-    uint64_t q = exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c);
-    double x = __dmul_rn(__ull2double_rn(q), 0x1p-58);
+__device__ __forceinline__ LnC ln_tables() {
+    return LnC{g_ln.L, g_ln.R, g_ln.ln2_q64, g_ln.c3};
+}
+
+constexpr size_t LN_SMEM_BYTES = sizeof(uint64_t) * LN_N + sizeof(uint32_t) * LN_N;
+
+// copy the logarithm tables into shared memory (all threads of the block)
+__device__ __forceinline__ LnC ln_tables_shared(unsigned char* smem) {
+    uint4* dst = (uint4*)smem;
+    const uint4* src = (const uint4*)&g_ln;  // L then R, contiguous, 16-byte aligned
+    for (uint32_t i = threadIdx.x; i < LN_SMEM_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return LnC{(const uint64_t*)smem, (const uint32_t*)(smem + sizeof(uint64_t) * LN_N), g_ln.ln2_q64, g_ln.c3};
+}
+
+// binary64 of q 2^-58: the hardware conversion rounds q to nearest even, and
+// the scaling by 2^-58 is exact (normal range), applied to the exponent field
+__device__ __forceinline__ double q58_to_double_hw(uint64_t q) {
+    if (q == 0ull) return 0.0;
+    const uint64_t b = (uint64_t)__double_as_longlong(__ull2double_rn(q));
+    return __longlong_as_double((long long)(b - (58ull << 52)));
+}
+
+__device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const LaneSim& c) {
+    const double x = q58_to_double_hw(exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3));
     return c.lam1 ? x : __ddiv_rn(x, c.lam);
 }
 
-// first point of loc's event process strictly after tau; negative on overflow
-__device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnSh& ln) {
-    uint64_t k = __double2ull_rd(__dmul_rn(tau, c.inv_dt));
+// first point of loc's event process strictly after tau; negative on overflow.
+// Times are non-negative binary64, so they order like their bit patterns: the
+// compares, floor(tau / delta_t) and k delta_t are done on the bits.  WIDE
+// blocks (2 WIDE draws) are generated and converted together; the draws of a
+// step are independent, so their logarithms overlap, and only the binary64
+// sums run one after another, in the spec's order.
+template <int WIDE>
+__device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
     for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
-        double p = __dmul_rn(__ull2double_rn(k), c.dt);
-        const double end = __dmul_rn(__ull2double_rn(k + 1ull), c.dt);
+        if (k >= (1ull << 52)) return -1.0;
+        double p = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const uint64_t end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
         bool next_interval = false;
-        for (uint32_t j = 0; j < INTERVAL_BLOCK_LIMIT; ++j) {
-            const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
-            p = __dadd_rn(p, exp_draw(b.lo, ln, c));
-            if (p >= end) {
-                next_interval = true;
-                break;
+        for (uint32_t j = 0; j < INTERVAL_BLOCK_LIMIT; j += WIDE) {
+            double x[2 * WIDE];
+#pragma unroll
+            for (int w = 0; w < WIDE; ++w) {
+                const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
+                x[2 * w] = exp_draw(b.lo, ln, c);
+                x[2 * w + 1] = exp_draw(b.hi, ln, c);
             }
-            if (p > tau) return p;
-            p = __dadd_rn(p, exp_draw(b.hi, ln, c));
-            if (p >= end) {
-                next_interval = true;
-                break;
+#pragma unroll
+            for (int d = 0; d < 2 * WIDE; ++d) {
+                p = __dadd_rn(p, x[d]);
+                const uint64_t pb = (uint64_t)__double_as_longlong(p);
+                if (pb >= end_b) {
+                    next_interval = true;
+                    break;
+                }
+                if (pb > tau_b) return p;
             }
-            if (p > tau) return p;
+            if (next_interval) break;
         }
         if (!next_interval) return -1.0;
         ++k;
@@ -305,9 +340,13 @@ __device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, co
     return -1.0;
 }
 
-__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, uint32_t n, int32_t half,
-                                              uint64_t r) {
-    return (int32_t)upper_bound_u64(t, n, r) - half;
+// discretised normal by inversion: -half + #{k : cdf[k] <= r}; the guide
+// gives the count below the start of r's top-8-bit bucket
+__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
+                                              uint32_t n, int32_t half, uint64_t r) {
+    uint32_t idx = __ldg(guide + (r >> 56));
+    while (idx < n && __ldg(t + idx) <= r) ++idx;
+    return (int32_t)idx - half;
 }
 
 // one event at (loc, tau); returns true if the lineage speciated, else
@@ -327,10 +366,11 @@ __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __re
     const uint32_t x = loc_x(loc), y = loc_y(loc);
     if (c.kind == KIND_TORUS) {
         const uint64_t* g = p->gauss;
+        const uint16_t* gd = p->gauss_guide;
         const uint32_t gn = __ldg(&p->gauss_n);
         const int32_t gh = __ldg(&p->gauss_half);
-        const uint32_t tx = wrap_add(x, gauss_step(g, gn, gh, b0.hi), c.W);
-        const uint32_t ty = wrap_add(y, gauss_step(g, gn, gh, b1.lo), c.H);
+        const uint32_t tx = wrap_add(x, gauss_step(g, gd, gn, gh, b0.hi), c.W);
+        const uint32_t ty = wrap_add(y, gauss_step(g, gd, gn, gh, b1.lo), c.H);
         const uint64_t ti = c.D > 1 ? umulhi64(b1.hi, c.D) : 0ull;
         loc = pack_loc(tx, ty, ti);
         return false;
@@ -432,14 +472,7 @@ __device__ __forceinline__ void warp_add_by_sim(unsigned mask, uint32_t sim, uin
 // kernels
 // ---------------------------------------------------------------------------
 __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32_t n_lin) {
-    __shared__ uint64_t sL[256];
-    __shared__ uint32_t sR[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        sL[i] = g_ln.L[i];
-        sR[i] = g_ln.R[i];
-    }
-    __syncthreads();
-    LnSh ln{sL, sR, g_ln.ln2_q64, {g_ln.c[0], g_ln.c[1], g_ln.c[2], g_ln.c[3], g_ln.c[4], g_ln.c[5], g_ln.c[6]}};
+    const LnC ln = ln_tables();
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_lin; g += gridDim.x * blockDim.x) {
         // simulation of lineage g: last s with gid_base[s] <= g
         uint32_t lo = 0, hi = B.n_sims;
@@ -451,7 +484,7 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
         LaneSim c;
         load_lanesim(c, B.P, B.S, lo);
         const uint64_t loc = B.P[lo].sample_loc[g - gid_base[lo]];
-        double t = next_event_time(c, loc, 0.0, ln);
+        double t = next_event_time<1>(c, loc, 0.0, ln);
         if (t < 0.0) {
             atomicOr(&B.S[lo].error, 1u);
             atomicOr(&B.G->error, 1u);
@@ -465,23 +498,20 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
     }
 }
 
-template <bool COUNT>
+template <bool COUNT, int WIDE>
 __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
-    __shared__ uint64_t sL[256];
-    __shared__ uint32_t sR[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        sL[i] = g_ln.L[i];
-        sR[i] = g_ln.R[i];
-    }
-    __syncthreads();
-    const LnSh ln{sL, sR, g_ln.ln2_q64, {g_ln.c[0], g_ln.c[1], g_ln.c[2], g_ln.c[3], g_ln.c[4], g_ln.c[5], g_ln.c[6]}};
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    const uint32_t chunk = 32u * B.lpl;
+    // a block whose first possible claim lies beyond the active lineages has
+    // nothing to do (claims go out in order of arrival, at most one per warp)
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    const LnC ln = ln_tables_shared(adv_smem);
 
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
-    const uint32_t n = B.G->n_total;
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const uint32_t chunk = 32u * B.lpl;
 
     uint32_t chunk_next = 0, chunk_end = 0;  // warp-uniform
     bool exhausted = false;
@@ -554,7 +584,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                     L.gid[idx] = gid | DONE_BIT;
                     has = false;
                 } else {
-                    const double nt = next_event_time(c, loc, tn, ln);
+                    const double nt = next_event_time<WIDE>(c, loc, tn, ln);
                     if (nt < 0.0) {
                         atomicOr(&B.S[c.sim].error, 1u);
                         atomicOr(&B.G->error, 1u);
@@ -1042,18 +1072,10 @@ __global__ void k_sample_write(const uint32_t* flags, const uint32_t* pos, uint6
 // device arithmetic probes for the conformance tests
 __global__ void k_selftest(const uint64_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ exp_q58,
                            uint32_t* __restrict__ philox_out) {
-    __shared__ uint64_t sL[256];
-    __shared__ uint32_t sR[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        sL[i] = g_ln.L[i];
-        sR[i] = g_ln.R[i];
-    }
-    __syncthreads();
-    int64_t c[7];
-    for (int k = 0; k < 7; ++k) c[k] = g_ln.c[k];
+    const LnC ln = ln_tables();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t v = in[i];
-        if (exp_q58) exp_q58[i] = exp1_q58(v >> 11, sL, sR, g_ln.ln2_q64, c);
+        if (exp_q58) exp_q58[i] = exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3);
         if (philox_out) {
             const uint64_t w = in[(i + 1) % n], z = in[(i + 2) % n];
             const u32x4 o = philox10((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)w, (uint32_t)(w >> 32),
@@ -1087,6 +1109,7 @@ struct ind_sim {
     Pool sample;   // sampled locations
     Pool results;  // outputs
     uint64_t* d_gauss = nullptr;
+    uint16_t* d_gauss_guide = nullptr;
     uint32_t gauss_n = 0;
     int gauss_half = 0;
     uint8_t* d_deme = nullptr;
@@ -1140,12 +1163,14 @@ struct Batch {
     uint32_t* d_gid_base = nullptr;
     BatchDev dev{};
     Globals* h_g = nullptr;  // pinned
+    bool h_g_valid = false;
     std::vector<SimState> h_state;
     bool started = false;
     bool finished = false;
     uint64_t rounds = 0;
-    cudaGraphExec_t graph = nullptr;
-    uint32_t graph_rounds = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured chunk of rounds per advance variant
+    uint32_t graph_rounds[2] = {0, 0};
+    bool wide = false;                               // latency variant of the advance kernel
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -1154,7 +1179,8 @@ struct Batch {
     double ms = 0.0;
 
     ~Batch() {
-        if (graph) cudaGraphExecDestroy(graph);
+        for (auto g : graph)
+            if (g) cudaGraphExecDestroy(g);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_end) cudaEventDestroy(e);
@@ -1187,6 +1213,7 @@ static ind_status batch_build(Batch& b) {
         p.gauss_half = m->gauss_half;
         p.gauss_n = m->gauss_n;
         p.gauss = m->d_gauss;
+        p.gauss_guide = m->d_gauss_guide;
         p.deme_map = m->d_deme;
         p.row_of = m->d_row_of;
         p.alias = m->d_alias;
@@ -1278,6 +1305,10 @@ static ind_status batch_build(Batch& b) {
         }
     }
     const uint32_t sms = sm_count();
+    CK(cudaFuncSetAttribute(k_advance<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
     b.cmp_blocks = sms * 4;
@@ -1297,8 +1328,13 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     const bool prof = b.tun.profile && r < b.ev_start.size();
     const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
-    if (b.dev.count_unique) k_advance<true><<<b.adv_blocks, b.adv_threads, 0, s>>>(b.dev);
-    else k_advance<false><<<b.adv_blocks, b.adv_threads, 0, s>>>(b.dev);
+    if (b.dev.count_unique) {
+        if (b.wide) k_advance<true, 2><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+    } else {
+        if (b.wide) k_advance<false, 2><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+    }
     CKL();
     if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));
     k_compact<<<b.cmp_blocks, 256, 0, s>>>(b.dev);
@@ -1308,10 +1344,11 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
 
 static ind_status batch_rounds(Batch& b, uint32_t rounds) {
     if (b.tun.use_graph) {
-        if (!b.graph || b.graph_rounds != rounds) {
-            if (b.graph) {
-                cudaGraphExecDestroy(b.graph);
-                b.graph = nullptr;
+        const int v = b.wide ? 1 : 0;
+        if (!b.graph[v] || b.graph_rounds[v] != rounds) {
+            if (b.graph[v]) {
+                cudaGraphExecDestroy(b.graph[v]);
+                b.graph[v] = nullptr;
             }
             cudaGraph_t g;
             if (!b.cap_stream) CK(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
@@ -1324,11 +1361,11 @@ static ind_status batch_rounds(Batch& b, uint32_t rounds) {
                 }
             }
             CK(cudaStreamEndCapture(b.cap_stream, &g));
-            CK(cudaGraphInstantiate(&b.graph, g, 0));
+            CK(cudaGraphInstantiate(&b.graph[v], g, 0));
             cudaGraphDestroy(g);
-            b.graph_rounds = rounds;
+            b.graph_rounds[v] = rounds;
         }
-        CK(cudaGraphLaunch(b.graph, b.stream));
+        CK(cudaGraphLaunch(b.graph[v], b.stream));
         g_launches.fetch_add(2ull * rounds);
         return IND_OK;
     }
@@ -1473,12 +1510,14 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
             }
             chunk = (uint32_t)std::min<uint64_t>(chunk, round_budget - done_rounds);
         }
+        b.wide = false;  // the four-draw variant measured slower on B300
         ind_status st = batch_rounds(b, chunk);
         if (st != IND_OK) return st;
         done_rounds += chunk;
         b.rounds += chunk;
         CK(cudaMemcpyAsync(b.h_g, b.d_g, sizeof(Globals), cudaMemcpyDeviceToHost, b.stream));
         CK(cudaStreamSynchronize(b.stream));
+        b.h_g_valid = true;
         collect_profile(b, chunk);
         if (b.h_g->error) {
             CK(cudaMemcpyAsync(b.h_state.data(), b.d_state, sizeof(SimState) * b.n_sims, cudaMemcpyDeviceToHost,
@@ -1636,9 +1675,14 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
         std::vector<uint64_t> cdf = host_gauss_cdf(D->sigma);
         m->gauss_half = host_gauss_half(D->sigma);
         m->gauss_n = (uint32_t)cdf.size();
+        std::vector<uint16_t> guide(256);
+        for (uint32_t g = 0; g < 256; ++g)
+            guide[g] = (uint16_t)(std::lower_bound(cdf.begin(), cdf.end(), (uint64_t)g << 56) - cdf.begin());
         m->d_gauss = m->tables.get<uint64_t>(cdf.size());
-        if (!m->d_gauss) return fail(IND_ERR_OOM);
+        m->d_gauss_guide = m->tables.get<uint16_t>(256);
+        if (!m->d_gauss || !m->d_gauss_guide) return fail(IND_ERR_OOM);
         if (cudaMemcpyAsync(m->d_gauss, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(m->d_gauss_guide, guide.data(), 512, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             g_last_cuda_error.store((int)cudaGetLastError());
             return fail(IND_ERR_CUDA);

@@ -1,7 +1,7 @@
 // tables.cpp -- host-side integer tables of the library, computed in binary128
 // (libquadmath).  They are roundings of real-valued definitions:
-//   ln tables   L_j = round(2^62 ln(2^16 / R_j)), R_j = round(2^25/(513+2j)),
-//               ln2 = round(2^64 ln 2), c_k = round(2^62 / k)  (inverse
+//   ln tables   L_j = round(2^62 ln(2^32 / R_j)), R_j = round(2^45/(8193+2j)),
+//               ln2 = round(2^64 ln 2), c3 = round(2^64 / 3)  (inverse
 //               transform -ln U of the appendix "Inverse Transform: Uniform
 //               and Exponential")
 //   Gaussian    C_k = round(2^64 Phi((k - half + 1/2) / sigma)), clamped to
@@ -29,16 +29,15 @@ static uint64_t round_q(__float128 x) {
     return (uint64_t)f;
 }
 
-void host_ln_tables(uint64_t L[256], uint32_t R[256], uint64_t* ln2_q64, int64_t c[7]) {
-    for (uint32_t j = 0; j < 256; ++j) {
-        uint64_t d = 513u + 2u * (uint64_t)j;
-        R[j] = (uint32_t)(((1ull << 26) + d) / (2u * d));
-        __float128 v = logq((__float128)65536 / (__float128)R[j]);
+void host_ln_tables(uint64_t* L, uint32_t* R, int n, uint64_t* ln2_q64, int64_t* c3) {
+    for (int j = 0; j < n; ++j) {
+        uint64_t d = 8193u + 2u * (uint64_t)j;
+        R[j] = (uint32_t)(((1ull << 46) + d) / (2u * d));
+        __float128 v = logq(ldexpq((__float128)1, 32) / (__float128)R[j]);
         L[j] = round_q(ldexpq(v, 62));
     }
     *ln2_q64 = round_q(ldexpq(logq((__float128)2), 64));
-    c[0] = 0;
-    for (int k = 1; k <= 6; ++k) c[k] = (int64_t)(((1ull << 63) + (uint64_t)k) / (2ull * (uint64_t)k));
+    *c3 = (int64_t)((((unsigned __int128)1 << 65) + 3) / 6);  // round(2^64 / 3)
 }
 
 int host_gauss_half(double sigma) { return (int)std::ceil(10.0 * sigma); }

@@ -161,6 +161,8 @@ TUNINGS = [
     dict(block_threads=512, blocks_per_sm=2, lineages_per_lane=16),
     dict(events_per_round=500.0, min_events_per_lineage=0.5, tail_events=0.5, occupancy_step=0.05),
     dict(events_per_round=1e9, min_events_per_lineage=1e6),
+    dict(busy_lineages=0.0),
+    dict(busy_lineages=1e12),
 ]
 
 
