@@ -204,6 +204,56 @@ void sim_destroy(ind_sim* sim);
 ind_status sim_batch_run(ind_sim** sims, uint32_t n, const ind_tuning* tuning,
                          ind_run_stats* per_sim);
 
+/* ------------------------------------------------------------------------
+ * Continuous-batching server.
+ * Simulations (requests) are submitted while others run.  At every step the
+ * server admits queued requests in arrival order while their
+ * sim_mem_estimate fits in the HBM budget and a slot is free, appends their
+ * lineages to the resident batch (each request keeps its own horizon, so a
+ * newcomer starts at the present while others are deep in the past), runs a
+ * chunk of horizon rounds of one persistent advance kernel over all resident
+ * lineages, and retires the requests that finished: their species are
+ * resolved on a second stream, overlapping the next rounds, and become
+ * available through sim_species / sim_species_keys.  Results are
+ * bit-identical to running each request alone.
+ * ------------------------------------------------------------------------ */
+typedef struct ind_server ind_server;
+
+typedef struct {
+    uint64_t submitted, admitted, finished;  /* requests so far */
+    uint64_t queued, resident;               /* requests waiting / on the GPU */
+    uint64_t resident_lineages;              /* active lineages after the last step */
+    uint64_t bytes_admitted;                 /* sum of sim_mem_estimate of resident requests */
+    uint64_t rounds;                         /* horizon rounds run */
+    uint64_t raw_events;                     /* events executed by retired requests */
+    uint64_t lineage_capacity;               /* resident-lineage capacity of the buffers */
+} ind_server_stats;
+
+/* hbm_budget: bytes that resident requests may hold (their sim_mem_estimate
+ * summed); the lineage buffers are sized from it.  max_sims: resident
+ * requests at most (1..65536).  tuning NULL = defaults.  All work runs on
+ * cuda_stream (resolution of finished requests on a stream of the server's
+ * own that waits for it). */
+ind_status srv_create(uint64_t hbm_budget, uint32_t max_sims, const ind_tuning* tuning, void* cuda_stream,
+                      ind_server** out);
+
+/* Queue a created and sampled simulation that has not run yet; the server
+ * does not take ownership (destroy it after it finished or after
+ * srv_destroy).  *ticket (may be NULL) receives the submission number. */
+ind_status srv_submit(ind_server* srv, ind_sim* sim, uint64_t* ticket);
+
+/* Admit what fits, run up to `rounds` horizon rounds (>= 1) if anything is
+ * resident, then retire finished requests: up to cap tickets of requests
+ * finished in this step go to finished[] (host), their count to
+ * *n_finished.  Tickets beyond cap are reported by later calls. */
+ind_status srv_step(ind_server* srv, uint32_t rounds, uint64_t* finished, uint32_t cap, uint32_t* n_finished);
+
+ind_status srv_stats(const ind_server* srv, ind_server_stats* out);
+
+/* Free the server's device state.  Requests still resident are abandoned
+ * (their sim_species returns IND_ERR_STATE). NULL is a no-op. */
+void srv_destroy(ind_server* srv);
+
 /* Synthetic habitat map (seeded site percolation): cell (x, y) is habitable
  * iff the top 53 bits of the first draw of its map stream (stream key of
  * map_seed, location x | y << 20, time 0, tag MAP) are below

@@ -94,6 +94,13 @@ EXPORTS = {
                                     ctypes.c_void_p]),
     "ind_species_rank_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "srv_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "srv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "srv_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
+                                ctypes.c_void_p]),
+    "srv_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "srv_destroy": (None, [ctypes.c_void_p]),
     "ind_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ind_last_cuda_error": (ctypes.c_int, []),
     "ind_kernel_launches": (ctypes.c_uint64, []),
@@ -274,6 +281,54 @@ def batch_run(sims, **tuning):
     t = _tuning(tuning) if tuning else None
     _check(lib().sim_batch_run(arr, len(sims), ctypes.byref(t) if t else None, stats), "sim_batch_run")
     return [s.as_dict() for s in stats]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "admitted", "finished", "queued", "resident",
+                                               "resident_lineages", "bytes_admitted", "rounds", "raw_events",
+                                               "lineage_capacity")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Server:
+    """Continuous-batching server (srv_create / srv_submit / srv_step / srv_destroy)."""
+
+    def __init__(self, hbm_budget, max_sims=1024, stream=None, **tuning):
+        use_torch_allocator()
+        self._h = ctypes.c_void_p()
+        t = _tuning(tuning) if tuning else None
+        _check(lib().srv_create(int(hbm_budget), int(max_sims), ctypes.byref(t) if t else None, _stream(stream),
+                                ctypes.byref(self._h)), "srv_create")
+        self._fin = (ctypes.c_uint64 * 4096)()
+
+    def submit(self, sim):
+        t = ctypes.c_uint64(0)
+        _check(lib().srv_submit(self._h, sim._h, ctypes.byref(t)), "srv_submit")
+        return int(t.value)
+
+    def step(self, rounds=8):
+        """admit, run `rounds` horizon rounds, retire; returns finished tickets"""
+        n = ctypes.c_uint32(0)
+        _check(lib().srv_step(self._h, int(rounds), self._fin, len(self._fin), ctypes.byref(n)), "srv_step")
+        return [int(self._fin[i]) for i in range(n.value)]
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().srv_stats(self._h, ctypes.byref(st)), "srv_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().srv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def habitat(map_seed, width, height, p_habitable=0.6, max_deme=8, out=None, stream=None):
