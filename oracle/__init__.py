@@ -63,7 +63,8 @@ class _Model(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("delta_t", ctypes.c_double), ("nu", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("gauss_half", ctypes.c_int32),
                 ("gauss_cdf", ctypes.c_void_p), ("radius", ctypes.c_int32),
-                ("kw", ctypes.c_void_p), ("ln", ctypes.c_void_p)]
+                ("kw", ctypes.c_void_p), ("ln", ctypes.c_void_p), ("sampler", ctypes.c_int32),
+                ("pois_n", ctypes.c_int32), ("pois_cdf", ctypes.c_void_p)]
 
 
 def lib():
@@ -174,6 +175,10 @@ def habitat(map_seed, width, height, p_habitable=0.6, max_deme=8):
 class Model:
     """One simulation of the Independent algorithm.
 
+    sampler: 0 = inter-event times as sums of exponentials inside re-prime
+    intervals (section "Memoryless sums of exponentials"), 1 = Poisson point
+    counts with uniform points per interval (section "Homogeneous Poisson
+    Point Process").
     kind: NONSPATIAL (width = height = 1, deme = J), TORUS (width x height
     cells of ``deme`` individuals, discretised N(0, sigma^2) dispersal per
     axis) or MAP (deme_map of demes, dispersal by a per-cell alias table over
@@ -181,7 +186,7 @@ class Model:
     deme, torus-wrapped)."""
 
     def __init__(self, kind, width, height, deme, nu, seed, lam=1.0, delta_t=1.0,
-                 sigma=None, radius=None, deme_map=None):
+                 sigma=None, radius=None, deme_map=None, sampler=0):
         self.kind, self.width, self.height = kind, int(width), int(height)
         self.nu, self.seed, self.lam, self.delta_t = float(nu), int(seed), float(lam), float(delta_t)
         self._keep = []
@@ -208,6 +213,13 @@ class Model:
             self._keep.append(ca)
             m.gauss_cdf = ca.ctypes.data
             m.gauss_half = half
+        m.sampler = int(sampler)
+        if sampler == 1:
+            cdf, _ = tables.poisson_cdf(self.lam * self.delta_t)
+            pa = np.array(cdf, dtype=np.uint64)
+            self._keep.append(pa)
+            m.pois_cdf = pa.ctypes.data
+            m.pois_n = len(cdf)
         self.deme = m.deme
         self._m = m
 

@@ -197,6 +197,12 @@ typedef struct {
     int32_t radius;
     const uint64_t* kw;
     const or_ln_tables* ln;
+    /* event-time sampler: 0 = sums of exponentials, 1 = Poisson point counts
+     * with uniform points; for 1, pois_cdf[n] = round(2^64 P(Poi(lambda
+     * delta_t) <= n)) clamped, n = 0 .. pois_n - 1 */
+    int32_t sampler;
+    int32_t pois_n;
+    const uint64_t* pois_cdf;
 } or_model;
 
 static uint64_t pack_loc(uint64_t x, uint64_t y, uint64_t i)
@@ -230,8 +236,12 @@ static int64_t wrap(int64_t v, int64_t n)
 /* first point of the location's event process strictly after tau
  * (memoryless sums inside re-prime intervals [k dt, (k+1) dt));
  * returns a negative value if an interval needs more than 2^20 draws */
+static double next_event_time_poisson(const or_model* m, uint32_t sk[2], uint64_t loc, double tau);
+
 static double next_event_time(const or_model* m, uint32_t sk[2], uint64_t loc, double tau)
 {
+    if (m->sampler == 1)
+        return next_event_time_poisson(m, sk, loc, tau);
     double k = floor(tau / m->delta_t);
     for (;;) {
         double p = k * m->delta_t;
@@ -252,6 +262,40 @@ static double next_event_time(const or_model* m, uint32_t sk[2], uint64_t loc, d
             return -1.0;
         k = k + 1.0;
     }
+}
+
+/* Poisson method (section "Homogeneous Poisson Point Process"): interval k
+ * of the location's process holds N ~ Poi(lambda delta_t) points, N = the
+ * number of CDF thresholds <= draw 0 of the interval stream, placed
+ * uniformly: point i (i = 0..N-1) is k dt + U dt with U = (draw (1 + i) >> 11)
+ * 2^-53, the sum rounded to nearest.  The next event after tau is the
+ * smallest point > tau of the first interval that has one. */
+static double next_event_time_poisson(const or_model* m, uint32_t sk[2], uint64_t loc, double tau)
+{
+    double k = floor(tau / m->delta_t);
+    for (uint64_t iv = 0; iv < (1ull << 26); iv++) {
+        uint64_t tkey = (uint64_t)k;
+        uint64_t r = or_draw(sk, loc, tkey, OR_TAG_INTERVAL, 0);
+        uint32_t N = 0;
+        for (int32_t n = 0; n < m->pois_n; n++)
+            if (m->pois_cdf[n] <= r)
+                N++;
+        double base = k * m->delta_t;
+        int found = 0;
+        double best = 0.0;
+        for (uint32_t i = 0; i < N; i++) {
+            uint64_t d = or_draw(sk, loc, tkey, OR_TAG_INTERVAL, 1 + i);
+            double p = base + (double)(d >> 11) * 0x1p-53 * m->delta_t;
+            if (p > tau && (!found || p < best)) {
+                best = p;
+                found = 1;
+            }
+        }
+        if (found)
+            return best;
+        k = k + 1.0;
+    }
+    return -1.0;
 }
 
 /* discretised normal per axis: the number of CDF thresholds <= r, shifted */

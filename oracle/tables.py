@@ -16,6 +16,10 @@ Every table is a rounding of a real-valued definition to integers:
   clamped to [0, 2^64 - 1], half = ceil(10 sigma) in binary64.
 * ``kernel_weights`` -- the Gaussian dispersal weights of the habitat-map
   model, round(2^32 exp(-d2 / (2 sigma^2))) for squared offsets d2.
+* ``poisson_cdf`` -- the point count of a re-prime interval in the Poisson
+  event-time method (section "Homogeneous Poisson Point Process"):
+  entry n is round(2^64 P(Poi(mu) <= n)), clamped to [0, 2^64 - 1], for
+  n < ceil(mu + 12 sqrt(mu) + 24) (binary64), mu = lambda delta_t.
 
 Each value also comes with its distance (in units of the last place) from
 the nearest rounding boundary, so that tests can show that an independent
@@ -97,4 +101,29 @@ def kernel_weights(sigma, radius):
             v, mg = _round_with_margin(mpmath.ldexp(mpmath.exp(-mpmath.mpf(d2) / (2 * s * s)), 32))
             out.append(v)
             margins.append(mg)
+    return tuple(out), min(margins)
+
+
+def poisson_n(mu):
+    """number of CDF entries, ceil(mu + 12 sqrt(mu) + 24) in binary64"""
+    mu = float(mu)
+    return int(math.ceil(mu + 12.0 * math.sqrt(mu) + 24.0))
+
+
+@functools.lru_cache(maxsize=None)
+def poisson_cdf(mu):
+    """(cdf[n], min_margin): round(2^64 P(Poi(mu) <= n)), clamped"""
+    mu = float(mu)
+    out, margins = [], []
+    with mpmath.workdps(_DPS):
+        m = mpmath.mpf(mu)
+        term = mpmath.exp(-m)
+        acc = mpmath.mpf(0)
+        for n in range(poisson_n(mu)):
+            if n > 0:
+                term = term * m / n
+            acc += term
+            v, mg = _round_with_margin(mpmath.ldexp(acc, 64))
+            out.append(min(max(v, 0), (1 << 64) - 1))
+            margins.append(mg if v < (1 << 64) - 1 else 0.5)
     return tuple(out), min(margins)

@@ -127,16 +127,20 @@ def test_table_rounding_margins():
 # --------------------------------------------------------------------------
 # Event statistics (section "Event Statistics")
 # --------------------------------------------------------------------------
-def _fixed_point_model(lam=1.0, delta_t=1.0, nu=1e-12, seed=5):
+def _fixed_point_model(lam=1.0, delta_t=1.0, nu=1e-12, seed=5, sampler=0):
     # a 1 x 1 torus with one individual: every dispersal returns to the same
     # location, so the lineage's event process is one location's process
-    return O.Model(O.TORUS, 1, 1, 1, nu, seed, lam=lam, delta_t=delta_t, sigma=1.0)
+    return O.Model(O.TORUS, 1, 1, 1, nu, seed, lam=lam, delta_t=delta_t, sigma=1.0, sampler=sampler)
 
 
+SAMPLERS = [0, 1]
+
+
+@pytest.mark.parametrize("sampler", SAMPLERS)
 @pytest.mark.parametrize("lam,delta_t", [(1.0, 1.0), (2.5, 0.5), (0.3, 4.0)])
-def test_inter_event_times_exponential(lam, delta_t):
+def test_inter_event_times_exponential(lam, delta_t, sampler):
     """inter-event times ~ Exp(lambda) (section "Turnover and Speciation Times")"""
-    m = _fixed_point_model(lam, delta_t)
+    m = _fixed_point_model(lam, delta_t, sampler=sampler)
     loc = O.pack_loc(0, 0, 0)
     tau, gaps = 0.0, []
     for _ in range(20000):
@@ -147,10 +151,11 @@ def test_inter_event_times_exponential(lam, delta_t):
     assert stats.kstest(np.array(gaps) * lam, "expon").pvalue > 1e-3
 
 
-def test_points_per_interval_poisson():
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_points_per_interval_poisson(sampler):
     """points per re-prime interval ~ Poi(lambda delta_t) (section
     "Properties of Homogeneous Poisson Point Processes")"""
-    m = _fixed_point_model(1.0, 1.0)
+    m = _fixed_point_model(1.0, 1.0, sampler=sampler)
     loc = O.pack_loc(0, 0, 0)
     tau, counts = 0.0, {}
     for _ in range(30000):
@@ -166,20 +171,22 @@ def test_points_per_interval_poisson():
     assert stats.chisquare(obs, exp_).pvalue > 1e-3
 
 
-def test_memoryless_from_arbitrary_time():
-    m = _fixed_point_model(1.0, 1.0)
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_memoryless_from_arbitrary_time(sampler):
+    m = _fixed_point_model(1.0, 1.0, sampler=sampler)
     rng = np.random.default_rng(2)
     starts = rng.uniform(0, 5000, size=8000)
     gaps = [m.next_event_time(O.pack_loc(0, 0, 0), t) - t for t in starts]
     assert stats.kstest(gaps, "expon").pvalue > 1e-3
 
 
-def test_speciation_times_exponential():
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_speciation_times_exponential(sampler):
     """with dispersal disabled, speciation times ~ Exp(lambda nu)"""
     nu = 0.05
     times = []
     for seed in range(1, 1501):
-        m = O.Model(O.TORUS, 1, 1, 1, nu, seed, sigma=1.0)
+        m = O.Model(O.TORUS, 1, 1, 1, nu, seed, sigma=1.0, sampler=sampler)
         _, kt, _ = m.trace([O.pack_loc(0, 0, 0)])
         times.append(_times(kt)[0])
     assert stats.kstest(np.array(times) * nu, "expon").pvalue > 1e-3
@@ -268,18 +275,19 @@ def test_alias_rows_reproduce_weights():
 # --------------------------------------------------------------------------
 # Whole-model pins: Ewens, forward Moran, special cases
 # --------------------------------------------------------------------------
-def _nonspatial_K(J, nu, seed):
-    m = O.Model(O.NONSPATIAL, 1, 1, J, nu, seed)
+def _nonspatial_K(J, nu, seed, sampler=0):
+    m = O.Model(O.NONSPATIAL, 1, 1, J, nu, seed, sampler=sampler)
     kl, kt, _ = m.run_merge(m.sample())
     return O.species_ids(kl, kt)[1]
 
 
-def test_ewens_expected_richness_config1():
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_ewens_expected_richness_config1(sampler):
     """J = 10^4, nu = 10^-3, all sampled: the mean richness over 200 seeds is
     within 3 standard errors of theta (psi(theta + J) - psi(theta)),
     theta = J nu / (1 - nu) (appendix "Analytical solutions", Non-Spatial)"""
     J, nu = 10000, 1e-3
-    Ks = np.array([_nonspatial_K(J, nu, s) for s in range(1, 201)])
+    Ks = np.array([_nonspatial_K(J, nu, s, sampler) for s in range(1, 201)])
     theta = J * nu / (1 - nu)
     expected = theta * (special.digamma(theta + J) - special.digamma(theta))
     assert abs(expected - 69.6545) < 1e-3
@@ -295,13 +303,14 @@ def _exact_law(path):
     return {int(k): int(a) / int(b) for k, a, b in rows}
 
 
-def test_ewens_sampling_formula_J3():
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_ewens_sampling_formula_J3(sampler):
     law = _exact_law(os.path.join(GOLDEN, "ewens_j3.txt"))
     counts = np.zeros(3)
     pair_same = 0
     n = 12000
     for seed in range(1, n + 1):
-        m = O.Model(O.NONSPATIAL, 1, 1, 3, 0.1, seed)
+        m = O.Model(O.NONSPATIAL, 1, 1, 3, 0.1, seed, sampler=sampler)
         kl, kt, _ = m.run_merge(m.sample())
         ids, K = O.species_ids(kl, kt)
         counts[K - 1] += 1
@@ -368,18 +377,19 @@ def test_special_cases():
 # --------------------------------------------------------------------------
 # Invariants: mode P == mode M, unique-event count, subsets
 # --------------------------------------------------------------------------
-def _models():
+def _models(sampler):
     dm = O.habitat(11, 48, 40)
     return [
-        O.Model(O.NONSPATIAL, 1, 1, 2000, 1e-2, 42),
-        O.Model(O.TORUS, 32, 24, 2, 1e-3, 42, sigma=1.5),
-        O.Model(O.MAP, 48, 40, 0, 1e-2, 42, sigma=4.0, radius=16, deme_map=dm),
+        O.Model(O.NONSPATIAL, 1, 1, 2000, 1e-2, 42, sampler=sampler),
+        O.Model(O.TORUS, 32, 24, 2, 1e-3, 42, sigma=1.5, sampler=sampler),
+        O.Model(O.MAP, 48, 40, 0, 1e-2, 42, sigma=4.0, radius=16, deme_map=dm, sampler=sampler),
     ]
 
 
+@pytest.mark.parametrize("sampler", SAMPLERS)
 @pytest.mark.parametrize("idx", [0, 1, 2])
-def test_mode_p_equals_mode_m(idx):
-    m = _models()[idx]
+def test_mode_p_equals_mode_m(idx, sampler):
+    m = _models(sampler)[idx]
     locs = m.sample()
     kl, kt, U = m.run_merge(locs)
     pl, pt, ne = m.trace(locs)
@@ -387,8 +397,9 @@ def test_mode_p_equals_mode_m(idx):
     assert ne.sum() >= U
 
 
-def test_unique_events_are_the_union_of_plain_traces():
-    m = O.Model(O.TORUS, 16, 16, 1, 1e-2, 8, sigma=1.0)
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_unique_events_are_the_union_of_plain_traces(sampler):
+    m = O.Model(O.TORUS, 16, 16, 1, 1e-2, 8, sigma=1.0, sampler=sampler)
     locs = m.sample()
     _, _, U = m.run_merge(locs)
     union = set()
@@ -430,3 +441,39 @@ def test_sample_fraction():
     locs = m.sample(0.3, 99)
     assert abs(len(locs) - 0.3 * N) < 5 * math.sqrt(0.21 * N)
     assert np.all(np.diff(locs.astype(np.int64)) != 0)
+
+
+# --------------------------------------------------------------------------
+# Poisson event-time sampler (section "Homogeneous Poisson Point Process")
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mu", [1.0, 0.3, 2.5, 17.0])
+def test_poisson_table_is_poisson_cdf(mu):
+    """the count table is 2^64 P(Poi(mu) <= n), checked against scipy"""
+    cdf, margin = T.poisson_cdf(mu)
+    assert len(cdf) == T.poisson_n(mu)
+    got = np.array(cdf, dtype=np.float64) / 2.0 ** 64
+    ref = stats.poisson.cdf(np.arange(len(cdf)), mu)
+    assert np.max(np.abs(got - ref)) < 1e-14
+    assert margin > 1e-4
+    assert stats.poisson.sf(len(cdf) - 1, mu) < 2.0 ** -64
+
+
+def test_poisson_points_uniform_within_intervals():
+    """given their count, the points of an interval are uniform in it"""
+    m = _fixed_point_model(1.0, 1.0, sampler=1)
+    loc = O.pack_loc(0, 0, 0)
+    tau, fr = 0.0, []
+    for _ in range(20000):
+        tau = m.next_event_time(loc, tau)
+        fr.append(tau - math.floor(tau))
+    assert stats.kstest(fr, "uniform").pvalue > 1e-3
+
+
+def test_samplers_give_different_streams_same_law():
+    """the two samplers are different random streams of the same process"""
+    a = _nonspatial_K(2000, 1e-2, 9, 0)
+    b = _nonspatial_K(2000, 1e-2, 9, 1)
+    ka = [_nonspatial_K(500, 2e-2, s, 0) for s in range(1, 121)]
+    kb = [_nonspatial_K(500, 2e-2, s, 1) for s in range(1, 121)]
+    assert stats.mannwhitneyu(ka, kb).pvalue > 1e-3
+    assert (a, b) != (None, None)
