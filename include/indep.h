@@ -81,7 +81,17 @@ typedef struct {
     const uint8_t* deme_map; /* IND_MAP only: host or device pointer, copied */
     double lambda;           /* turnover rate: events per unit time per lineage */
     double delta_t;          /* re-prime interval length */
+    /* event-time sampler (both give Exp(lambda) inter-event times; they are
+     * different random streams):
+     *  IND_SAMPLER_EXP: points of a re-prime interval are running sums of
+     *    Exp(lambda) draws (section "Memoryless sums of exponentials");
+     *  IND_SAMPLER_POISSON: N ~ Poi(lambda delta_t) points placed uniformly
+     *    in the interval (section "Homogeneous Poisson Point Process");
+     *    requires lambda * delta_t <= 64. */
+    int32_t event_sampler;
 } ind_landscape;
+
+enum { IND_SAMPLER_EXP = 0, IND_SAMPLER_POISSON = 1 };
 
 /* Dispersal (DispersalSampler of section "The Statically Checked Component
  * System"; the intra-deme index is uniform, CoalescenceSampler).
@@ -122,6 +132,8 @@ typedef struct {
     uint32_t dedup;             /* 1: horizon dedup (default); 0: none */
     uint32_t count_unique;      /* 1: count distinct events exactly (slower, for measurement) */
     uint32_t profile;           /* 1: time every advance-kernel launch with CUDA events */
+    uint32_t events_per_visit;  /* events a lane runs on its lineage between warp votes, 1..1024 */
+    uint32_t reserved;
     /* horizon step of a simulation with n active lineages over S indexed
      * locations: lambda * step = max(floor, min(occupancy_step * S / n,
      * events_per_round / n)), floor = tail_events while n < busy_lineages

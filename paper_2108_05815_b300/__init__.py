@@ -17,6 +17,7 @@ import threading
 import numpy as np
 
 NONSPATIAL, TORUS, MAP = 0, 1, 2
+SAMPLER_EXP, SAMPLER_POISSON = 0, 1
 DISPERSAL_UNIFORM, DISPERSAL_GAUSSIAN, DISPERSAL_ALIAS_GAUSSIAN = 0, 1, 2
 
 STATUS = {0: "IND_OK", -1: "IND_ERR_ARG", -2: "IND_ERR_OOM", -3: "IND_ERR_CUDA", -4: "IND_ERR_BUDGET",
@@ -37,7 +38,7 @@ class IndError(RuntimeError):
 class Landscape(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("deme", ctypes.c_uint32), ("deme_map", ctypes.c_void_p), ("lambda_", ctypes.c_double),
-                ("delta_t", ctypes.c_double)]
+                ("delta_t", ctypes.c_double), ("event_sampler", ctypes.c_int32)]
 
 
 class Dispersal(ctypes.Structure):
@@ -57,13 +58,13 @@ class RunStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("block_threads", "blocks_per_sm", "lineages_per_lane",
                                                "rounds_per_check", "use_graph", "dedup", "count_unique",
-                                               "profile")] + \
+                                               "profile", "events_per_visit", "reserved")] + \
                [("events_per_round", ctypes.c_double), ("min_events_per_lineage", ctypes.c_double),
                 ("occupancy_step", ctypes.c_double), ("tail_events", ctypes.c_double),
                 ("busy_lineages", ctypes.c_double)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -182,9 +183,10 @@ def _tuning(kw):
     return t
 
 
-def landscape(kind, width=1, height=1, deme=1, deme_map=None, lam=1.0, delta_t=1.0):
+def landscape(kind, width=1, height=1, deme=1, deme_map=None, lam=1.0, delta_t=1.0, sampler=0):
     L = Landscape()
     L.kind, L.width, L.height, L.deme, L.lambda_, L.delta_t = kind, width, height, deme, lam, delta_t
+    L.event_sampler = sampler
     keep = None
     if deme_map is not None:
         if hasattr(deme_map, "data_ptr"):
@@ -206,9 +208,9 @@ class Simulation:
     """One simulation (sim_create ... sim_destroy)."""
 
     def __init__(self, kind, nu, seed, width=1, height=1, deme=1, sigma=0.0, radius=0, deme_map=None,
-                 lam=1.0, delta_t=1.0, stream=None, tuning=None):
+                 lam=1.0, delta_t=1.0, stream=None, tuning=None, sampler=0):
         use_torch_allocator()
-        L, keep = landscape(kind, width, height, deme, deme_map, lam, delta_t)
+        L, keep = landscape(kind, width, height, deme, deme_map, lam, delta_t, sampler)
         dk = {NONSPATIAL: DISPERSAL_UNIFORM, TORUS: DISPERSAL_GAUSSIAN, MAP: DISPERSAL_ALIAS_GAUSSIAN}[kind]
         D = dispersal(dk, sigma, radius)
         self._h = ctypes.c_void_p()

@@ -39,6 +39,8 @@ void host_ln_tables(uint64_t* L, uint32_t* R, int n, uint64_t* ln2_q64, int64_t*
 int host_gauss_half(double sigma);
 std::vector<uint64_t> host_gauss_cdf(double sigma);
 std::vector<uint64_t> host_kernel_weights(double sigma, int radius);
+int host_poisson_n(double mu);
+std::vector<uint64_t> host_poisson_cdf(double mu);
 }  // namespace indep
 
 using namespace indep;
@@ -156,6 +158,10 @@ struct SimParams {
     uint32_t gauss_n;
     const uint64_t* gauss;     // 2 half discretised-normal CDF thresholds
     const uint16_t* gauss_guide;  // 256 entries: thresholds below (g << 56)
+    int32_t sampler;              // 0: sums of exponentials, 1: Poisson point counts
+    uint32_t pois_n;
+    const uint64_t* pois_cdf;     // round(2^64 P(Poi(lambda dt) <= n))
+    const uint16_t* pois_guide;   // 256 entries
     const uint8_t* deme_map;   // W*H
     const uint32_t* row_of;    // W*H alias row of a cell
     const uint64_t* alias;     // rows x n_off entries: q | alias << 32 | full << 63
@@ -231,6 +237,8 @@ struct BatchDev {
     uint32_t lpl;
     int dedup;
     int count_unique;
+    int need_ln;  // some simulation uses the exponential-sums sampler
+    uint32_t events_per_visit;
 };
 
 // ---------------------------------------------------------------------------
@@ -246,6 +254,10 @@ struct LaneSim {
     double lam;
     bool lam1;
     double horizon;
+    int sampler;
+    uint32_t pois_n;
+    const uint64_t* pois_cdf;
+    const uint16_t* pois_guide;
 };
 
 __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
@@ -262,6 +274,10 @@ __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __rest
     c.dt_log2 = __ldg(&p->dt_log2);
     c.lam = __ldg(&p->lambda);
     c.lam1 = (c.lam == 1.0);
+    c.sampler = __ldg(&p->sampler);
+    c.pois_n = __ldg(&p->pois_n);
+    c.pois_cdf = p->pois_cdf;
+    c.pois_guide = p->pois_guide;
     c.horizon = *(volatile const double*)&S[sim].horizon;
 }
 
@@ -308,7 +324,7 @@ __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const Lane
 // step are independent, so their logarithms overlap, and only the binary64
 // sums run one after another, in the spec's order.
 template <int WIDE>
-__device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+__device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
     for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
@@ -342,13 +358,59 @@ __device__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, co
     return -1.0;
 }
 
+// number of table entries <= r, starting from the guide of r's top 8 bits
+__device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
+                                                 uint32_t n, uint64_t r) {
+    uint32_t idx = __ldg(guide + (r >> 56));
+    while (idx < n && __ldg(t + idx) <= r) ++idx;
+    return idx;
+}
+
+// Poisson method: interval k holds N ~ Poi(lambda dt) points (N = the count
+// of CDF thresholds <= draw 0), point i at k dt + U dt, U = (draw (1 + i)
+// >> 11) 2^-53, the sum rounded to nearest; the next event is the smallest
+// point > tau of the first interval that has one.  The points of an interval
+// are independent of each other, so there is no sequential chain.
+__device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double tau) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
+    const uint64_t scale = (uint64_t)(53 - c.dt_log2) << 52;  // U dt = (r >> 11) 2^(dt_log2 - 53)
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
+        if (k >= (1ull << 52)) return -1.0;
+        const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t best = ~0ull;
+        auto consider = [&](uint64_t r) {
+            const uint64_t q = r >> 11;
+            const double x = q == 0ull ? 0.0
+                                       : __longlong_as_double((long long)((uint64_t)__double_as_longlong(
+                                                                              __ull2double_rn(q)) - scale));
+            const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+            if (pb > tau_b && pb < best) best = pb;
+        };
+        if (N >= 1) consider(b0.hi);
+        for (uint32_t j = 1; 2 * j <= N; ++j) {
+            const u64x2 bj = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+            consider(bj.lo);
+            if (2 * j + 1 <= N) consider(bj.hi);
+        }
+        if (best != ~0ull) return __longlong_as_double((long long)best);
+        ++k;
+    }
+    return -1.0;
+}
+
+template <int WIDE>
+__device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+    return c.sampler == 1 ? next_event_time_poisson(c, loc, tau) : next_event_time_exp<WIDE>(c, loc, tau, ln);
+}
+
 // discretised normal by inversion: -half + #{k : cdf[k] <= r}; the guide
 // gives the count below the start of r's top-8-bit bucket
 __device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
                                               uint32_t n, int32_t half, uint64_t r) {
-    uint32_t idx = __ldg(guide + (r >> 56));
-    while (idx < n && __ldg(t + idx) <= r) ++idx;
-    return (int32_t)idx - half;
+    return (int32_t)guided_count(t, guide, n, r) - half;
 }
 
 // one event at (loc, tau); returns true if the lineage speciated, else
@@ -508,7 +570,8 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     // a block whose first possible claim lies beyond the active lineages has
     // nothing to do (claims go out in order of arrival, at most one per warp)
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
-    const LnC ln = ln_tables_shared(adv_smem);
+    // the logarithm tables are staged only if some simulation sums exponentials
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
 
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
@@ -570,8 +633,10 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
             if (exhausted) break;
             continue;
         }
-        if (has) {
-            if (!(tn <= c.horizon)) {
+        // up to events_per_visit events of the lane's lineage between warp votes
+        for (uint32_t visit = 0; has && visit < B.events_per_visit; ++visit) {
+            // both non-negative: compare the bit patterns (an integer compare)
+            if ((uint64_t)__double_as_longlong(tn) > (uint64_t)__double_as_longlong(c.horizon)) {
                 // at the horizon: write back and enter the dedup
                 L.loc[idx] = loc;
                 L.tn[idx] = tn;
@@ -1167,6 +1232,9 @@ struct ind_sim {
     Pool results;  // outputs
     uint64_t* d_gauss = nullptr;
     uint16_t* d_gauss_guide = nullptr;
+    uint64_t* d_pois = nullptr;
+    uint16_t* d_pois_guide = nullptr;
+    uint32_t pois_n = 0;
     uint32_t gauss_n = 0;
     int gauss_half = 0;
     uint8_t* d_deme = nullptr;
@@ -1271,6 +1339,10 @@ static ind_status batch_build(Batch& b) {
         p.gauss_n = m->gauss_n;
         p.gauss = m->d_gauss;
         p.gauss_guide = m->d_gauss_guide;
+        p.sampler = m->land.event_sampler;
+        p.pois_n = m->pois_n;
+        p.pois_cdf = m->d_pois;
+        p.pois_guide = m->d_pois_guide;
         p.deme_map = m->d_deme;
         p.row_of = m->d_row_of;
         p.alias = m->d_alias;
@@ -1340,7 +1412,10 @@ static ind_status batch_build(Batch& b) {
     d.G = b.d_g;
     d.n_sims = b.n_sims;
     d.lpl = b.tun.lineages_per_lane;
+    d.events_per_visit = b.tun.events_per_visit;
     d.dedup = b.tun.dedup ? 1 : 0;
+    d.need_ln = 0;
+    for (uint32_t si = 0; si < b.n_sims; ++si) d.need_ln |= hp[si].sampler == IND_SAMPLER_EXP ? 1 : 0;
     cudaStream_t s = b.stream;
     CK(cudaMemcpyAsync(b.d_params, hp.data(), sizeof(SimParams) * b.n_sims, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b.d_gid_base, gid_base.data(), sizeof(uint32_t) * b.n_sims, cudaMemcpyHostToDevice, s));
@@ -1640,6 +1715,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->block_threads = 256;
     t->blocks_per_sm = 8;
     t->lineages_per_lane = 4;
+    t->events_per_visit = 8;
     t->rounds_per_check = 16;
     t->use_graph = 1;
     t->dedup = 1;
@@ -1655,6 +1731,7 @@ void ind_default_tuning(ind_tuning* t) {
 static bool tuning_ok(const ind_tuning* t) {
     return t->block_threads >= 64 && t->block_threads <= 512 && t->block_threads % 32 == 0 &&
            t->blocks_per_sm >= 1 && t->blocks_per_sm <= 32 && t->lineages_per_lane >= 1 &&
+           t->events_per_visit >= 1 && t->events_per_visit <= 1024 &&
            t->lineages_per_lane <= 64 && t->rounds_per_check >= 1 && t->rounds_per_check <= 4096 &&
            t->events_per_round >= 1.0 && t->min_events_per_lineage > 0.0 && t->occupancy_step > 0.0 &&
            t->tail_events > 0.0 && t->busy_lineages >= 0.0 && std::isfinite(t->tail_events) &&
@@ -1678,6 +1755,8 @@ static ind_status validate(const ind_landscape* L, const ind_dispersal* D, doubl
     *dt_log2 = pow2_log2(L->delta_t, &ok);
     if (!ok || !(L->delta_t > 0.0)) return IND_ERR_ARG;
     if (!(L->lambda * L->delta_t >= 0x1p-20)) return IND_ERR_ARG;  // bounded interval search
+    if (L->event_sampler != IND_SAMPLER_EXP && L->event_sampler != IND_SAMPLER_POISSON) return IND_ERR_ARG;
+    if (L->event_sampler == IND_SAMPLER_POISSON && !(L->lambda * L->delta_t <= 64.0)) return IND_ERR_ARG;
     if (L->width < 1 || L->height < 1 || L->width > (1u << 20) || L->height > (1u << 20)) return IND_ERR_ARG;
     if (L->kind == IND_NONSPATIAL) {
         if (L->width != 1 || L->height != 1 || L->deme < 1 || L->deme >= (1u << 23)) return IND_ERR_ARG;
@@ -1728,6 +1807,22 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
         delete m;
         return e;
     };
+    if (L->event_sampler == IND_SAMPLER_POISSON) {
+        std::vector<uint64_t> cdf = host_poisson_cdf(L->lambda * L->delta_t);
+        std::vector<uint16_t> guide(256);
+        for (uint32_t g = 0; g < 256; ++g)
+            guide[g] = (uint16_t)(std::lower_bound(cdf.begin(), cdf.end(), (uint64_t)g << 56) - cdf.begin());
+        m->pois_n = (uint32_t)cdf.size();
+        m->d_pois = m->tables.get<uint64_t>(cdf.size());
+        m->d_pois_guide = m->tables.get<uint16_t>(256);
+        if (!m->d_pois || !m->d_pois_guide) return fail(IND_ERR_OOM);
+        if (cudaMemcpyAsync(m->d_pois, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(m->d_pois_guide, guide.data(), 512, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            g_last_cuda_error.store((int)cudaGetLastError());
+            return fail(IND_ERR_CUDA);
+        }
+    }
     if (L->kind == IND_TORUS) {
         std::vector<uint64_t> cdf = host_gauss_cdf(D->sigma);
         m->gauss_half = host_gauss_half(D->sigma);
@@ -2401,6 +2496,10 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         hp.gauss_n = m->gauss_n;
         hp.gauss = m->d_gauss;
         hp.gauss_guide = m->d_gauss_guide;
+        hp.sampler = m->land.event_sampler;
+        hp.pois_n = m->pois_n;
+        hp.pois_cdf = m->d_pois;
+        hp.pois_guide = m->d_pois_guide;
         hp.deme_map = m->d_deme;
         hp.row_of = m->d_row_of;
         hp.alias = m->d_alias;
@@ -2510,8 +2609,10 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     d.G = b.d_g;
     d.n_sims = max_sims;
     d.lpl = b.tun.lineages_per_lane;
+    d.events_per_visit = b.tun.events_per_visit;
     d.dedup = b.tun.dedup ? 1 : 0;
     d.count_unique = 0;  // exact counting is a batch-only measurement mode
+    d.need_ln = 1;       // requests of either sampler may arrive
     auto fail = [&](cudaError_t e) {
         g_last_cuda_error.store((int)e);
         delete sv;

@@ -9,6 +9,8 @@
 //               per-axis discretised normal of section "Normal Dispersal"
 //   kernel      K[d2] = round(2^32 exp(-d2 / (2 sigma^2))): Gaussian weights
 //               of the habitat-map dispersal
+//   Poisson     round(2^64 P(Poi(mu) <= n)), clamped, n < ceil(mu + 12 sqrt(mu)
+//               + 24): point counts of the Poisson event-time sampler
 // binary128 carries about 113 bits, far more than the 64 needed, so ties of
 // the rounding cannot flip (the tables' distance to the rounding boundary is
 // asserted in the test suite).
@@ -60,6 +62,22 @@ std::vector<uint64_t> host_kernel_weights(double sigma, int radius) {
     __float128 s = (__float128)sigma;
     for (int d2 = 0; d2 <= radius * radius; ++d2)
         out[d2] = round_q(ldexpq(expq(-(__float128)d2 / (2 * s * s)), 32));
+    return out;
+}
+
+int host_poisson_n(double mu) { return (int)std::ceil(mu + 12.0 * std::sqrt(mu) + 24.0); }
+
+// round(2^64 P(Poi(mu) <= n)), clamped, n = 0 .. host_poisson_n(mu) - 1
+std::vector<uint64_t> host_poisson_cdf(double mu) {
+    const int n = host_poisson_n(mu);
+    std::vector<uint64_t> out(n);
+    __float128 m = (__float128)mu;
+    __float128 term = expq(-m), acc = 0;
+    for (int i = 0; i < n; ++i) {
+        if (i > 0) term = term * m / (__float128)i;
+        acc += term;
+        out[i] = round_q(ldexpq(acc, 64));
+    }
     return out;
 }
 

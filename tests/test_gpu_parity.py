@@ -29,7 +29,7 @@ def _gpu():
 def gpu_sim(cfg, deme_map=None, tuning=None):
     kw = dict(width=cfg.get("width", 1), height=cfg.get("height", 1), deme=cfg.get("deme", 1),
               sigma=cfg.get("sigma", 0.0), radius=cfg.get("radius", 0), lam=cfg.get("lam", 1.0),
-              delta_t=cfg.get("delta_t", 1.0), tuning=tuning)
+              delta_t=cfg.get("delta_t", 1.0), tuning=tuning, sampler=cfg.get("sampler", 0))
     if cfg["kind"] == W.MAP:
         kw["deme_map"] = deme_map
     return ind.Simulation(cfg["kind"], cfg["nu"], cfg["seed"], **kw)
@@ -38,7 +38,8 @@ def gpu_sim(cfg, deme_map=None, tuning=None):
 def oracle_model(cfg, deme_map=None):
     return O.Model(cfg["kind"], cfg.get("width", 1), cfg.get("height", 1), cfg.get("deme", 1), cfg["nu"],
                    cfg["seed"], lam=cfg.get("lam", 1.0), delta_t=cfg.get("delta_t", 1.0),
-                   sigma=cfg.get("sigma"), radius=cfg.get("radius"), deme_map=deme_map)
+                   sigma=cfg.get("sigma"), radius=cfg.get("radius"), deme_map=deme_map,
+                   sampler=cfg.get("sampler", 0))
 
 
 def run_gpu(cfg, deme_map=None, tuning=None, fraction=1.0, sample_seed=0):
@@ -197,7 +198,9 @@ def test_batch_equals_alone():
             dict(kind=W.NONSPATIAL, width=1, height=1, deme=3, nu=0.5, seed=5),
             dict(kind=W.MAP, width=60, height=60, sigma=4.0, radius=16, nu=1e-2, seed=6),
             dict(kind=W.TORUS, width=20, height=20, deme=4, sigma=1.0, nu=1e-1, seed=7),
-            dict(kind=W.NONSPATIAL, width=1, height=1, deme=1, nu=1e-4, seed=8)]
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=1, nu=1e-4, seed=8),
+            dict(kind=W.TORUS, width=70, height=50, deme=2, sigma=2.0, nu=2e-3, seed=9, sampler=1),
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=5000, nu=1e-3, seed=10, sampler=1)]
     alone = [run_gpu(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
     sims = [gpu_sim(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
     for s in sims:
@@ -257,3 +260,27 @@ def test_config3_full_size_sampled_parity():
     pick = np.random.default_rng(0).choice(g["n"], size=6, replace=False)
     kl, kt, _ = m.trace(locs[pick])
     assert np.array_equal(kl, g["kl"][pick]) and np.array_equal(kt, g["kt"][pick])
+
+
+# --------------------------------------------------------------------------
+# Poisson event-time sampler
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [
+    dict(W.config1(), sampler=1),
+    dict(W.config2(), sampler=1),
+    dict(kind=W.TORUS, width=40, height=30, deme=3, sigma=2.5, nu=3e-3, seed=5, sampler=1, lam=2.5, delta_t=0.5),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=2000, nu=1e-2, seed=7, sampler=1, lam=0.3, delta_t=4.0),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=300, nu=1.0, seed=8, sampler=1),
+    dict(kind=W.TORUS, width=25, height=25, deme=1, sigma=1.0, nu=1e-2, seed=9, sampler=1, lam=40.0, delta_t=1.0),
+])
+def test_poisson_sampler_parity(cfg):
+    assert_same(run_gpu(cfg), run_oracle(cfg))
+
+
+def test_poisson_sampler_map_parity_and_count():
+    dm = O.habitat(21, 64, 64)
+    cfg = dict(kind=W.MAP, width=64, height=64, sigma=4.0, radius=16, nu=5e-3, seed=23, sampler=1)
+    o = run_oracle(cfg, dm)
+    g = run_gpu(cfg, dm, tuning=dict(count_unique=1))
+    assert_same(g, o)
+    assert g["stats"]["unique_events"] == o["U"]
