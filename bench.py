@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="simulations in the batched-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    ap.add_argument("--workload", default="config2", choices=["config2", "batch", "served"])
+    ap.add_argument("--sampler", default="exp", choices=["exp", "poisson"],
+                    help="event-time sampler of the headline (the other is reported beside it)")
+    ap.add_argument("--window", type=float, default=60.0, help="served: arrival window in seconds")
+    ap.add_argument("--plain-subset", type=int, default=32, help="batch: simulations timed one by one")
     return ap.parse_args()
 
 
@@ -144,15 +149,19 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # our implementation
 # --------------------------------------------------------------------------
-def make_sim(ind, seed=42, tuning=None):
+SAMPLER = {"exp": 0, "poisson": 1}
+_sampler = 0
+
+
+def make_sim(ind, seed=42, tuning=None, sampler=None):
     from paper_2108_05815_b300 import workloads as W
     c = W.config2(seed)
     return ind.Simulation(c["kind"], c["nu"], c["seed"], width=c["width"], height=c["height"], deme=c["deme"],
-                          sigma=c["sigma"], tuning=tuning)
+                          sigma=c["sigma"], tuning=tuning, sampler=_sampler if sampler is None else sampler)
 
 
-def unique_events(ind, seed):
-    s = make_sim(ind, seed, tuning=dict(count_unique=1))
+def unique_events(ind, seed, sampler=None):
+    s = make_sim(ind, seed, tuning=dict(count_unique=1), sampler=sampler)
     s.sample()
     assert s.run()
     st = s.stats()
@@ -261,6 +270,28 @@ def run_ours(args, rank, world, local, pg):
     for x in sims:
         x.close()
 
+    # the other event-time sampler on the same workload (same protocol, fewer steps)
+    other = 1 - _sampler
+    U_o, _ = unique_events(ind, 42, sampler=other)
+    so = make_sim(ind, 42, sampler=other)
+    o_ms = []
+    for k in range(args.warmup + max(3, args.steps // 2)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        so.sample()
+        so.run()
+        so.species(out=ids)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            o_ms.append(e0.elapsed_time(e1))
+    so.close()
+    other_line = {"sampler": [n for n, v in SAMPLER.items() if v == other][0], "unique_events_per_step": U_o,
+                  "ms_per_step": sum(o_ms) / len(o_ms), "value": U_o / (sum(o_ms) / len(o_ms) * 1e-3)}
+
     # roofline of the advance kernel (events per launch / its CUDA-event time)
     raw_per_step = raw / args.steps
     events_per_launch = raw / max(adv_n, 1)
@@ -274,7 +305,8 @@ def run_ours(args, rank, world, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "replicas (one independent simulation per GPU)",
+        "config": {"workload": WORKLOAD, "event_sampler": args.sampler,
+                   "parallelism": "replicas (one independent simulation per GPU)",
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "unique_events_per_step": U, "raw_events_per_step": raw_per_step,
                    "species": K, "tuning": ind.default_tuning()},
@@ -292,6 +324,7 @@ def run_ours(args, rank, world, local, pg):
         "batched": {"sims": args.batch, "workload": "config2 replicas, seeds 42..%d" % (41 + args.batch),
                     "unique_events": sum(Us), "batched_events_per_s": sum(Us) / batch_s,
                     "plain_events_per_s": sum(Us) / plain_s, "speedup": plain_s / batch_s},
+        "other_sampler": other_line,
         "gpu_launches": launches, "clocks": clk, "wall_s_timed": t_wall,
     }
     if rank == 0:
@@ -314,6 +347,170 @@ def ops_per_raw_event():
     # per event: one event block (two for Gaussian dispersal), plus the
     # re-prime interval walk: E[blocks] = 1.35, E[draws] = 2.7 at lambda dt = 1
     return 2 * PHILOX_OPS + 1.35 * PHILOX_OPS + 2.7 * EXP_DRAW_OPS + EVENT_FIXED_OPS
+
+
+# --------------------------------------------------------------------------
+# config 4: 256 uneven simulations in one batch
+# --------------------------------------------------------------------------
+def _make_from(ind, c, tuning=None, sampler=0):
+    return ind.Simulation(c["kind"], c["nu"], c["seed"], width=c["width"], height=c["height"], deme=c["deme"],
+                          sigma=c.get("sigma", 0.0), tuning=tuning, sampler=sampler)
+
+
+def run_batch(args, rank, world, local, pg):
+    import torch
+    import paper_2108_05815_b300 as ind
+    from paper_2108_05815_b300 import autotune, build, workloads as W
+    build.build()
+    torch.cuda.set_device(local)
+    specs = W.config4()
+
+    def make_all(specs_, tuning=None):
+        sims = [_make_from(ind, c, tuning, _sampler) for c in specs_]
+        for x in sims:
+            x.sample()
+        return sims
+
+    # exact distinct events of every simulation (untimed counting pass)
+    sims = make_all(specs)
+    st = ind.batch_run(sims, count_unique=1)
+    U = sum(x["unique_events"] for x in st)
+    for x in sims:
+        x.close()
+    # autotuning on a probe of the same batch with short speciation times
+    probe = [dict(c, nu=max(c["nu"], 2e-3)) for c in specs]
+    trials = []
+    tuned, probe_s, n_trials = autotune.tune(lambda: make_all(probe), passes=1, log=trials)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        sims = make_all(specs)
+        ind.batch_run(sims, **tuned)
+        for x in sims:
+            x.close()
+    launches0 = ind.kernel_launches()
+    clocks.start()
+    step_ms, adv_ms, adv_n, raw = [], 0.0, 0, 0
+    for _ in range(args.steps):
+        sims = make_all(specs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ind.batch_run(sims, profile=1, **tuned)
+        for x in sims:
+            x.species()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        adv_ms += st[0]["advance_ms"]
+        adv_n += st[0]["advance_launches"]
+        raw += sum(x["raw_events"] for x in st)
+        for x in sims:
+            x.close()
+    clk = clocks.stop()
+    launches = ind.kernel_launches() - launches0
+    ms = sum(step_ms) / len(step_ms)
+    # the plain path (one simulation per sim_run) on a stratified subset
+    order = sorted(range(len(specs)), key=lambda k: specs[k]["nu"])
+    stride = max(1, len(specs) // args.plain_subset)
+    subset = order[::stride][: args.plain_subset]
+    plain_s = 0.0
+    for k in subset:
+        x = _make_from(ind, specs[k], tuned, _sampler)
+        x.sample()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.run()
+        x.species()
+        torch.cuda.synchronize()
+        plain_s += time.perf_counter() - t0
+        x.close()
+    plain_est_s = plain_s * len(specs) / len(subset)
+    ops = ops_per_raw_event()
+    avg_launch_ms = adv_ms / max(adv_n, 1)
+    ev_per_launch = raw / max(adv_n, 1)
+    achieved = ev_per_launch * ops / (avg_launch_ms * 1e-3) / 1e12
+    peak = torch.cuda.get_device_properties(local).multi_processor_count * INT32_LANES_PER_SM * 2032e6 / 1e12
+    line = {
+        "metric": METRIC, "value": U / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+        "config": {"workload": "config4: 256 simulations in one batch (sizes log-uniform 1e3..1e6, nu log-uniform "
+                               "1e-6..1e-2, half non-spatial, half torus with sigma uniform 1..8; master seed 42)",
+                   "event_sampler": args.sampler, "unique_events_per_step": U, "raw_events_per_step": raw / args.steps,
+                   "tuning": tuned, "autotune": {"trials": n_trials, "probe_seconds": probe_s}},
+        "batched": {"events_per_s": U / (ms * 1e-3), "plain_events_per_s_estimated": U / plain_est_s,
+                    "speedup": plain_est_s / (ms * 1e-3),
+                    "plain": "sim_run one simulation at a time on %d of the 256 (stratified by nu), scaled"
+                             % len(subset)},
+        "roofline": {"bound": "alu", "kernel": "k_advance", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (32-bit integer)", "frac": achieved / peak, "traffic": None,
+                     "events_per_launch": ev_per_launch, "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# config 5: served Poisson arrivals with continuous batching
+# --------------------------------------------------------------------------
+def run_served(args, rank, world, local, pg):
+    import torch
+    import paper_2108_05815_b300 as ind
+    from paper_2108_05815_b300 import build, workloads as W
+    build.build()
+    torch.cuda.set_device(local)
+    reqs = W.config5(window_s=args.window)
+    srv_stream = torch.cuda.Stream()
+    prep_stream = torch.cuda.Stream()
+    srv = ind.Server(150 * 10 ** 9, max_sims=4096, stream=srv_stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sims, lat, arrival, tickets = {}, [], {}, {}
+    nxt, done = 0, 0
+    t0 = time.perf_counter()
+    raw = 0
+    while done < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+            r = reqs[nxt]
+            with torch.cuda.stream(prep_stream):
+                x = _make_from(ind, r, None, _sampler)
+                x.sample(r["fraction"], r["sample_seed"])
+            tk = srv.submit(x)
+            sims[tk] = x
+            arrival[tk] = r["arrival"]
+            nxt += 1
+        fin = srv.step(4)
+        t_now = time.perf_counter() - t0
+        for tk in fin:
+            x = sims.pop(tk)
+            x.species()
+            raw += x.stats()["raw_events"]
+            lat.append(time.perf_counter() - t0 - arrival[tk])
+            x.close()
+            done += 1
+        if not fin and srv.stats()["resident"] == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, min(0.01, reqs[nxt]["arrival"] - t_now)))
+    total = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    line = {
+        "metric": METRIC, "value": raw / total, "unit": "raw events/s", "n_gpus": world, "steps": 1,
+        "warmup": 0, "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
+        "config": {"workload": "config5: Poisson arrivals 50/s over %.0f s, torus side log-uniform 128..4096, deme "
+                               "1..4, fraction 0.01..1, nu log-uniform 1e-7..1e-3, sigma 1..8, HBM budget 150 GB"
+                               % args.window, "requests": len(reqs), "event_sampler": args.sampler},
+        "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat),
+                      "what": "arrival to species identities on the device"},
+        "server": st, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------
@@ -372,8 +569,15 @@ def main():
         if rank == 0:
             run_reference(args, 0, int(os.environ.get("WORLD_SIZE", "1")), 0, None)
         return
+    global _sampler
+    _sampler = SAMPLER[args.sampler]
     rank, world, local, pg = dist_setup(args)
-    run_ours(args, rank, world, local, pg)
+    if args.workload == "batch":
+        run_batch(args, rank, world, local, pg)
+    elif args.workload == "served":
+        run_served(args, rank, world, local, pg)
+    else:
+        run_ours(args, rank, world, local, pg)
     if pg is not None:
         pg.destroy_process_group()
 

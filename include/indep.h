@@ -133,7 +133,7 @@ typedef struct {
     uint32_t count_unique;      /* 1: count distinct events exactly (slower, for measurement) */
     uint32_t profile;           /* 1: time every advance-kernel launch with CUDA events */
     uint32_t events_per_visit;  /* events a lane runs on its lineage between warp votes, 1..1024 */
-    uint32_t reserved;
+    uint32_t coop_lineages;     /* at most this many active lineages: one warp per lineage (0: never) */
     /* horizon step of a simulation with n active lineages over S indexed
      * locations: lambda * step = max(floor, min(occupancy_step * S / n,
      * events_per_round / n)), floor = tail_events while n < busy_lineages

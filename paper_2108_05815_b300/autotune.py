@@ -1,0 +1,95 @@
+"""Autotuner of the engine's launch shape and dedup cadence.
+
+Results are bit-identical for every tuning (the horizon dedup is exact and
+the work distribution only decides which lane runs which lineage), so any
+trial is a valid run and the only objective is time.  The search is a
+coordinate descent from the library's defaults over
+
+  block_threads      advance-kernel threads per block
+  blocks_per_sm      persistent grid size per SM
+  lineages_per_lane  lineages a warp claims per lane at a time (lineages per warp / 32)
+  events_per_visit   events a lane runs between warp votes
+  occupancy_step     dedup cadence while the GPU is full (alpha of the horizon step)
+  tail_events        dedup cadence below busy_lineages (latency-bound phase)
+
+timed on a probe batch the caller builds (typically the real workload with
+short speciation times, so that one trial takes a fraction of a second).
+"""
+import json
+import os
+import time
+
+from . import default_tuning, batch_run
+
+SPACE = {
+    "block_threads": [128, 256, 512],
+    "blocks_per_sm": [2, 4, 8],
+    "lineages_per_lane": [1, 2, 4, 8],
+    "events_per_visit": [1, 8, 32],
+    "occupancy_step": [0.1, 0.25, 0.5, 1.0],
+    "tail_events": [32.0, 128.0, 512.0],
+}
+
+
+def _time_batch(make_sims, tuning, repeats):
+    import torch
+    best = float("inf")
+    for _ in range(repeats):
+        sims = make_sims()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch_run(sims, **tuning)
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+        for s in sims:
+            s.close()
+    return best
+
+
+def tune(make_sims, passes=2, repeats=1, space=None, log=None):
+    """coordinate descent; returns (best tuning dict, best seconds, trials)"""
+    space = space or SPACE
+    cur = {k: v for k, v in default_tuning().items() if k in space}
+    cache = {}
+
+    def measure(cfg):
+        key = tuple(sorted(cfg.items()))
+        if key not in cache:
+            cache[key] = _time_batch(make_sims, dict(cfg), repeats)
+            if log is not None:
+                log.append({"tuning": dict(cfg), "seconds": cache[key]})
+        return cache[key]
+
+    best_t = measure(cur)
+    for _ in range(passes):
+        improved = False
+        for name, values in space.items():
+            for v in values:
+                if v == cur[name]:
+                    continue
+                cand = dict(cur)
+                cand[name] = v
+                t = measure(cand)
+                if t < best_t * 0.98:
+                    best_t, cur, improved = t, cand, True
+        if not improved:
+            break
+    return cur, best_t, len(cache)
+
+
+def cached_tune(key, make_sims, path=None, **kw):
+    """tune once per workload key and remember the result in a JSON file"""
+    path = path or os.path.join(os.path.expanduser("~"), ".cache", "paper_2108_05815_b300", "tuning.json")
+    db = {}
+    if os.path.exists(path):
+        try:
+            db = json.load(open(path))
+        except Exception:
+            db = {}
+    if key in db:
+        return db[key]["tuning"], db[key]["seconds"], 0
+    best, secs, trials = tune(make_sims, **kw)
+    db[key] = {"tuning": best, "seconds": secs}
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    json.dump(db, open(path, "w"), indent=1)
+    return best, secs, trials

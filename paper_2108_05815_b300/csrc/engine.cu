@@ -406,6 +406,103 @@ __device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc
     return c.sampler == 1 ? next_event_time_poisson(c, loc, tau) : next_event_time_exp<WIDE>(c, loc, tau, ln);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative next-event searches (one lineage per warp; every lane
+// returns the same time).  They compute exactly what the one-lane searches
+// compute; the lanes only evaluate draws that the one-lane search may need,
+// ahead of time and side by side.
+// ---------------------------------------------------------------------------
+// Poisson sampler: lane l searches interval k + l (k = floor(tau / dt)); the
+// answer is the smallest point > tau of the lowest interval that has one.
+__device__ double coop_next_poisson(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    const uint64_t scale = (uint64_t)(53 - c.dt_log2) << 52;
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 32; ++round) {
+        const uint64_t k = k0 + 32ull * round + lane;
+        uint64_t best = ~0ull;
+        if (k < (1ull << 52)) {
+            const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+            const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+            const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+            auto consider = [&](uint64_t r) {
+                const uint64_t q = r >> 11;
+                const double x = q == 0ull ? 0.0
+                                           : __longlong_as_double((long long)((uint64_t)__double_as_longlong(
+                                                                                  __ull2double_rn(q)) - scale));
+                const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+                if (pb > tau_b && pb < best) best = pb;
+            };
+            if (N >= 1) consider(b0.hi);
+            for (uint32_t j = 1; 2 * j <= N; ++j) {
+                const u64x2 bj = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+                consider(bj.lo);
+                if (2 * j + 1 <= N) consider(bj.hi);
+            }
+        }
+        const unsigned found = __ballot_sync(0xFFFFFFFFu, best != ~0ull);
+        if (found) return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, best, __ffs(found) - 1));
+        if (k0 + 32ull * round + 32ull >= (1ull << 52)) return -1.0;
+    }
+    return -1.0;
+}
+
+// Sums of exponentials: in each step lanes 0-15 hold draws 16 qa .. 16 qa + 15
+// of interval k and lanes 16-31 draws 0 .. 15 of interval k + 1, all
+// converted side by side; the binary64 running sums then follow the spec's
+// order one draw at a time (shuffled from the lane that holds it).
+__device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
+    uint32_t qa = 0;  // 16-draw groups of interval k already summed
+    double p = 0.0;   // running sum of interval k (valid when qa > 0)
+    for (uint32_t it = 0; it < INTERVAL_LIMIT; ++it) {
+        if (k + 2ull >= (1ull << 52) || qa >= 2u * INTERVAL_BLOCK_LIMIT / 16u) return -1.0;
+        if (qa == 0) p = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const uint64_t end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
+        const uint64_t kk = lane < 16u ? k : k + 1ull;
+        const uint32_t d = lane < 16u ? 16u * qa + lane : lane - 16u;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, kk, d >> 1, TAG_INTERVAL);
+        const double x = exp_draw((d & 1u) ? b.hi : b.lo, ln, c);
+        bool done_k = false;
+        for (uint32_t i = 0; i < 16u; ++i) {
+            p = __dadd_rn(p, __shfl_sync(0xFFFFFFFFu, x, i));
+            const uint64_t pb = (uint64_t)__double_as_longlong(p);
+            if (pb >= end_b) {
+                done_k = true;
+                break;
+            }
+            if (pb > tau_b) return p;
+        }
+        if (!done_k) {  // interval k goes on: its next 16 draws in the next step
+            ++qa;
+            continue;
+        }
+        // interval k + 1 from its first 16 draws (lanes 16-31)
+        double p1 = __longlong_as_double((long long)k_times_pow2_bits(k + 1ull, c.dt_log2));
+        const uint64_t end1_b = k_times_pow2_bits(k + 2ull, c.dt_log2);
+        bool done_k1 = false;
+        for (uint32_t i = 0; i < 16u; ++i) {
+            p1 = __dadd_rn(p1, __shfl_sync(0xFFFFFFFFu, x, 16 + i));
+            const uint64_t pb = (uint64_t)__double_as_longlong(p1);
+            if (pb >= end1_b) {
+                done_k1 = true;
+                break;
+            }
+            if (pb > tau_b) return p1;
+        }
+        if (done_k1) {
+            k += 2ull;
+            qa = 0;
+        } else {  // interval k + 1 needs more than 16 draws: go on from draw 16
+            k += 1ull;
+            qa = 1;
+            p = p1;
+        }
+    }
+    return -1.0;
+}
+
 // discretised normal by inversion: -half + #{k : cdf[k] <= r}; the guide
 // gives the count below the start of r's top-8-bit bucket
 __device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
@@ -672,6 +769,81 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     if (valid) {
         warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
         if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
+    }
+}
+
+// Tail phase: one lineage per warp.  All lanes run the lineage's event
+// (identical values, no divergence) and share its next-event search, which
+// evaluates in parallel the draws a one-lane search would reach one after
+// another.  Lane 0 writes the results.
+template <bool COUNT>
+__global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(&B.G->work_ctr, 1u);
+        idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+        if (idx >= n) break;
+        const uint32_t gid = L.gid[idx];
+        uint64_t loc = L.loc[idx];
+        double tn = L.tn[idx];
+        const uint32_t s = L.sim[idx];
+        LaneSim c;
+        load_lanesim(c, B.P, B.S, s);
+        if (s != cnt_sim) {
+            if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
+                atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                if (COUNT)
+                    atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
+            }
+            ev_raw = ev_unique = 0;
+            cnt_sim = s;
+        }
+        const uint64_t hz = (uint64_t)__double_as_longlong(c.horizon);
+        for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
+            if ((uint64_t)__double_as_longlong(tn) > hz) {
+                if (lane == 0) {
+                    L.loc[idx] = loc;
+                    L.tn[idx] = tn;
+                    if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                }
+                break;
+            }
+            ++ev_raw;
+            if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+            if (do_event(c, B.P, loc, tn)) {
+                if (lane == 0) {
+                    B.key_loc[gid] = loc;
+                    B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                    L.gid[idx] = gid | DONE_BIT;
+                }
+                break;
+            }
+            const double nt = c.sampler == 1 ? coop_next_poisson(c, loc, tn, lane) : coop_next_exp(c, loc, tn, ln, lane);
+            if (nt < 0.0) {
+                if (lane == 0) {
+                    atomicOr(&B.S[c.sim].error, 1u);
+                    atomicOr(&B.G->error, 1u);
+                    B.key_loc[gid] = ~0ull;
+                    B.key_time[gid] = ~0ull;
+                    L.gid[idx] = gid | DONE_BIT;
+                }
+                break;
+            }
+            tn = nt;
+        }
+    }
+    if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
+        atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+        if (COUNT) atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
     }
 }
 
@@ -1295,7 +1467,7 @@ struct Batch {
     uint64_t rounds = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured chunk of rounds per advance variant
     uint32_t graph_rounds[2] = {0, 0};
-    bool wide = false;                               // latency variant of the advance kernel
+    bool wide = false;                               // warp-cooperative (tail) advance kernel
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -1390,11 +1562,15 @@ static ind_status batch_build(Batch& b) {
     }
     d.count_unique = b.tun.count_unique ? 1 : 0;
     if (d.count_unique) {
+        // events of one round, from the horizon-step rule: n * step <=
+        // max(floor n, min(alpha S, events_per_round)) per simulation
         double est = 0;
+        const double fl = std::max(b.tun.tail_events, b.tun.min_events_per_lineage);
         for (uint32_t s = 0; s < b.n_sims; ++s)
-            est += std::max(b.tun.events_per_round, b.tun.min_events_per_lineage * (double)hp[s].n_lineages) + 64.0;
+            est += 1.3 * (fl * (double)hp[s].n_lineages +
+                          std::min(b.tun.occupancy_step * hp[s].n_slots, b.tun.events_per_round)) + 64.0;
         uint64_t ec = 2;
-        while ((double)ec < 3.0 * est && ec < (1ull << 30)) ec <<= 1;
+        while ((double)ec < 2.0 * est && ec < (1ull << 30)) ec <<= 1;
         d.ev_mask = (uint32_t)(ec - 1);
         for (int t = 0; t < 2; ++t) {
             d.ev[t] = P.get<EvSlot>(ec);
@@ -1439,8 +1615,8 @@ static ind_status batch_build(Batch& b) {
     const uint32_t sms = sm_count();
     CK(cudaFuncSetAttribute(k_advance<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
-    CK(cudaFuncSetAttribute(k_advance<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
-    CK(cudaFuncSetAttribute(k_advance<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
     b.cmp_blocks = sms * 4;
@@ -1461,10 +1637,10 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
     if (b.dev.count_unique) {
-        if (b.wide) k_advance<true, 2><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        if (b.wide) k_advance_coop<true><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
         else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
     } else {
-        if (b.wide) k_advance<false, 2><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        if (b.wide) k_advance_coop<false><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
         else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
     }
     CKL();
@@ -1642,7 +1818,8 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
             }
             chunk = (uint32_t)std::min<uint64_t>(chunk, round_budget - done_rounds);
         }
-        b.wide = false;  // the four-draw variant measured slower on B300
+        // few active lineages: the warp-cooperative (latency) variant
+        b.wide = (b.h_g_valid ? b.h_g->n_total : b.n_lin) <= b.tun.coop_lineages;
         ind_status st = batch_rounds(b, chunk);
         if (st != IND_OK) return st;
         done_rounds += chunk;
@@ -1716,6 +1893,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->blocks_per_sm = 8;
     t->lineages_per_lane = 4;
     t->events_per_visit = 8;
+    t->coop_lineages = 4096;
     t->rounds_per_check = 16;
     t->use_graph = 1;
     t->dedup = 1;
@@ -2637,7 +2815,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
     if ((e = cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
-        (e = cudaFuncSetAttribute(k_advance<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
+        (e = cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
         return fail(e);
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
@@ -2694,7 +2872,7 @@ ind_status srv_step(ind_server* sv, uint32_t rounds, uint64_t* finished, uint32_
     if (st != IND_OK) return st;
     // 3. launch the next chunk of rounds on the main stream
     if (sv->n_total > 0) {
-        b.wide = false;
+        b.wide = sv->n_total <= b.tun.coop_lineages;
         st = batch_rounds(b, rounds);
         if (st != IND_OK) return st;
         sv->chunk_in_flight = true;

@@ -164,6 +164,9 @@ TUNINGS = [
     dict(events_per_round=1e9, min_events_per_lineage=1e6),
     dict(busy_lineages=0.0),
     dict(busy_lineages=1e12),
+    dict(coop_lineages=0),              # one lineage per lane throughout
+    dict(coop_lineages=1 << 30),        # one lineage per warp throughout
+    dict(coop_lineages=200, events_per_visit=1, lineages_per_lane=2),
 ]
 
 
@@ -284,3 +287,28 @@ def test_poisson_sampler_map_parity_and_count():
     g = run_gpu(cfg, dm, tuning=dict(count_unique=1))
     assert_same(g, o)
     assert g["stats"]["unique_events"] == o["U"]
+
+
+@pytest.mark.parametrize("coop", [0, 1 << 30])
+@pytest.mark.parametrize("cfg", [
+    dict(W.config1(), sampler=1),
+    dict(kind=W.TORUS, width=40, height=30, deme=3, sigma=2.5, nu=3e-3, seed=5, sampler=1, lam=2.5, delta_t=0.5),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=2000, nu=1e-2, seed=7, lam=0.3, delta_t=4.0),
+    dict(kind=W.TORUS, width=25, height=25, deme=1, sigma=1.0, nu=1e-2, seed=9, lam=40.0, delta_t=1.0),
+    dict(kind=W.TORUS, width=25, height=25, deme=1, sigma=1.0, nu=1e-2, seed=9, sampler=1, lam=40.0),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=700, nu=3e-3, seed=4, lam=0.05, delta_t=2.0),
+])
+def test_cooperative_tail_parity(cfg, coop):
+    """the warp-cooperative advance kernel gives the oracle's results for both
+    samplers, including long and nearly empty re-prime intervals"""
+    o = run_oracle(cfg)
+    g = run_gpu(cfg, tuning=dict(coop_lineages=coop, count_unique=1))
+    assert_same(g, o)
+    assert g["stats"]["unique_events"] == o["U"]
+
+
+def test_cooperative_map_parity():
+    dm = O.habitat(31, 50, 50)
+    for sampler in (0, 1):
+        cfg = dict(kind=W.MAP, width=50, height=50, sigma=3.0, radius=9, nu=8e-3, seed=33, sampler=sampler)
+        assert_same(run_gpu(cfg, dm, tuning=dict(coop_lineages=1 << 30)), run_oracle(cfg, dm))
