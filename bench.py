@@ -199,6 +199,7 @@ def run_ours(args, rank, world, local, pg):
     barrier(pg)
     torch.cuda.synchronize()
     step_ms, lat_ms, adv_ms, adv_n, raw = [], [], 0.0, 0, 0
+    best = None
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -218,6 +219,9 @@ def run_ours(args, rank, world, local, pg):
         adv_ms += st["advance_ms"]
         adv_n += st["advance_launches"]
         raw += st["raw_events"]
+        if st["busiest_launch_ms"] and (best is None or st["busiest_launch_events"] / st["busiest_launch_ms"] >
+                                        best["busiest_launch_events"] / best["busiest_launch_ms"]):
+            best = st
     torch.cuda.synchronize()
     barrier(pg)
     t_wall = time.perf_counter() - t_wall0
@@ -316,6 +320,7 @@ def run_ours(args, rank, world, local, pg):
                      "unit": "Tops/s (32-bit integer)", "frac": achieved / peak, "traffic": None,
                      "ops_per_event": ops_per_event, "events_per_launch": events_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
+                     "busiest_launch": busiest(best or {}, ops_per_event, peak),
                      "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived, see DESIGN.md)"},
         "cpu_baseline": cpu,
         "e2e": {"value": U * world / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -341,12 +346,30 @@ def pct(xs, q):
     return xs[f] + (xs[c] - xs[f]) * (k - f)
 
 
-def ops_per_raw_event():
-    """integer operations per executed event of the workload (spec-derived; the
-    per-event draw counts are those of the exponential and dispersal draws)"""
-    # per event: one event block (two for Gaussian dispersal), plus the
-    # re-prime interval walk: E[blocks] = 1.35, E[draws] = 2.7 at lambda dt = 1
-    return 2 * PHILOX_OPS + 1.35 * PHILOX_OPS + 2.7 * EXP_DRAW_OPS + EVENT_FIXED_OPS
+POINT_OPS = 15            # Poisson sampler: one uniform point (conversion, rounded add, compare)
+COUNT_OPS = 20            # Poisson sampler: guided inversion of the point count
+
+
+def ops_per_raw_event(sampler=None):
+    """integer operations per executed event (spec-derived): the event's own
+    Philox blocks (two for Gaussian dispersal) and bookkeeping, plus the
+    next-event search at lambda dt = 1: sums of exponentials draw on average
+    2.7 exponentials from 1.35 blocks; the Poisson sampler visits 1.6
+    intervals of one block, one count and on average one point each"""
+    sampler = _sampler if sampler is None else sampler
+    event = 2 * PHILOX_OPS + EVENT_FIXED_OPS
+    if sampler == 1:
+        return event + 1.6 * (PHILOX_OPS + COUNT_OPS + 1.0 * POINT_OPS)
+    return event + 1.35 * PHILOX_OPS + 2.7 * EXP_DRAW_OPS
+
+
+def busiest(st, ops, peak):
+    ms, ev = st.get("busiest_launch_ms", 0.0), st.get("busiest_launch_events", 0)
+    if not ms:
+        return None
+    a = ev * ops / (ms * 1e-3) / 1e12
+    return {"events": ev, "ms": ms, "achieved": a, "frac": a / peak,
+            "what": "the advance launch with the highest event rate (throughput-bound phase)"}
 
 
 # --------------------------------------------------------------------------
@@ -391,6 +414,7 @@ def run_batch(args, rank, world, local, pg):
     launches0 = ind.kernel_launches()
     clocks.start()
     step_ms, adv_ms, adv_n, raw = [], 0.0, 0, 0
+    best = None
     for _ in range(args.steps):
         sims = make_all(specs)
         torch.cuda.synchronize()
@@ -406,6 +430,9 @@ def run_batch(args, rank, world, local, pg):
         adv_ms += st[0]["advance_ms"]
         adv_n += st[0]["advance_launches"]
         raw += sum(x["raw_events"] for x in st)
+        if st[0]["busiest_launch_ms"] and (best is None or st[0]["busiest_launch_events"] / st[0]["busiest_launch_ms"]
+                                           > best["busiest_launch_events"] / best["busiest_launch_ms"]):
+            best = st[0]
         for x in sims:
             x.close()
     clk = clocks.stop()
@@ -446,7 +473,8 @@ def run_batch(args, rank, world, local, pg):
                              % len(subset)},
         "roofline": {"bound": "alu", "kernel": "k_advance", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (32-bit integer)", "frac": achieved / peak, "traffic": None,
-                     "events_per_launch": ev_per_launch, "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n},
+                     "events_per_launch": ev_per_launch, "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
+                     "ops_per_event": ops, "busiest_launch": busiest(best or {}, ops, peak)},
         "gpu_launches": launches, "clocks": clk,
     }
     if rank == 0:

@@ -120,6 +120,8 @@ typedef struct {
     double ms_total;        /* wall time of the sim_run calls (host clock) */
     double advance_ms;      /* summed advance-kernel time (profile = 1 only) */
     uint64_t advance_launches; /* advance-kernel launches timed (profile = 1 only) */
+    double busiest_launch_ms;       /* profile = 1: the advance launch with the highest */
+    uint64_t busiest_launch_events; /* event rate of the run: its time and events (all sims) */
 } ind_run_stats;
 
 /* Tuning of the engine.  None of it changes results (bit-identical). */
@@ -144,6 +146,9 @@ typedef struct {
     double occupancy_step;         /* alpha: duplicate work per round stays near alpha / 2 */
     double tail_events;            /* lower bound of lambda x horizon step below busy_lineages */
     double busy_lineages;          /* active lineages that fill the GPU */
+    double max_step_events;        /* upper bound of lambda x horizon step: no round waits long on
+                                      one simulation's few lineages (all resident simulations share
+                                      each round) */
 } ind_tuning;
 
 typedef struct {

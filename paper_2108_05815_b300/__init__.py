@@ -49,7 +49,8 @@ class RunStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("rounds", "raw_events", "unique_events", "culled", "n_sampled",
                                                "n_species", "n_roots")] + \
                [("ms_total", ctypes.c_double), ("advance_ms", ctypes.c_double),
-                ("advance_launches", ctypes.c_uint64)]
+                ("advance_launches", ctypes.c_uint64), ("busiest_launch_ms", ctypes.c_double),
+                ("busiest_launch_events", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -61,7 +62,7 @@ class Tuning(ctypes.Structure):
                                                "profile", "events_per_visit", "coop_lineages")] + \
                [("events_per_round", ctypes.c_double), ("min_events_per_lineage", ctypes.c_double),
                 ("occupancy_step", ctypes.c_double), ("tail_events", ctypes.c_double),
-                ("busy_lineages", ctypes.c_double)]
+                ("busy_lineages", ctypes.c_double), ("max_step_events", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

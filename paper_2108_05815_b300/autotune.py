@@ -11,6 +11,7 @@ coordinate descent from the library's defaults over
   events_per_visit   events a lane runs between warp votes
   occupancy_step     dedup cadence while the GPU is full (alpha of the horizon step)
   tail_events        dedup cadence below busy_lineages (latency-bound phase)
+  coop_lineages      below this many active lineages, one warp per lineage
 
 timed on a probe batch the caller builds (typically the real workload with
 short speciation times, so that one trial takes a fraction of a second).
@@ -28,6 +29,7 @@ SPACE = {
     "events_per_visit": [1, 8, 32],
     "occupancy_step": [0.1, 0.25, 0.5, 1.0],
     "tail_events": [32.0, 128.0, 512.0],
+    "coop_lineages": [0, 1024, 4096, 16384],
 }
 
 

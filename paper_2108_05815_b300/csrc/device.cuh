@@ -149,6 +149,15 @@ __device__ __forceinline__ double q58_to_double(uint64_t q) {
     return __longlong_as_double((long long)(((uint64_t)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// binary64 of q 2^e for q < 2^53 (exact), by integer assembly: keeps the
+// conversion on the integer pipes (B300's FP64 pipe is narrow)
+__device__ __forceinline__ double q53_scaled(uint64_t q, int e) {
+    if (q == 0ull) return 0.0;
+    const int lz = __clzll((long long)q);                 // >= 11
+    const uint64_t mant = q << (lz - 11);                  // bit 52 set
+    return __longlong_as_double((long long)(((uint64_t)(63 - lz + e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+
 // ---------------------------------------------------------------------------
 // exact integer forms of the event-time bookkeeping (delta_t = 2^d)
 // ---------------------------------------------------------------------------

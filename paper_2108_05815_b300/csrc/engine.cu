@@ -177,6 +177,7 @@ struct SimParams {
     double occupancy_step;
     double tail_events;
     double busy_lineages;
+    double max_step_events;
     double n_slots;            // indexed locations of the landscape
 };
 
@@ -205,6 +206,9 @@ struct Globals {
     uint32_t ev_used[2];    // occupied-slot counts of the event-count tables
     uint32_t error;
     uint32_t n_live_sims;
+    unsigned long long* prof_events;  // profile: cumulative raw events after each round of a chunk
+    uint32_t prof_slot;               // round index within the chunk
+    uint32_t prof_n;
 };
 
 struct __align__(16) EvSlot {
@@ -313,7 +317,7 @@ __device__ __forceinline__ double q58_to_double_hw(uint64_t q) {
 }
 
 __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const LaneSim& c) {
-    const double x = q58_to_double_hw(exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+    const double x = q58_to_double(exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3));
     return c.lam1 ? x : __ddiv_rn(x, c.lam);
 }
 
@@ -374,7 +378,6 @@ __device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t,
 __device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double tau) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
-    const uint64_t scale = (uint64_t)(53 - c.dt_log2) << 52;  // U dt = (r >> 11) 2^(dt_log2 - 53)
     for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
         if (k >= (1ull << 52)) return -1.0;
         const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
@@ -382,10 +385,7 @@ __device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double
         const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
         uint64_t best = ~0ull;
         auto consider = [&](uint64_t r) {
-            const uint64_t q = r >> 11;
-            const double x = q == 0ull ? 0.0
-                                       : __longlong_as_double((long long)((uint64_t)__double_as_longlong(
-                                                                              __ull2double_rn(q)) - scale));
+            const double x = q53_scaled(r >> 11, c.dt_log2 - 53);  // U dt, exact
             const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
             if (pb > tau_b && pb < best) best = pb;
         };
@@ -417,7 +417,6 @@ __device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc
 __device__ double coop_next_poisson(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     const uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
-    const uint64_t scale = (uint64_t)(53 - c.dt_log2) << 52;
     for (uint32_t round = 0; round < INTERVAL_LIMIT / 32; ++round) {
         const uint64_t k = k0 + 32ull * round + lane;
         uint64_t best = ~0ull;
@@ -426,10 +425,7 @@ __device__ double coop_next_poisson(const LaneSim& c, uint64_t loc, double tau, 
             const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
             const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
             auto consider = [&](uint64_t r) {
-                const uint64_t q = r >> 11;
-                const double x = q == 0ull ? 0.0
-                                           : __longlong_as_double((long long)((uint64_t)__double_as_longlong(
-                                                                                  __ull2double_rn(q)) - scale));
+                const double x = q53_scaled(r >> 11, c.dt_log2 - 53);  // U dt, exact
                 const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
                 if (pb > tau_b && pb < best) best = pb;
             };
@@ -852,7 +848,7 @@ __device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n) {
     const double dn = (double)n;
     const double floor_ev = dn < p->busy_lineages ? p->tail_events : p->min_events;
     const double per = fmax(floor_ev, fmin(p->occupancy_step * p->n_slots / dn, p->events_per_round / dn));
-    return per / p->lambda;
+    return fmin(per, p->max_step_events) / p->lambda;
 }
 
 __global__ void k_compact(BatchDev B) {
@@ -962,6 +958,20 @@ __global__ void k_compact(BatchDev B) {
         st->horizon = st->horizon + horizon_step(B.P + s, na);
     }
     __syncthreads();
+    if (B.G->prof_events) {
+        __shared__ unsigned long long ev_sum;
+        if (threadIdx.x == 0) ev_sum = 0;
+        __syncthreads();
+        unsigned long long part = 0;
+        for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) part += B.S[s].raw_events;
+        atomicAdd(&ev_sum, part);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t slot = B.G->prof_slot;
+            if (slot < B.G->prof_n) B.G->prof_events[slot] = ev_sum;
+            B.G->prof_slot = slot + 1;
+        }
+    }
     if (threadIdx.x == 0) {
         Globals* G = B.G;
         const uint32_t nt = atomicAdd(&G->n_total_next, 0u);
@@ -1472,6 +1482,11 @@ struct Batch {
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
     uint64_t advance_launches = 0;
+    unsigned long long* d_prof = nullptr;        // profile: cumulative events per round of a chunk
+    std::vector<unsigned long long> h_prof;
+    unsigned long long prof_last = 0;
+    double best_launch_ms = 0.0;                 // the launch with the highest event rate
+    uint64_t best_launch_events = 0;
     uint32_t adv_blocks = 0, adv_threads = 0, cmp_blocks = 0;
     double ms = 0.0;
 
@@ -1529,6 +1544,7 @@ static ind_status batch_build(Batch& b) {
         p.occupancy_step = b.tun.occupancy_step;
         p.tail_events = b.tun.tail_events;
         p.busy_lineages = b.tun.busy_lineages;
+        p.max_step_events = b.tun.max_step_events;
         p.n_slots = (double)m->n_slots;
         gid_base[s] = (uint32_t)lin;
         lin += m->n_sampled;
@@ -1611,6 +1627,15 @@ static ind_status batch_build(Batch& b) {
             CK(cudaEventCreate(&b.ev_start[r]));
             CK(cudaEventCreate(&b.ev_end[r]));
         }
+        b.d_prof = P.get<unsigned long long>(b.tun.rounds_per_check);
+        if (!b.d_prof) return IND_ERR_OOM;
+        Globals hg;
+        memset(&hg, 0, sizeof(hg));
+        hg.prof_events = b.d_prof;
+        hg.prof_n = b.tun.rounds_per_check;
+        CK(cudaMemcpyAsync(&b.d_g->prof_events, &hg.prof_events, sizeof(hg.prof_events), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(&b.d_g->prof_n, &hg.prof_n, sizeof(hg.prof_n), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
     }
     const uint32_t sms = sm_count();
     CK(cudaFuncSetAttribute(k_advance<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
@@ -1636,12 +1661,14 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     const bool prof = b.tun.profile && r < b.ev_start.size();
     const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
+    // shared memory only when some simulation sums exponentials (leaves L1 larger otherwise)
+    const size_t smem = b.dev.need_ln ? LN_SMEM_BYTES : 0;
     if (b.dev.count_unique) {
-        if (b.wide) k_advance_coop<true><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
-        else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        if (b.wide) k_advance_coop<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     } else {
-        if (b.wide) k_advance_coop<false><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
-        else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, LN_SMEM_BYTES, s>>>(b.dev);
+        if (b.wide) k_advance_coop<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     }
     CKL();
     if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));
@@ -1687,11 +1714,28 @@ static ind_status batch_rounds(Batch& b, uint32_t rounds) {
 // after a synchronised chunk: add up the timed advance launches
 static void collect_profile(Batch& b, uint32_t rounds) {
     if (!b.tun.profile) return;
+    if (b.d_prof) {
+        b.h_prof.resize(rounds);
+        if (cudaMemcpy(b.h_prof.data(), b.d_prof, sizeof(unsigned long long) * rounds, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            cudaGetLastError();
+        unsigned int zero = 0;
+        cudaMemcpy(&b.d_g->prof_slot, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    }
     for (uint32_t r = 0; r < rounds && r < b.ev_start.size(); ++r) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, b.ev_start[r], b.ev_end[r]) == cudaSuccess) {
             b.advance_ms += ms;
             b.advance_launches += 1;
+            if (b.d_prof && r < b.h_prof.size()) {
+                const unsigned long long ev = b.h_prof[r] - b.prof_last;
+                b.prof_last = b.h_prof[r];
+                if (ms > 0.f && (b.best_launch_events == 0 ||
+                                 (double)ev / ms > (double)b.best_launch_events / b.best_launch_ms)) {
+                    b.best_launch_events = ev;
+                    b.best_launch_ms = ms;
+                }
+            }
         } else {
             cudaGetLastError();
         }
@@ -1853,6 +1897,8 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
         m->stats.ms_total = b.ms;
         m->stats.advance_ms = b.advance_ms;
         m->stats.advance_launches = b.advance_launches;
+        m->stats.busiest_launch_ms = b.best_launch_ms;
+        m->stats.busiest_launch_events = b.best_launch_events;
     }
     return result;
 }
@@ -1891,7 +1937,7 @@ void ind_default_tuning(ind_tuning* t) {
     memset(t, 0, sizeof(*t));
     t->block_threads = 256;
     t->blocks_per_sm = 8;
-    t->lineages_per_lane = 4;
+    t->lineages_per_lane = 1;
     t->events_per_visit = 8;
     t->coop_lineages = 4096;
     t->rounds_per_check = 16;
@@ -1904,6 +1950,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->occupancy_step = 0.25;
     t->tail_events = 128.0;
     t->busy_lineages = 32768.0;
+    t->max_step_events = 1024.0;
 }
 
 static bool tuning_ok(const ind_tuning* t) {
@@ -1913,6 +1960,7 @@ static bool tuning_ok(const ind_tuning* t) {
            t->lineages_per_lane <= 64 && t->rounds_per_check >= 1 && t->rounds_per_check <= 4096 &&
            t->events_per_round >= 1.0 && t->min_events_per_lineage > 0.0 && t->occupancy_step > 0.0 &&
            t->tail_events > 0.0 && t->busy_lineages >= 0.0 && std::isfinite(t->tail_events) &&
+           t->max_step_events > 0.0 &&
            std::isfinite(t->busy_lineages) &&
            std::isfinite(t->events_per_round) && std::isfinite(t->min_events_per_lineage) &&
            std::isfinite(t->occupancy_step);
@@ -2692,6 +2740,7 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         hp.occupancy_step = b.tun.occupancy_step;
         hp.tail_events = b.tun.tail_events;
         hp.busy_lineages = b.tun.busy_lineages;
+        hp.max_step_events = b.tun.max_step_events;
         hp.n_slots = (double)m->n_slots;
         SimState hs;
         memset(&hs, 0, sizeof(hs));
@@ -2702,7 +2751,7 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
             const double dn = (double)std::max<uint32_t>(n, 1u);
             const double floor_ev = dn < hp.busy_lineages ? hp.tail_events : hp.min_events;
             const double per = std::max(floor_ev, std::min(hp.occupancy_step * hp.n_slots / dn, hp.events_per_round / dn));
-            hs.horizon = per / hp.lambda;
+            hs.horizon = std::min(per, hp.max_step_events) / hp.lambda;
         }
         CK(cudaMemcpyAsync(b.d_params + slot, &hp, sizeof(hp), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(b.d_state + slot, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
@@ -2749,7 +2798,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.pool.stream = b.scratch.stream = s;
     sv->budget = budget;
     sv->s_cap = max_sims;
-    sv->n_cap = (uint32_t)std::min<uint64_t>(budget / 156ull, (1ull << 30));
+    sv->n_cap = (uint32_t)std::min<uint64_t>(budget / 156ull, (1ull << 29));
     b.n_sims = max_sims;
     const uint32_t n = std::max<uint32_t>(sv->n_cap, 1u);
     Pool& P = b.pool;

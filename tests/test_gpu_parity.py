@@ -167,6 +167,7 @@ TUNINGS = [
     dict(coop_lineages=0),              # one lineage per lane throughout
     dict(coop_lineages=1 << 30),        # one lineage per warp throughout
     dict(coop_lineages=200, events_per_visit=1, lineages_per_lane=2),
+    dict(max_step_events=3.0, tail_events=8.0),
 ]
 
 
