@@ -136,6 +136,10 @@ typedef struct {
     uint32_t profile;           /* 1: time every advance-kernel launch with CUDA events */
     uint32_t events_per_visit;  /* events a lane runs on its lineage between warp votes, 1..1024 */
     uint32_t coop_lineages;     /* at most this many active lineages: one warp per lineage (0: never) */
+    uint32_t advance_variant;   /* more active lineages: 1 (default) = one lineage per lane, events in a
+                                   loop; 0 = convergent state machine (one Philox block per lane per step,
+                                   kept as an option: slower on B300 on every workload measured) */
+    uint32_t reserved;
     /* horizon step of a simulation with n active lineages over S indexed
      * locations: lambda * step = max(floor, min(occupancy_step * S / n,
      * events_per_round / n)), floor = tail_events while n < busy_lineages

@@ -59,13 +59,14 @@ class RunStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("block_threads", "blocks_per_sm", "lineages_per_lane",
                                                "rounds_per_check", "use_graph", "dedup", "count_unique",
-                                               "profile", "events_per_visit", "coop_lineages")] + \
+                                               "profile", "events_per_visit", "coop_lineages",
+                                               "advance_variant", "reserved")] + \
                [("events_per_round", ctypes.c_double), ("min_events_per_lineage", ctypes.c_double),
                 ("occupancy_step", ctypes.c_double), ("tail_events", ctypes.c_double),
                 ("busy_lineages", ctypes.c_double), ("max_step_events", ctypes.c_double)]
 
     def as_dict(self):
-        return {n: getattr(self, n) for n, _ in self._fields_}
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
 
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

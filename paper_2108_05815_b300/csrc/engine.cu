@@ -506,6 +506,39 @@ __device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, co
     return (int32_t)guided_count(t, guide, n, r) - half;
 }
 
+// dispersal target from the event stream's draws 1, 2, 3 (draw 0 decided
+// speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index);
+// map d1 (alias column and threshold), d2 (deme index)
+__device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* __restrict__ P, uint64_t loc,
+                                            uint64_t d1, uint64_t d2, uint64_t d3) {
+    if (c.kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
+    const SimParams* p = P + c.sim;
+    const uint32_t x = loc_x(loc), y = loc_y(loc);
+    if (c.kind == KIND_TORUS) {
+        const uint64_t* g = p->gauss;
+        const uint16_t* gd = p->gauss_guide;
+        const uint32_t gn = __ldg(&p->gauss_n);
+        const int32_t gh = __ldg(&p->gauss_half);
+        const uint32_t tx = wrap_add(x, gauss_step(g, gd, gn, gh, d1), c.W);
+        const uint32_t ty = wrap_add(y, gauss_step(g, gd, gn, gh, d2), c.H);
+        const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
+        return pack_loc(tx, ty, ti);
+    }
+    // habitat map: alias row of the origin cell
+    const uint32_t n_off = __ldg(&p->n_off);
+    const uint32_t row = __ldg(p->row_of + (size_t)y * c.W + x);
+    const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
+    const uint64_t e = __ldg(p->alias + (size_t)row * n_off + col);
+    const uint32_t u = (uint32_t)d1;
+    const uint32_t o = ((e >> 63) != 0 || u < (uint32_t)e) ? col : (uint32_t)((e >> 32) & 0xFFFFu);
+    const int8_t* off = p->off;
+    const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+    const uint32_t tx = wrap_add(x, dx, c.W);
+    const uint32_t ty = wrap_add(y, dy, c.H);
+    const uint32_t d = __ldg(p->deme_map + (size_t)ty * c.W + tx);
+    return pack_loc(tx, ty, umulhi64(d2, d));
+}
+
 // one event at (loc, tau); returns true if the lineage speciated, else
 // moves loc to the dispersal target
 __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
@@ -514,37 +547,12 @@ __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __re
     const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
     if (c.kind == KIND_NONSPATIAL) {
         if ((b0.lo >> 11) < c.nu_thr) return true;
-        loc = pack_loc(0, 0, umulhi64(b0.hi, c.D));
+        loc = disperse(c, P, loc, b0.hi, 0ull, 0ull);
         return false;
     }
     const u64x2 b1 = stream_block(c.sk0, c.sk1, loc, tk, 1, TAG_EVENT);
     if ((b0.lo >> 11) < c.nu_thr) return true;
-    const SimParams* p = P + c.sim;
-    const uint32_t x = loc_x(loc), y = loc_y(loc);
-    if (c.kind == KIND_TORUS) {
-        const uint64_t* g = p->gauss;
-        const uint16_t* gd = p->gauss_guide;
-        const uint32_t gn = __ldg(&p->gauss_n);
-        const int32_t gh = __ldg(&p->gauss_half);
-        const uint32_t tx = wrap_add(x, gauss_step(g, gd, gn, gh, b0.hi), c.W);
-        const uint32_t ty = wrap_add(y, gauss_step(g, gd, gn, gh, b1.lo), c.H);
-        const uint64_t ti = c.D > 1 ? umulhi64(b1.hi, c.D) : 0ull;
-        loc = pack_loc(tx, ty, ti);
-        return false;
-    }
-    // habitat map: alias row of the origin cell
-    const uint32_t n_off = __ldg(&p->n_off);
-    const uint32_t row = __ldg(p->row_of + (size_t)y * c.W + x);
-    const uint32_t col = (uint32_t)(((b0.hi >> 32) * (uint64_t)n_off) >> 32);
-    const uint64_t e = __ldg(p->alias + (size_t)row * n_off + col);
-    const uint32_t u = (uint32_t)b0.hi;
-    const uint32_t o = ((e >> 63) != 0 || u < (uint32_t)e) ? col : (uint32_t)((e >> 32) & 0xFFFFu);
-    const int8_t* off = p->off;
-    const int32_t dx = off[2 * o], dy = off[2 * o + 1];
-    const uint32_t tx = wrap_add(x, dx, c.W);
-    const uint32_t ty = wrap_add(y, dy, c.H);
-    const uint32_t d = __ldg(p->deme_map + (size_t)ty * c.W + tx);
-    loc = pack_loc(tx, ty, umulhi64(b1.lo, d));
+    loc = disperse(c, P, loc, b0.hi, b1.lo, b1.hi);
     return false;
 }
 
@@ -768,8 +776,218 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     }
 }
 
-// Tail phase: one lineage per warp.  All lanes run the lineage's event
-// (identical values, no divergence) and share its next-event search, which
+// Throughput phase, convergent form: every iteration each lane computes
+// exactly one Philox block whose counter depends on the lane's state (event
+// block 0 or 1, or the next block of its re-prime interval search), so the
+// bulk of the instructions runs with all lanes active; only the short
+// state-specific processing diverges.  Lanes refill from the warp's chunk
+// whenever they fall idle.  Same draws, same order, same results as the
+// one-lane-per-lineage loop above.
+constexpr uint32_t SM_IDLE = 0, SM_EVENT0 = 1, SM_EVENT1 = 2, SM_SEARCH = 3;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    const uint32_t chunk = 32u * B.lpl;
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    uint32_t chunk_next = 0, chunk_end = 0;  // warp-uniform
+    bool exhausted = false;
+
+    uint32_t st = SM_IDLE, idx = 0, gid = 0;
+    uint64_t loc = 0;
+    double tn = 0.0;
+    LaneSim c;
+    memset(&c, 0, sizeof(c));
+    c.sim = 0xFFFFFFFFu;
+    c.lam = 1.0;
+    c.lam1 = true;
+    uint64_t hz = 0;                          // horizon bits of the lane's simulation
+    uint64_t k = 0, tau_b = 0, end_b = 0, best = ~0ull, e0hi = 0;
+    uint32_t j = 0, N = 0, iv = 0;
+    double p = 0.0, base = 0.0;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+
+    auto fail = [&]() {
+        atomicOr(&B.S[c.sim].error, 1u);
+        atomicOr(&B.G->error, 1u);
+        B.key_loc[gid] = ~0ull;
+        B.key_time[gid] = ~0ull;
+        L.gid[idx] = gid | DONE_BIT;
+        st = SM_IDLE;
+    };
+    auto start_interval = [&]() {
+        base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
+        p = base;
+        best = ~0ull;
+        N = 0;
+        j = 0;
+        if (k >= (1ull << 52) || iv >= INTERVAL_LIMIT) fail();
+    };
+    auto begin_search = [&]() {
+        tau_b = (uint64_t)__double_as_longlong(tn);
+        k = floor_div_pow2(tau_b, c.dt_log2);
+        iv = 0;
+        st = SM_SEARCH;
+        start_interval();
+    };
+    auto found = [&](double v) {
+        tn = v;
+        if ((uint64_t)__double_as_longlong(tn) > hz) {  // beyond the horizon: park the lineage
+            L.loc[idx] = loc;
+            L.tn[idx] = tn;
+            if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+            st = SM_IDLE;
+        } else {
+            st = SM_EVENT0;
+        }
+    };
+
+    for (;;) {
+        // refill idle lanes from the warp's chunk
+        const unsigned need = __ballot_sync(0xFFFFFFFFu, st == SM_IDLE);
+        if (need) {
+            if (chunk_next >= chunk_end && !exhausted) {
+                uint32_t b0 = 0;
+                if (lane == 0) b0 = atomicAdd(&B.G->work_ctr, chunk);
+                b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                if (b0 >= n) {
+                    exhausted = true;
+                } else {
+                    chunk_next = b0;
+                    chunk_end = min(b0 + chunk, n);
+                }
+            }
+            if (chunk_next < chunk_end) {
+                const uint32_t avail = chunk_end - chunk_next;
+                const uint32_t rank = __popc(need & lt_mask);
+                if (st == SM_IDLE && rank < avail) {
+                    idx = chunk_next + rank;
+                    gid = L.gid[idx];
+                    loc = L.loc[idx];
+                    tn = L.tn[idx];
+                    const uint32_t s = L.sim[idx];
+                    if (s != c.sim) {
+                        if (cnt_sim != 0xFFFFFFFFu && (ev_raw | ev_unique)) {
+                            atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                            if (COUNT)
+                                atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events,
+                                          (unsigned long long)ev_unique);
+                            ev_raw = ev_unique = 0;
+                        }
+                        load_lanesim(c, B.P, B.S, s);
+                        cnt_sim = s;
+                        hz = (uint64_t)__double_as_longlong(c.horizon);
+                    }
+                    if ((uint64_t)__double_as_longlong(tn) > hz) {
+                        if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);  // already at the horizon
+                    } else {
+                        st = SM_EVENT0;
+                    }
+                }
+                chunk_next += min(avail, (uint32_t)__popc(need));
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, st != SM_IDLE)) {
+            if (exhausted) break;
+            continue;
+        }
+        // one Philox block per lane, its counter chosen by the lane's state
+        const bool ev = st == SM_EVENT0 || st == SM_EVENT1;
+        const uint64_t tkey = ev ? (uint64_t)__double_as_longlong(tn) : k;
+        const uint32_t jj = ev ? (st == SM_EVENT1 ? 1u : 0u) : j;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, tkey, jj, ev ? TAG_EVENT : TAG_INTERVAL);
+        // the two exponentials of the block, when some lane of the warp sums them
+        double x0 = 0.0, x1 = 0.0;
+        if (__any_sync(0xFFFFFFFFu, st == SM_SEARCH && c.sampler == 0)) {
+            x0 = exp_draw(b.lo, ln, c);
+            x1 = exp_draw(b.hi, ln, c);
+        }
+        if (st == SM_EVENT0) {
+            ++ev_raw;
+            if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+            if ((b.lo >> 11) < c.nu_thr) {
+                B.key_loc[gid] = loc;
+                B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                L.gid[idx] = gid | DONE_BIT;
+                st = SM_IDLE;
+            } else if (c.kind == KIND_NONSPATIAL) {
+                loc = disperse(c, B.P, loc, b.hi, 0ull, 0ull);
+                begin_search();
+            } else {
+                e0hi = b.hi;
+                st = SM_EVENT1;
+            }
+        } else if (st == SM_EVENT1) {
+            loc = disperse(c, B.P, loc, e0hi, b.lo, b.hi);
+            begin_search();
+        } else if (st == SM_SEARCH) {
+            if (c.sampler == 0) {
+                // sums of exponentials: draws 2j and 2j + 1 of interval k
+                int r = 0;
+                p = __dadd_rn(p, x0);
+                uint64_t pb = (uint64_t)__double_as_longlong(p);
+                r = pb >= end_b ? 2 : (pb > tau_b ? 1 : 0);
+                if (r == 0) {
+                    p = __dadd_rn(p, x1);
+                    pb = (uint64_t)__double_as_longlong(p);
+                    r = pb >= end_b ? 2 : (pb > tau_b ? 1 : 0);
+                }
+                if (r == 1) {
+                    found(p);
+                } else if (r == 2) {
+                    ++k;
+                    ++iv;
+                    start_interval();
+                } else if (++j >= INTERVAL_BLOCK_LIMIT) {
+                    fail();
+                }
+            } else {
+                // Poisson points: block j holds draws 2j, 2j + 1; draw 0 is the count
+                auto consider = [&](uint64_t r) {
+                    const double x = q53_scaled(r >> 11, c.dt_log2 - 53);
+                    const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+                    if (pb > tau_b && pb < best) best = pb;
+                };
+                if (j == 0) {
+                    N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b.lo);
+                    if (N >= 1) consider(b.hi);
+                } else {
+                    if (2u * j - 1u < N) consider(b.lo);
+                    if (2u * j < N) consider(b.hi);
+                }
+                if (2u * j + 1u >= N) {
+                    if (best != ~0ull) {
+                        found(__longlong_as_double((long long)best));
+                    } else {
+                        ++k;
+                        ++iv;
+                        start_interval();
+                    }
+                } else {
+                    ++j;
+                }
+            }
+        }
+    }
+    // flush the event counters, aggregated over lanes of the same simulation
+    const bool valid = cnt_sim != 0xFFFFFFFFu;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+        warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
+        if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
+    }
+}
+
+
 // evaluates in parallel the draws a one-lane search would reach one after
 // another.  Lane 0 writes the results.
 template <bool COUNT>
@@ -1642,6 +1860,8 @@ static ind_status batch_build(Batch& b) {
     CK(cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance_sm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
     b.cmp_blocks = sms * 4;
@@ -1663,11 +1883,14 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
     // shared memory only when some simulation sums exponentials (leaves L1 larger otherwise)
     const size_t smem = b.dev.need_ln ? LN_SMEM_BYTES : 0;
+    const bool conv = b.tun.advance_variant == 0;  // convergent state machine or one-lane loop
     if (b.dev.count_unique) {
         if (b.wide) k_advance_coop<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     } else {
         if (b.wide) k_advance_coop<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     }
     CKL();
@@ -1940,6 +2163,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->lineages_per_lane = 1;
     t->events_per_visit = 8;
     t->coop_lineages = 4096;
+    t->advance_variant = 1;
     t->rounds_per_check = 16;
     t->use_graph = 1;
     t->dedup = 1;
@@ -1956,7 +2180,7 @@ void ind_default_tuning(ind_tuning* t) {
 static bool tuning_ok(const ind_tuning* t) {
     return t->block_threads >= 64 && t->block_threads <= 512 && t->block_threads % 32 == 0 &&
            t->blocks_per_sm >= 1 && t->blocks_per_sm <= 32 && t->lineages_per_lane >= 1 &&
-           t->events_per_visit >= 1 && t->events_per_visit <= 1024 &&
+           t->events_per_visit >= 1 && t->events_per_visit <= 1024 && t->advance_variant <= 1 &&
            t->lineages_per_lane <= 64 && t->rounds_per_check >= 1 && t->rounds_per_check <= 4096 &&
            t->events_per_round >= 1.0 && t->min_events_per_lineage > 0.0 && t->occupancy_step > 0.0 &&
            t->tail_events > 0.0 && t->busy_lineages >= 0.0 && std::isfinite(t->tail_events) &&
@@ -2864,7 +3088,8 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
     if ((e = cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
-        (e = cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
+        (e = cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
+        (e = cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
         return fail(e);
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;

@@ -168,6 +168,8 @@ TUNINGS = [
     dict(coop_lineages=1 << 30),        # one lineage per warp throughout
     dict(coop_lineages=200, events_per_visit=1, lineages_per_lane=2),
     dict(max_step_events=3.0, tail_events=8.0),
+    dict(advance_variant=0, coop_lineages=0),   # convergent state machine throughout
+    dict(advance_variant=1, coop_lineages=0),   # one-lane loop throughout
 ]
 
 
@@ -288,6 +290,16 @@ def test_poisson_sampler_map_parity_and_count():
     g = run_gpu(cfg, dm, tuning=dict(count_unique=1))
     assert_same(g, o)
     assert g["stats"]["unique_events"] == o["U"]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_advance_variants_match_oracle(variant):
+    for cfg in [dict(W.config1(), sampler=1), dict(kind=W.TORUS, width=60, height=50, deme=2, sigma=3.0, nu=2e-3,
+                                                   seed=12, lam=40.0), dict(W.config2())]:
+        o = run_oracle(cfg)
+        g = run_gpu(cfg, tuning=dict(advance_variant=variant, coop_lineages=0, count_unique=1))
+        assert_same(g, o)
+        assert g["stats"]["unique_events"] == o["U"]
 
 
 @pytest.mark.parametrize("coop", [0, 1 << 30])
