@@ -189,10 +189,12 @@ __host__ __device__ __forceinline__ uint32_t loc_i(uint64_t l) { return (uint32_
 
 __device__ __forceinline__ uint32_t wrap_add(uint32_t x, int32_t d, uint32_t n) {
     // (x + d) mod n for |d| < 2^24, x < n <= 2^20
-    int32_t v = (int32_t)x + d;
+    const int32_t v = (int32_t)x + d;
     if ((uint32_t)v < n) return (uint32_t)v;
-    v %= (int32_t)n;
-    return (uint32_t)(v < 0 ? v + (int32_t)n : v);
+    const int32_t w = v < 0 ? v + (int32_t)n : v - (int32_t)n;  // one lap
+    if ((uint32_t)w < n) return (uint32_t)w;
+    const int32_t r = v % (int32_t)n;
+    return (uint32_t)(r < 0 ? r + (int32_t)n : r);
 }
 
 // number of table entries <= r (table nondecreasing, length n)

@@ -145,6 +145,12 @@ constexpr uint32_t DONE_BIT = 0x80000000u;
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr uint32_t INTERVAL_BLOCK_LIMIT = 1u << 19;  // 2^20 draws per re-prime interval
 constexpr uint32_t INTERVAL_LIMIT = 1u << 26;        // empty intervals crossed in one search
+// inverse-CDF guides: one entry per 2^-12 of the draw's range (its top 12
+// bits) holding the number of thresholds <= the bucket's first value, with
+// GUIDE_SCAN set when a threshold falls inside the bucket
+constexpr int GUIDE_BITS = 12;
+constexpr uint32_t GUIDE_N = 1u << GUIDE_BITS;
+constexpr uint32_t GUIDE_SCAN = 0x80000000u;
 
 struct SimParams {
     int32_t kind;
@@ -157,11 +163,11 @@ struct SimParams {
     int32_t gauss_half;
     uint32_t gauss_n;
     const uint64_t* gauss;     // 2 half discretised-normal CDF thresholds
-    const uint16_t* gauss_guide;  // 256 entries: thresholds below (g << 56)
+    const uint32_t* gauss_guide;  // GUIDE_N entries
     int32_t sampler;              // 0: sums of exponentials, 1: Poisson point counts
     uint32_t pois_n;
     const uint64_t* pois_cdf;     // round(2^64 P(Poi(lambda dt) <= n))
-    const uint16_t* pois_guide;   // 256 entries
+    const uint32_t* pois_guide;   // GUIDE_N entries
     const uint8_t* deme_map;   // W*H
     const uint32_t* row_of;    // W*H alias row of a cell
     const uint64_t* alias;     // rows x n_off entries: q | alias << 32 | full << 63
@@ -170,7 +176,7 @@ struct SimParams {
     uint32_t n_lineages;
     uint64_t slot_base;        // first global slot index of this simulation
     uint32_t gid_base;         // first global lineage id of this simulation
-    uint32_t pad;
+    uint32_t coop_short;       // lambda dt <= 2: the warp-cooperative searches look 4 intervals ahead
     const uint64_t* sample_loc;  // n_lineages sampled locations
     double events_per_round;
     double min_events;
@@ -259,9 +265,14 @@ struct LaneSim {
     bool lam1;
     double horizon;
     int sampler;
+    bool coop_short;
     uint32_t pois_n;
     const uint64_t* pois_cdf;
-    const uint16_t* pois_guide;
+    const uint32_t* pois_guide;
+    int32_t gauss_half;
+    uint32_t gauss_n;
+    const uint64_t* gauss;
+    const uint32_t* gauss_guide;
 };
 
 __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
@@ -282,6 +293,11 @@ __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __rest
     c.pois_n = __ldg(&p->pois_n);
     c.pois_cdf = p->pois_cdf;
     c.pois_guide = p->pois_guide;
+    c.coop_short = __ldg(&p->coop_short) != 0u;
+    c.gauss_half = __ldg(&p->gauss_half);
+    c.gauss_n = __ldg(&p->gauss_n);
+    c.gauss = p->gauss;
+    c.gauss_guide = p->gauss_guide;
     c.horizon = *(volatile const double*)&S[sim].horizon;
 }
 
@@ -316,9 +332,19 @@ __device__ __forceinline__ double q58_to_double_hw(uint64_t q) {
     return __longlong_as_double((long long)(b - (58ull << 52)));
 }
 
+// Exp(lambda) draw.  LAM1 (lambda = 1) is a template argument rather than a
+// select: given both operands the compiler evaluates the binary64 division
+// even where it is not used, on the latency chain and on B300's narrow FP64
+// pipe.  Callers branch on c.lam1 once per search.
+// the division out of line, for code whose lanes mix lambdas: a call is
+// not evaluated speculatively
+__device__ __noinline__ double div_rn_call(double x, double y) { return __ddiv_rn(x, y); }
+
+template <bool LAM1>
 __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const LaneSim& c) {
     const double x = q58_to_double(exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3));
-    return c.lam1 ? x : __ddiv_rn(x, c.lam);
+    if (LAM1) return x;
+    return __ddiv_rn(x, c.lam);
 }
 
 // first point of loc's event process strictly after tau; negative on overflow.
@@ -327,7 +353,7 @@ __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const Lane
 // blocks (2 WIDE draws) are generated and converted together; the draws of a
 // step are independent, so their logarithms overlap, and only the binary64
 // sums run one after another, in the spec's order.
-template <int WIDE>
+template <int WIDE, bool LAM1>
 __device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
@@ -341,8 +367,8 @@ __device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau
 #pragma unroll
             for (int w = 0; w < WIDE; ++w) {
                 const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
-                x[2 * w] = exp_draw(b.lo, ln, c);
-                x[2 * w + 1] = exp_draw(b.hi, ln, c);
+                x[2 * w] = exp_draw<LAM1>(b.lo, ln, c);
+                x[2 * w + 1] = exp_draw<LAM1>(b.hi, ln, c);
             }
 #pragma unroll
             for (int d = 0; d < 2 * WIDE; ++d) {
@@ -362,11 +388,14 @@ __device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau
     return -1.0;
 }
 
-// number of table entries <= r, starting from the guide of r's top 8 bits
-__device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
+// number of table entries <= r: the guide entry of r's bucket, and a scan
+// of the table only where a threshold falls inside the bucket
+__device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t, const uint32_t* __restrict__ guide,
                                                  uint32_t n, uint64_t r) {
-    uint32_t idx = __ldg(guide + (r >> 56));
-    while (idx < n && __ldg(t + idx) <= r) ++idx;
+    const uint32_t e = __ldg(guide + (r >> (64 - GUIDE_BITS)));
+    uint32_t idx = e & ~GUIDE_SCAN;
+    if (e & GUIDE_SCAN)
+        while (idx < n && __ldg(t + idx) <= r) ++idx;
     return idx;
 }
 
@@ -403,7 +432,8 @@ __device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double
 
 template <int WIDE>
 __device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
-    return c.sampler == 1 ? next_event_time_poisson(c, loc, tau) : next_event_time_exp<WIDE>(c, loc, tau, ln);
+    if (c.sampler == 1) return next_event_time_poisson(c, loc, tau);
+    return c.lam1 ? next_event_time_exp<WIDE, true>(c, loc, tau, ln) : next_event_time_exp<WIDE, false>(c, loc, tau, ln);
 }
 
 // ---------------------------------------------------------------------------
@@ -447,6 +477,7 @@ __device__ double coop_next_poisson(const LaneSim& c, uint64_t loc, double tau, 
 // of interval k and lanes 16-31 draws 0 .. 15 of interval k + 1, all
 // converted side by side; the binary64 running sums then follow the spec's
 // order one draw at a time (shuffled from the lane that holds it).
+template <bool LAM1>
 __device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
@@ -459,7 +490,7 @@ __device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, cons
         const uint64_t kk = lane < 16u ? k : k + 1ull;
         const uint32_t d = lane < 16u ? 16u * qa + lane : lane - 16u;
         const u64x2 b = stream_block(c.sk0, c.sk1, loc, kk, d >> 1, TAG_INTERVAL);
-        const double x = exp_draw((d & 1u) ? b.hi : b.lo, ln, c);
+        const double x = exp_draw<LAM1>((d & 1u) ? b.hi : b.lo, ln, c);
         bool done_k = false;
         for (uint32_t i = 0; i < 16u; ++i) {
             p = __dadd_rn(p, __shfl_sync(0xFFFFFFFFu, x, i));
@@ -499,9 +530,89 @@ __device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, cons
     return -1.0;
 }
 
+// Short searches (lambda dt <= 2, and >= 1/2 for Poisson points): lanes
+// 8 m .. 8 m + 7 take interval k + m (m = 0..3, k = floor(tau / dt)), lane
+// 8 m + i the interval's point i.  Intervals of more than 8 points are rare
+// here (Poi(2) > 8: 2.4e-4 of intervals); the search then starts again in
+// the general form above.  Four intervals without an answer: go on at k + 4.
+__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        if (k0 + 4ull >= (1ull << 52)) return coop_next_poisson(c, loc, tau, lane);
+        const uint64_t k = k0 + m;
+        // draw 0 gives the count N; point i is draw 1 + i
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const u64x2 bi = stream_block(c.sk0, c.sk1, loc, k, (1u + i) >> 1, TAG_INTERVAL);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t pb = ~0ull;
+        if (i < N) {
+            const uint64_t r = (i & 1u) ? bi.lo : bi.hi;
+            const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+            const uint64_t q = (uint64_t)__double_as_longlong(__dadd_rn(base, q53_scaled(r >> 11, c.dt_log2 - 53)));
+            if (q > tau_b) pb = q;
+        }
+        if (__any_sync(0xFFFFFFFFu, N > 8u)) return coop_next_poisson(c, loc, tau, lane);
+        // the smallest point > tau of the four intervals is the smallest of
+        // the first interval that has one: points of interval k lie in
+        // [k dt, (k + 1) dt], rounding included
+        const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32));
+        if (hi != 0xFFFFFFFFu) {
+            const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32) == hi ? (uint32_t)pb : 0xFFFFFFFFu);
+            return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
+        }
+    }
+    return -1.0;
+}
+
+// sums of exponentials: every lane runs interval k's binary64 running sum in
+// the spec's order on the shuffled draws; intervals k + 1 .. k + 3 only need
+// their first point
+template <bool LAM1>
+__device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        if (k0 + 4ull >= (1ull << 52)) return coop_next_exp<LAM1>(c, loc, tau, ln, lane);
+        const uint64_t k = k0 + m;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, i >> 1, TAG_INTERVAL);
+        const double x = exp_draw<LAM1>((i & 1u) ? b.hi : b.lo, ln, c);
+        double xs[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xs[j] = __shfl_sync(0xFFFFFFFFu, x, j);
+        // first point of interval k (lanes 8 m), kept if inside the interval
+        const double first = __dadd_rn(__longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2)), x);
+        const bool has = i == 0u && m > 0u &&
+                         (uint64_t)__double_as_longlong(first) < k_times_pow2_bits(k + 1ull, c.dt_log2);
+        double p = __longlong_as_double((long long)k_times_pow2_bits(k0, c.dt_log2));
+        const uint64_t end0 = k_times_pow2_bits(k0 + 1ull, c.dt_log2);
+        int state = 0;  // 1: point after tau, 2: interval k0 ended first
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            p = __dadd_rn(p, xs[j]);
+            const uint64_t pb = (uint64_t)__double_as_longlong(p);
+            if (pb >= end0) {
+                state = 2;
+                break;
+            }
+            if (pb > tau_b) {
+                state = 1;
+                break;
+            }
+        }
+        if (state == 1) return p;
+        if (state == 0) return coop_next_exp<LAM1>(c, loc, tau, ln, lane);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+        if (bal) return __shfl_sync(0xFFFFFFFFu, first, __ffs(bal) - 1);
+    }
+    return -1.0;
+}
+
 // discretised normal by inversion: -half + #{k : cdf[k] <= r}; the guide
 // gives the count below the start of r's top-8-bit bucket
-__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint16_t* __restrict__ guide,
+__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint32_t* __restrict__ guide,
                                               uint32_t n, int32_t half, uint64_t r) {
     return (int32_t)guided_count(t, guide, n, r) - half;
 }
@@ -515,12 +626,8 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     const SimParams* p = P + c.sim;
     const uint32_t x = loc_x(loc), y = loc_y(loc);
     if (c.kind == KIND_TORUS) {
-        const uint64_t* g = p->gauss;
-        const uint16_t* gd = p->gauss_guide;
-        const uint32_t gn = __ldg(&p->gauss_n);
-        const int32_t gh = __ldg(&p->gauss_half);
-        const uint32_t tx = wrap_add(x, gauss_step(g, gd, gn, gh, d1), c.W);
-        const uint32_t ty = wrap_add(y, gauss_step(g, gd, gn, gh, d2), c.H);
+        const uint32_t tx = wrap_add(x, gauss_step(c.gauss, c.gauss_guide, c.gauss_n, c.gauss_half, d1), c.W);
+        const uint32_t ty = wrap_add(y, gauss_step(c.gauss, c.gauss_guide, c.gauss_n, c.gauss_half, d2), c.H);
         const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
         return pack_loc(tx, ty, ti);
     }
@@ -908,8 +1015,12 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
         // the two exponentials of the block, when some lane of the warp sums them
         double x0 = 0.0, x1 = 0.0;
         if (__any_sync(0xFFFFFFFFu, st == SM_SEARCH && c.sampler == 0)) {
-            x0 = exp_draw(b.lo, ln, c);
-            x1 = exp_draw(b.hi, ln, c);
+            x0 = exp_draw<true>(b.lo, ln, c);
+            x1 = exp_draw<true>(b.hi, ln, c);
+            if (!c.lam1) {
+                x0 = div_rn_call(x0, c.lam);
+                x1 = div_rn_call(x1, c.lam);
+            }
         }
         if (st == SM_EVENT0) {
             ++ev_raw;
@@ -1041,7 +1152,13 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                 }
                 break;
             }
-            const double nt = c.sampler == 1 ? coop_next_poisson(c, loc, tn, lane) : coop_next_exp(c, loc, tn, ln, lane);
+            const double nt = c.sampler == 1
+                                  ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
+                                                  : coop_next_poisson(c, loc, tn, lane))
+                                  : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
+                                                           : coop_next_exp_short<false>(c, loc, tn, ln, lane))
+                                  : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
+                                            : coop_next_exp<false>(c, loc, tn, ln, lane));
             if (nt < 0.0) {
                 if (lane == 0) {
                     atomicOr(&B.S[c.sim].error, 1u);
@@ -1631,9 +1748,9 @@ struct ind_sim {
     Pool sample;   // sampled locations
     Pool results;  // outputs
     uint64_t* d_gauss = nullptr;
-    uint16_t* d_gauss_guide = nullptr;
+    uint32_t* d_gauss_guide = nullptr;
     uint64_t* d_pois = nullptr;
-    uint16_t* d_pois_guide = nullptr;
+    uint32_t* d_pois_guide = nullptr;
     uint32_t pois_n = 0;
     uint32_t gauss_n = 0;
     int gauss_half = 0;
@@ -1720,6 +1837,60 @@ struct Batch {
     }
 };
 
+
+// guide of a nondecreasing threshold table (see GUIDE_BITS): bucket u holds
+// the draws [u 2^52, (u + 1) 2^52 - 1]
+static std::vector<uint32_t> fine_guide(const std::vector<uint64_t>& cdf) {
+    std::vector<uint32_t> g(GUIDE_N);
+    constexpr int SHIFT = 64 - GUIDE_BITS;
+    for (uint32_t u = 0; u < GUIDE_N; ++u) {
+        const uint64_t first = (uint64_t)u << SHIFT;
+        const uint64_t last = first + ((1ull << SHIFT) - 1ull);
+        const uint32_t lo = (uint32_t)(std::upper_bound(cdf.begin(), cdf.end(), first) - cdf.begin());
+        const uint32_t hi = (uint32_t)(std::upper_bound(cdf.begin(), cdf.end(), last) - cdf.begin());
+        g[u] = lo | (hi != lo ? GUIDE_SCAN : 0u);
+    }
+    return g;
+}
+
+// the per-simulation device parameters shared by batches and the server
+static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
+    memset(&p, 0, sizeof(p));
+    p.kind = m->land.kind;
+    p.W = m->land.width;
+    p.H = m->land.height;
+    p.D = m->land.kind == IND_MAP ? 0 : m->land.deme;
+    p.slot_deme = m->slot_deme;
+    p.dt_log2 = m->dt_log2;
+    p.nu_thr = m->nu_thr;
+    p.lambda = m->land.lambda;
+    p.sk0 = m->sk0;
+    p.sk1 = m->sk1;
+    p.gauss_half = m->gauss_half;
+    p.gauss_n = m->gauss_n;
+    p.gauss = m->d_gauss;
+    p.gauss_guide = m->d_gauss_guide;
+    p.sampler = m->land.event_sampler;
+    p.pois_n = m->pois_n;
+    p.pois_cdf = m->d_pois;
+    p.pois_guide = m->d_pois_guide;
+    p.deme_map = m->d_deme;
+    p.row_of = m->d_row_of;
+    p.alias = m->d_alias;
+    p.off = m->d_off;
+    p.n_off = m->n_off;
+    const double mu = m->land.lambda * m->land.delta_t;  // mean points per re-prime interval
+    p.coop_short = mu <= 2.0 && (m->land.event_sampler != IND_SAMPLER_POISSON || mu >= 0.5) ? 1u : 0u;
+    p.sample_loc = m->d_sample;
+    p.events_per_round = tun.events_per_round;
+    p.min_events = tun.min_events_per_lineage;
+    p.occupancy_step = tun.occupancy_step;
+    p.tail_events = tun.tail_events;
+    p.busy_lineages = tun.busy_lineages;
+    p.max_step_events = tun.max_step_events;
+    p.n_slots = (double)m->n_slots;
+}
+
 static ind_status batch_build(Batch& b) {
     b.pool.stream = b.scratch.stream = b.stream;
     b.n_sims = (uint32_t)b.sims.size();
@@ -1729,41 +1900,10 @@ static ind_status batch_build(Batch& b) {
     for (uint32_t s = 0; s < b.n_sims; ++s) {
         ind_sim* m = b.sims[s];
         SimParams& p = hp[s];
-        memset(&p, 0, sizeof(p));
-        p.kind = m->land.kind;
-        p.W = m->land.width;
-        p.H = m->land.height;
-        p.D = m->land.kind == IND_MAP ? 0 : m->land.deme;
-        p.slot_deme = m->slot_deme;
-        p.dt_log2 = m->dt_log2;
-        p.nu_thr = m->nu_thr;
-        p.lambda = m->land.lambda;
-        p.sk0 = m->sk0;
-        p.sk1 = m->sk1;
-        p.gauss_half = m->gauss_half;
-        p.gauss_n = m->gauss_n;
-        p.gauss = m->d_gauss;
-        p.gauss_guide = m->d_gauss_guide;
-        p.sampler = m->land.event_sampler;
-        p.pois_n = m->pois_n;
-        p.pois_cdf = m->d_pois;
-        p.pois_guide = m->d_pois_guide;
-        p.deme_map = m->d_deme;
-        p.row_of = m->d_row_of;
-        p.alias = m->d_alias;
-        p.off = m->d_off;
-        p.n_off = m->n_off;
+        fill_params(m, b.tun, p);
         p.n_lineages = (uint32_t)m->n_sampled;
         p.slot_base = slots;
         p.gid_base = (uint32_t)lin;
-        p.sample_loc = m->d_sample;
-        p.events_per_round = b.tun.events_per_round;
-        p.min_events = b.tun.min_events_per_lineage;
-        p.occupancy_step = b.tun.occupancy_step;
-        p.tail_events = b.tun.tail_events;
-        p.busy_lineages = b.tun.busy_lineages;
-        p.max_step_events = b.tun.max_step_events;
-        p.n_slots = (double)m->n_slots;
         gid_base[s] = (uint32_t)lin;
         lin += m->n_sampled;
         slots += (uint64_t)m->land.width * m->land.height * m->slot_deme;
@@ -2259,15 +2399,13 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
     };
     if (L->event_sampler == IND_SAMPLER_POISSON) {
         std::vector<uint64_t> cdf = host_poisson_cdf(L->lambda * L->delta_t);
-        std::vector<uint16_t> guide(256);
-        for (uint32_t g = 0; g < 256; ++g)
-            guide[g] = (uint16_t)(std::lower_bound(cdf.begin(), cdf.end(), (uint64_t)g << 56) - cdf.begin());
+        const std::vector<uint32_t> guide = fine_guide(cdf);
         m->pois_n = (uint32_t)cdf.size();
         m->d_pois = m->tables.get<uint64_t>(cdf.size());
-        m->d_pois_guide = m->tables.get<uint16_t>(256);
+        m->d_pois_guide = m->tables.get<uint32_t>(GUIDE_N);
         if (!m->d_pois || !m->d_pois_guide) return fail(IND_ERR_OOM);
         if (cudaMemcpyAsync(m->d_pois, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(m->d_pois_guide, guide.data(), 512, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(m->d_pois_guide, guide.data(), GUIDE_N * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             g_last_cuda_error.store((int)cudaGetLastError());
             return fail(IND_ERR_CUDA);
@@ -2277,14 +2415,12 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
         std::vector<uint64_t> cdf = host_gauss_cdf(D->sigma);
         m->gauss_half = host_gauss_half(D->sigma);
         m->gauss_n = (uint32_t)cdf.size();
-        std::vector<uint16_t> guide(256);
-        for (uint32_t g = 0; g < 256; ++g)
-            guide[g] = (uint16_t)(std::lower_bound(cdf.begin(), cdf.end(), (uint64_t)g << 56) - cdf.begin());
+        const std::vector<uint32_t> guide = fine_guide(cdf);
         m->d_gauss = m->tables.get<uint64_t>(cdf.size());
-        m->d_gauss_guide = m->tables.get<uint16_t>(256);
+        m->d_gauss_guide = m->tables.get<uint32_t>(GUIDE_N);
         if (!m->d_gauss || !m->d_gauss_guide) return fail(IND_ERR_OOM);
         if (cudaMemcpyAsync(m->d_gauss, cdf.data(), cdf.size() * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(m->d_gauss_guide, guide.data(), 512, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(m->d_gauss_guide, guide.data(), GUIDE_N * 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             g_last_cuda_error.store((int)cudaGetLastError());
             return fail(IND_ERR_CUDA);
@@ -2534,8 +2670,10 @@ size_t sim_mem_estimate(const ind_landscape* L, const ind_dispersal* D, double f
         tables = ncell * (1 + 4 + 4 + n_off * 8) + 2 * n_off + 8 * (size_t)(R * R + 1);
     } else {
         individuals = (double)ncell * L->deme;
-        if (L->kind == IND_TORUS) tables = 16 * (size_t)host_gauss_half(D->sigma);
+        if (L->kind == IND_TORUS) tables = 16 * (size_t)host_gauss_half(D->sigma) + 4 * GUIDE_N;
     }
+    if (L->event_sampler == IND_SAMPLER_POISSON)
+        tables += 8 * (size_t)host_poisson_n(L->lambda * L->delta_t) + 4 * GUIDE_N;
     const double sampled = std::ceil(individuals * fraction * 1.02) + 64;
     // sampling scratch (8 B per slot) is freed before the run
     const double slots = (L->kind == IND_MAP ? (double)ncell * 255.0 : individuals);
@@ -2931,41 +3069,10 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         sl.active = true;
         sv->bytes_admitted += bytes;
         SimParams hp;
-        memset(&hp, 0, sizeof(hp));
-        hp.kind = m->land.kind;
-        hp.W = m->land.width;
-        hp.H = m->land.height;
-        hp.D = m->land.kind == IND_MAP ? 0 : m->land.deme;
-        hp.slot_deme = m->slot_deme;
-        hp.dt_log2 = m->dt_log2;
-        hp.nu_thr = m->nu_thr;
-        hp.lambda = m->land.lambda;
-        hp.sk0 = m->sk0;
-        hp.sk1 = m->sk1;
-        hp.gauss_half = m->gauss_half;
-        hp.gauss_n = m->gauss_n;
-        hp.gauss = m->d_gauss;
-        hp.gauss_guide = m->d_gauss_guide;
-        hp.sampler = m->land.event_sampler;
-        hp.pois_n = m->pois_n;
-        hp.pois_cdf = m->d_pois;
-        hp.pois_guide = m->d_pois_guide;
-        hp.deme_map = m->d_deme;
-        hp.row_of = m->d_row_of;
-        hp.alias = m->d_alias;
-        hp.off = m->d_off;
-        hp.n_off = m->n_off;
+        fill_params(m, b.tun, hp);
         hp.n_lineages = n;
         hp.slot_base = (uint64_t)slot << 32;  // slots of different requests never collide
         hp.gid_base = g0;
-        hp.sample_loc = m->d_sample;
-        hp.events_per_round = b.tun.events_per_round;
-        hp.min_events = b.tun.min_events_per_lineage;
-        hp.occupancy_step = b.tun.occupancy_step;
-        hp.tail_events = b.tun.tail_events;
-        hp.busy_lineages = b.tun.busy_lineages;
-        hp.max_step_events = b.tun.max_step_events;
-        hp.n_slots = (double)m->n_slots;
         SimState hs;
         memset(&hs, 0, sizeof(hs));
         hs.n_active = n;

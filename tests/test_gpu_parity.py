@@ -310,10 +310,17 @@ def test_advance_variants_match_oracle(variant):
     dict(kind=W.TORUS, width=25, height=25, deme=1, sigma=1.0, nu=1e-2, seed=9, lam=40.0, delta_t=1.0),
     dict(kind=W.TORUS, width=25, height=25, deme=1, sigma=1.0, nu=1e-2, seed=9, sampler=1, lam=40.0),
     dict(kind=W.NONSPATIAL, width=1, height=1, deme=700, nu=3e-3, seed=4, lam=0.05, delta_t=2.0),
+    dict(kind=W.NONSPATIAL, width=1, height=1, deme=700, nu=3e-3, seed=4, sampler=1, lam=0.05, delta_t=2.0),
+    # lambda dt = 2: the four-interval searches, with intervals of more than 8 points
+    dict(kind=W.TORUS, width=30, height=30, deme=2, sigma=2.0, nu=5e-3, seed=21, lam=2.0),
+    dict(kind=W.TORUS, width=30, height=30, deme=2, sigma=2.0, nu=5e-3, seed=21, sampler=1, lam=2.0),
+    dict(kind=W.TORUS, width=3, height=2, deme=1, sigma=6.0, nu=1e-3, seed=22, lam=0.5, delta_t=1.0),
+    dict(kind=W.TORUS, width=3, height=2, deme=1, sigma=6.0, nu=1e-3, seed=22, sampler=1, lam=0.5),
 ])
 def test_cooperative_tail_parity(cfg, coop):
     """the warp-cooperative advance kernel gives the oracle's results for both
-    samplers, including long and nearly empty re-prime intervals"""
+    samplers and both search forms, including long and nearly empty re-prime
+    intervals and tori narrower than the dispersal kernel"""
     o = run_oracle(cfg)
     g = run_gpu(cfg, tuning=dict(coop_lineages=coop, count_unique=1))
     assert_same(g, o)
