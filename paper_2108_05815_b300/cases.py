@@ -1,0 +1,96 @@
+"""Small named runs of the engine for profilers (ncu) and latency checks.
+
+  python -m paper_2108_05815_b300.cases config2 [--sampler exp|poisson]
+      the 256 x 256 torus workload once, without CUDA graphs, so that every
+      advance launch is a separate kernel launch a profiler can select
+  python -m paper_2108_05815_b300.cases busy [--sampler ...] [--rounds 6]
+      a 1024 x 1024 torus (1,048,576 lineages, sigma 2, nu 1e-3) for a few
+      rounds: the throughput-bound phase, all lineages active
+  python -m paper_2108_05815_b300.cases tail [--sampler ...]
+      one lineage, nu 1e-4 (about 10^4 events), on a non-spatial deme of one
+      and on a 1 x 1 torus with sigma 2: the latency-bound phase; prints the
+      device time per event
+
+Every run prints one JSON line with what it did.  The device memory held is
+well under 1 GB in all cases.
+"""
+import argparse
+import json
+import time
+
+from . import workloads as W
+
+SAMPLERS = {"exp": 0, "poisson": 1}
+
+
+def _sim(ind, kind, nu, seed, sampler, tuning, **kw):
+    return ind.Simulation(kind, nu, seed, sampler=sampler, tuning=tuning, **kw)
+
+
+def run_config2(ind, sampler):
+    c = W.config2()
+    s = _sim(ind, c["kind"], c["nu"], c["seed"], sampler, dict(use_graph=0, profile=1),
+             width=c["width"], height=c["height"], deme=c["deme"], sigma=c["sigma"])
+    s.sample()
+    assert s.run()
+    _, K = s.species()
+    st = s.stats()
+    s.close()
+    return dict(case="config2", species=K, **{k: st[k] for k in ("rounds", "raw_events", "advance_launches")})
+
+
+def run_busy(ind, sampler, rounds):
+    s = _sim(ind, W.TORUS, 1e-3, 42, sampler, dict(use_graph=0), width=1024, height=1024, deme=1, sigma=2.0)
+    s.sample()
+    done = s.run(round_budget=rounds)
+    st = s.stats()
+    s.close()
+    return dict(case="busy", finished=bool(done), rounds=st["rounds"], raw_events=st["raw_events"])
+
+
+def run_tail(ind, sampler):
+    out = {}
+    for name, kw in (("nonspatial_deme1", dict(kind=W.NONSPATIAL, deme=1)),
+                     ("torus_1x1_sigma2", dict(kind=W.TORUS, width=1, height=1, deme=1, sigma=2.0))):
+        best = None
+        for _ in range(3):
+            kind = kw["kind"]
+            args = {k: v for k, v in kw.items() if k != "kind"}
+            s = _sim(ind, kind, 1e-4, 1, sampler, dict(profile=1), **args)
+            s.sample()
+            t0 = time.perf_counter()
+            assert s.run()
+            t1 = time.perf_counter()
+            st = s.stats()
+            s.close()
+            per = dict(events=st["raw_events"], us_per_event_wall=(t1 - t0) * 1e6 / st["raw_events"],
+                       us_per_event_device=st["advance_ms"] * 1e3 / st["raw_events"])
+            if best is None or per["us_per_event_device"] < best["us_per_event_device"]:
+                best = per
+        out[name] = best
+    return dict(case="tail", **out)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["config2", "busy", "tail"])
+    ap.add_argument("--sampler", default="exp", choices=sorted(SAMPLERS))
+    ap.add_argument("--rounds", type=int, default=6)
+    a = ap.parse_args(argv)
+    import torch  # noqa: F401  (device memory comes from torch's allocator)
+    import paper_2108_05815_b300 as ind
+    from . import build
+    build.build()
+    sampler = SAMPLERS[a.sampler]
+    if a.case == "config2":
+        r = run_config2(ind, sampler)
+    elif a.case == "busy":
+        r = run_busy(ind, sampler, a.rounds)
+    else:
+        r = run_tail(ind, sampler)
+    r["sampler"] = a.sampler
+    print(json.dumps(r))
+
+
+if __name__ == "__main__":
+    main()

@@ -430,6 +430,10 @@ __device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double
     return -1.0;
 }
 
+// the searches return a time >= 0, or -1 when they give up: a sign-bit test
+// rather than a binary64 compare, which is slow on B300 and on the chain
+__device__ __forceinline__ bool search_failed(double t) { return __double_as_longlong(t) < 0; }
+
 template <int WIDE>
 __device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
     if (c.sampler == 1) return next_event_time_poisson(c, loc, tau);
@@ -610,15 +614,9 @@ __device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau
     return -1.0;
 }
 
-// discretised normal by inversion: -half + #{k : cdf[k] <= r}; the guide
-// gives the count below the start of r's top-8-bit bucket
-__device__ __forceinline__ int32_t gauss_step(const uint64_t* __restrict__ t, const uint32_t* __restrict__ guide,
-                                              uint32_t n, int32_t half, uint64_t r) {
-    return (int32_t)guided_count(t, guide, n, r) - half;
-}
-
 // dispersal target from the event stream's draws 1, 2, 3 (draw 0 decided
-// speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index);
+// speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index),
+// each axis a discretised normal by inversion, -half + #{k : cdf[k] <= d};
 // map d1 (alias column and threshold), d2 (deme index)
 __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* __restrict__ P, uint64_t loc,
                                             uint64_t d1, uint64_t d2, uint64_t d3) {
@@ -626,8 +624,19 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     const SimParams* p = P + c.sim;
     const uint32_t x = loc_x(loc), y = loc_y(loc);
     if (c.kind == KIND_TORUS) {
-        const uint32_t tx = wrap_add(x, gauss_step(c.gauss, c.gauss_guide, c.gauss_n, c.gauss_half, d1), c.W);
-        const uint32_t ty = wrap_add(y, gauss_step(c.gauss, c.gauss_guide, c.gauss_n, c.gauss_half, d2), c.H);
+        // both guide entries first, so that the two loads overlap; a table
+        // scan only for draws in a bucket that holds a threshold
+        const uint32_t ex = __ldg(c.gauss_guide + (d1 >> (64 - GUIDE_BITS)));
+        const uint32_t ey = __ldg(c.gauss_guide + (d2 >> (64 - GUIDE_BITS)));
+        uint32_t cx = ex & ~GUIDE_SCAN, cy = ey & ~GUIDE_SCAN;
+        if ((ex | ey) & GUIDE_SCAN) {
+            if (ex & GUIDE_SCAN)
+                while (cx < c.gauss_n && __ldg(c.gauss + cx) <= d1) ++cx;
+            if (ey & GUIDE_SCAN)
+                while (cy < c.gauss_n && __ldg(c.gauss + cy) <= d2) ++cy;
+        }
+        const uint32_t tx = wrap_add(x, (int32_t)cx - c.gauss_half, c.W);
+        const uint32_t ty = wrap_add(y, (int32_t)cy - c.gauss_half, c.H);
         const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
         return pack_loc(tx, ty, ti);
     }
@@ -757,7 +766,7 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
         load_lanesim(c, B.P, B.S, lo);
         const uint64_t loc = B.P[lo].sample_loc[g - gid_base[lo]];
         double t = next_event_time<1>(c, loc, 0.0, ln);
-        if (t < 0.0) {
+        if (search_failed(t)) {
             atomicOr(&B.S[lo].error, 1u);
             atomicOr(&B.G->error, 1u);
             t = INFINITY;
@@ -860,7 +869,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                     has = false;
                 } else {
                     const double nt = next_event_time<WIDE>(c, loc, tn, ln);
-                    if (nt < 0.0) {
+                    if (search_failed(nt)) {
                         atomicOr(&B.S[c.sim].error, 1u);
                         atomicOr(&B.G->error, 1u);
                         B.key_loc[gid] = ~0ull;
@@ -1159,7 +1168,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                                                            : coop_next_exp_short<false>(c, loc, tn, ln, lane))
                                   : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
                                             : coop_next_exp<false>(c, loc, tn, ln, lane));
-            if (nt < 0.0) {
+            if (search_failed(nt)) {
                 if (lane == 0) {
                     atomicOr(&B.S[c.sim].error, 1u);
                     atomicOr(&B.G->error, 1u);
@@ -1684,7 +1693,7 @@ __global__ void k_append(BatchDev B, uint32_t pos, uint32_t n, uint32_t slot, ui
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint64_t loc = sample_loc[i];
         double t = next_event_time<1>(c, loc, 0.0, ln);
-        if (t < 0.0) {
+        if (search_failed(t)) {
             atomicOr(&B.S[slot].error, 1u);
             atomicOr(&B.G->error, 1u);
             t = INFINITY;
