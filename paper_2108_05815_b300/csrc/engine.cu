@@ -1110,7 +1110,12 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 
 // evaluates in parallel the draws a one-lane search would reach one after
 // another.  Lane 0 writes the results.
-template <bool COUNT>
+// MODE 1: every simulation sums exponentials with lambda = 1 on the short
+// search; MODE 2: every simulation draws Poisson points on the short search;
+// MODE 0: any mix (the search chosen per lineage).  The specialised kernels
+// are smaller, which matters where one warp runs alone and waits on
+// instruction fetch.
+template <bool COUNT, int MODE>
 __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
@@ -1161,13 +1166,19 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                 }
                 break;
             }
-            const double nt = c.sampler == 1
-                                  ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
-                                                  : coop_next_poisson(c, loc, tn, lane))
-                                  : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
-                                                           : coop_next_exp_short<false>(c, loc, tn, ln, lane))
-                                  : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
-                                            : coop_next_exp<false>(c, loc, tn, ln, lane));
+            double nt;
+            if (MODE == 1) {
+                nt = coop_next_exp_short<true>(c, loc, tn, ln, lane);
+            } else if (MODE == 2) {
+                nt = coop_next_poisson_short(c, loc, tn, lane);
+            } else {
+                nt = c.sampler == 1 ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
+                                                    : coop_next_poisson(c, loc, tn, lane))
+                     : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
+                                              : coop_next_exp_short<false>(c, loc, tn, ln, lane))
+                                    : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
+                                              : coop_next_exp<false>(c, loc, tn, ln, lane));
+            }
             if (search_failed(nt)) {
                 if (lane == 0) {
                     atomicOr(&B.S[c.sim].error, 1u);
@@ -1822,6 +1833,7 @@ struct Batch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured chunk of rounds per advance variant
     uint32_t graph_rounds[2] = {0, 0};
     bool wide = false;                               // warp-cooperative (tail) advance kernel
+    int coop_mode = 0;                               // its specialisation (k_advance_coop MODE)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -1900,6 +1912,26 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.n_slots = (double)m->n_slots;
 }
 
+template <bool COUNT>
+static cudaError_t set_coop_smem() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_advance_coop<COUNT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)LN_SMEM_BYTES)) ||
+        (e = cudaFuncSetAttribute(k_advance_coop<COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)LN_SMEM_BYTES)) ||
+        (e = cudaFuncSetAttribute(k_advance_coop<COUNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)LN_SMEM_BYTES)))
+        return e;
+    return cudaSuccess;
+}
+
+template <bool COUNT>
+static void launch_coop(const Batch& b, size_t smem, cudaStream_t s) {
+    if (b.coop_mode == 1) k_advance_coop<COUNT, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+    else if (b.coop_mode == 2) k_advance_coop<COUNT, 2><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+    else k_advance_coop<COUNT, 0><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+}
+
 static ind_status batch_build(Batch& b) {
     b.pool.stream = b.scratch.stream = b.stream;
     b.n_sims = (uint32_t)b.sims.size();
@@ -1975,6 +2007,12 @@ static ind_status batch_build(Batch& b) {
     d.dedup = b.tun.dedup ? 1 : 0;
     d.need_ln = 0;
     for (uint32_t si = 0; si < b.n_sims; ++si) d.need_ln |= hp[si].sampler == IND_SAMPLER_EXP ? 1 : 0;
+    bool all_exp1 = b.n_sims > 0, all_pois = b.n_sims > 0;
+    for (uint32_t si = 0; si < b.n_sims; ++si) {
+        all_exp1 &= hp[si].sampler == IND_SAMPLER_EXP && hp[si].coop_short && hp[si].lambda == 1.0;
+        all_pois &= hp[si].sampler == IND_SAMPLER_POISSON && hp[si].coop_short;
+    }
+    b.coop_mode = all_exp1 ? 1 : all_pois ? 2 : 0;
     cudaStream_t s = b.stream;
     CK(cudaMemcpyAsync(b.d_params, hp.data(), sizeof(SimParams) * b.n_sims, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b.d_gid_base, gid_base.data(), sizeof(uint32_t) * b.n_sims, cudaMemcpyHostToDevice, s));
@@ -2007,8 +2045,8 @@ static ind_status batch_build(Batch& b) {
     const uint32_t sms = sm_count();
     CK(cudaFuncSetAttribute(k_advance<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
-    CK(cudaFuncSetAttribute(k_advance_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
-    CK(cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(set_coop_smem<true>());
+    CK(set_coop_smem<false>());
     CK(cudaFuncSetAttribute(k_advance_sm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
@@ -2034,11 +2072,11 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     const size_t smem = b.dev.need_ln ? LN_SMEM_BYTES : 0;
     const bool conv = b.tun.advance_variant == 0;  // convergent state machine or one-lane loop
     if (b.dev.count_unique) {
-        if (b.wide) k_advance_coop<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (b.wide) launch_coop<true>(b, smem, s);
         else if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     } else {
-        if (b.wide) k_advance_coop<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (b.wide) launch_coop<false>(b, smem, s);
         else if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
     }
@@ -3204,7 +3242,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
     if ((e = cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
-        (e = cudaFuncSetAttribute(k_advance_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
+        (e = set_coop_smem<false>()) ||
         (e = cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
         return fail(e);
     b.adv_threads = b.tun.block_threads;
