@@ -31,7 +31,8 @@ METRIC = "lineage events/sec and species-count latency p50/p99; batched vs plain
 UNIT = "events/s"
 WORKLOAD = ("config2: torus 256x256, 1 individual per cell (65536 sampled lineages), Gaussian dispersal "
             "sigma=2 (discretised per axis), nu=1e-4, lambda=1, delta_t=1, seed=42")
-# Algorithmic 32-bit integer operations of the spec ("Roofline"):
+# Algorithmic 32-bit integer operations of one event of the spec (the integer
+# work the spec itself defines, not the instructions a compiler emits):
 PHILOX_OPS = 100          # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key adds)
 EXP_DRAW_OPS = 110        # fixed-point -ln U of one draw, incl. conversion to binary64
 EVENT_FIXED_OPS = 40      # speciation compare, dispersal index arithmetic, wrap, bookkeeping
@@ -296,6 +297,25 @@ def run_ours(args, rank, world, local, pg):
     other_line = {"sampler": [n for n, v in SAMPLER.items() if v == other][0], "unique_events_per_step": U_o,
                   "ms_per_step": sum(o_ms) / len(o_ms), "value": U_o / (sum(o_ms) / len(o_ms) * 1e-3)}
 
+    # The dependent chain: a round lasts as long as its busiest lineage, so a
+    # step takes at least (critical events) x (the time of one event of a
+    # lineage that runs alone).  Eight lineages sampled on the same landscape
+    # give that time (device time of their advance launches / their critical
+    # events).
+    crit = st["critical_events"]
+    lone = make_sim(ind, 42, tuning=dict(profile=1))
+    lone.sample(8.0 / 65536.0, 1)
+    assert lone.run()
+    ls = lone.stats()
+    lone.close()
+    lone_ns = ls["advance_ms"] * 1e6 / max(ls["critical_events"], 1)
+    crit_ns = ms_step * 1e6 / max(crit, 1)
+    latency = {"critical_events_per_step": crit, "ns_per_critical_event": crit_ns,
+               "lone_lineage_ns_per_event": lone_ns, "lone_lineages": ls["n_sampled"],
+               "frac": lone_ns / crit_ns,
+               "what": "step time / (sum over rounds of the most events one lineage ran in the round), against "
+                       "the advance-kernel time per event of a few lineages alone on the same landscape"}
+
     # roofline of the advance kernel (events per launch / its CUDA-event time)
     raw_per_step = raw / args.steps
     events_per_launch = raw / max(adv_n, 1)
@@ -321,7 +341,8 @@ def run_ours(args, rank, world, local, pg):
                      "ops_per_event": ops_per_event, "events_per_launch": events_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
                      "busiest_launch": busiest(best or {}, ops_per_event, peak),
-                     "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived, see DESIGN.md)"},
+                     "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived)"},
+        "latency_bound": latency,
         "cpu_baseline": cpu,
         "e2e": {"value": U * world / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max,
@@ -475,6 +496,10 @@ def run_batch(args, rank, world, local, pg):
                      "unit": "Tops/s (32-bit integer)", "frac": achieved / peak, "traffic": None,
                      "events_per_launch": ev_per_launch, "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
                      "ops_per_event": ops, "busiest_launch": busiest(best or {}, ops, peak)},
+        "latency_bound": {"critical_events_per_step": st[0]["critical_events"],
+                          "ns_per_critical_event": ms * 1e6 / max(st[0]["critical_events"], 1),
+                          "what": "step time / (sum over rounds of the most events one lineage of the batch ran "
+                                  "in the round): the batch lasts as long as its longest dependent chain"},
         "gpu_launches": launches, "clocks": clk,
     }
     if rank == 0:

@@ -52,8 +52,9 @@ typedef enum {
     IND_ERR_CUDA = -3,   /* a CUDA runtime call failed (see ind_last_cuda_error) */
     IND_ERR_BUDGET = -4, /* sim_run used its round budget; call it again to resume */
     IND_ERR_STATE = -5,  /* call out of order (e.g. species before the run ended) */
-    IND_ERR_DEVICE = -6  /* a device-side limit was hit (see DESIGN: re-prime
-                            interval draw limit); results are not valid */
+    IND_ERR_DEVICE = -6  /* a device-side limit was hit (more than 2^20 draws in one
+                            re-prime interval, 2^26 empty intervals crossed in one
+                            search, or a full hash table); results are not valid */
 } ind_status;
 
 /* landscape kinds */
@@ -122,6 +123,9 @@ typedef struct {
     uint64_t advance_launches; /* advance-kernel launches timed (profile = 1 only) */
     double busiest_launch_ms;       /* profile = 1: the advance launch with the highest */
     uint64_t busiest_launch_events; /* event rate of the run: its time and events (all sims) */
+    uint64_t critical_events; /* sum over rounds of the most events one lineage ran in the round:
+                                 the dependent chain the rounds' durations are bound by (of the
+                                 whole batch for sim_batch_run; 0 for served requests) */
 } ind_run_stats;
 
 /* Tuning of the engine.  None of it changes results (bit-identical). */

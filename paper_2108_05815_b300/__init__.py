@@ -50,7 +50,7 @@ class RunStats(ctypes.Structure):
                                                "n_species", "n_roots")] + \
                [("ms_total", ctypes.c_double), ("advance_ms", ctypes.c_double),
                 ("advance_launches", ctypes.c_uint64), ("busiest_launch_ms", ctypes.c_double),
-                ("busiest_launch_events", ctypes.c_uint64)]
+                ("busiest_launch_events", ctypes.c_uint64), ("critical_events", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -215,6 +215,8 @@ struct Globals {
     unsigned long long* prof_events;  // profile: cumulative raw events after each round of a chunk
     uint32_t prof_slot;               // round index within the chunk
     uint32_t prof_n;
+    uint32_t round_max;               // most events one lineage ran in the running round
+    unsigned long long critical_events;  // sum of round_max over completed rounds
 };
 
 struct __align__(16) EvSlot {
@@ -249,6 +251,7 @@ struct BatchDev {
     int count_unique;
     int need_ln;  // some simulation uses the exponential-sums sampler
     uint32_t events_per_visit;
+    uint32_t coop_lineages;  // a round with at most this many active lineages runs one warp per lineage
 };
 
 // ---------------------------------------------------------------------------
@@ -783,6 +786,7 @@ template <bool COUNT, int WIDE>
 __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
+    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
     const uint32_t chunk = 32u * B.lpl;
     // a block whose first possible claim lies beyond the active lineages has
     // nothing to do (claims go out in order of arrival, at most one per warp)
@@ -806,6 +810,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     c.sim = 0xFFFFFFFFu;
     uint64_t ev_raw = 0, ev_unique = 0;
     uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t ev_lin = 0, lane_max = 0;  // events of the lane's lineage this round, and their maximum
 
     for (;;) {
         unsigned need = __ballot_sync(0xFFFFFFFFu, !has);
@@ -842,6 +847,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                         cnt_sim = s;
                     }
                     has = true;
+                    ev_lin = 0;
                 }
                 chunk_next += min(avail, (uint32_t)__popc(need));
             }
@@ -861,6 +867,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                 has = false;
             } else {
                 ++ev_raw;
+                lane_max = max(lane_max, ++ev_lin);
                 if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
                 if (do_event(c, B.P, loc, tn)) {
                     B.key_loc[gid] = loc;
@@ -890,6 +897,8 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
         warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
         if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
     }
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, lane_max);
+    if (lane == 0 && wmax) atomicMax(&B.G->round_max, wmax);
 }
 
 // Throughput phase, convergent form: every iteration each lane computes
@@ -905,6 +914,7 @@ template <bool COUNT>
 __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
+    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
     const uint32_t chunk = 32u * B.lpl;
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
@@ -930,6 +940,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
     double p = 0.0, base = 0.0;
     uint64_t ev_raw = 0, ev_unique = 0;
     uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t ev_lin = 0, lane_max = 0;  // events of the lane's lineage this round, and their maximum
 
     auto fail = [&]() {
         atomicOr(&B.S[c.sim].error, 1u);
@@ -1003,6 +1014,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
                         cnt_sim = s;
                         hz = (uint64_t)__double_as_longlong(c.horizon);
                     }
+                    ev_lin = 0;
                     if ((uint64_t)__double_as_longlong(tn) > hz) {
                         if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);  // already at the horizon
                     } else {
@@ -1033,6 +1045,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
         }
         if (st == SM_EVENT0) {
             ++ev_raw;
+            lane_max = max(lane_max, ++ev_lin);
             if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             if ((b.lo >> 11) < c.nu_thr) {
                 B.key_loc[gid] = loc;
@@ -1105,6 +1118,8 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
         warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
         if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
     }
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, lane_max);
+    if (lane == 0 && wmax) atomicMax(&B.G->round_max, wmax);
 }
 
 
@@ -1119,6 +1134,7 @@ template <bool COUNT, int MODE>
 __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
+    if (n > B.coop_lineages) return;  // a round for the one-lane form
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
     const uint32_t t = B.G->round & 1u;
@@ -1126,6 +1142,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     const uint32_t lane = threadIdx.x & 31u;
     uint64_t ev_raw = 0, ev_unique = 0;
     uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t lane_max = 0;  // most events of one lineage this round (the same in every lane)
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(&B.G->work_ctr, 1u);
@@ -1147,6 +1164,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
             cnt_sim = s;
         }
         const uint64_t hz = (uint64_t)__double_as_longlong(c.horizon);
+        uint32_t ev_lin = 0;
         for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
             if ((uint64_t)__double_as_longlong(tn) > hz) {
                 if (lane == 0) {
@@ -1157,6 +1175,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                 break;
             }
             ++ev_raw;
+            lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             if (do_event(c, B.P, loc, tn)) {
                 if (lane == 0) {
@@ -1196,6 +1215,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
         atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
         if (COUNT) atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
     }
+    if (lane == 0 && lane_max) atomicMax(&B.G->round_max, lane_max);
 }
 
 // horizon step (time) of a simulation with n active lineages
@@ -1337,6 +1357,8 @@ __global__ void k_compact(BatchDev B) {
         G->used[tp] = 0;
         G->ev_used[tp] = 0;
         G->n_live_sims = live;
+        G->critical_events += G->round_max;
+        G->round_max = 0;
         uint32_t cap = 2u;
         while (cap < 2u * nt && cap < B.ht_cap) cap <<= 1;
         G->mask[tp] = cap - 1u;  // the next round uses table tp
@@ -1830,9 +1852,8 @@ struct Batch {
     bool started = false;
     bool finished = false;
     uint64_t rounds = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured chunk of rounds per advance variant
-    uint32_t graph_rounds[2] = {0, 0};
-    bool wide = false;                               // warp-cooperative (tail) advance kernel
+    cudaGraphExec_t graph = nullptr;  // captured chunk of rounds
+    uint32_t graph_rounds = 0;
     int coop_mode = 0;                               // its specialisation (k_advance_coop MODE)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
@@ -1847,8 +1868,7 @@ struct Batch {
     double ms = 0.0;
 
     ~Batch() {
-        for (auto g : graph)
-            if (g) cudaGraphExecDestroy(g);
+        if (graph) cudaGraphExecDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_end) cudaEventDestroy(e);
@@ -2004,6 +2024,7 @@ static ind_status batch_build(Batch& b) {
     d.n_sims = b.n_sims;
     d.lpl = b.tun.lineages_per_lane;
     d.events_per_visit = b.tun.events_per_visit;
+    d.coop_lineages = b.tun.coop_lineages;
     d.dedup = b.tun.dedup ? 1 : 0;
     d.need_ln = 0;
     for (uint32_t si = 0; si < b.n_sims; ++si) d.need_ln |= hp[si].sampler == IND_SAMPLER_EXP ? 1 : 0;
@@ -2063,6 +2084,8 @@ static ind_status batch_build(Batch& b) {
     return IND_OK;
 }
 
+constexpr uint64_t LAUNCHES_PER_ROUND = 3;  // one-lane advance, warp-per-lineage advance, compaction
+
 static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     cudaStream_t s = capturing ? b.cap_stream : b.stream;
     const bool prof = b.tun.profile && r < b.ev_start.size();
@@ -2071,29 +2094,35 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     // shared memory only when some simulation sums exponentials (leaves L1 larger otherwise)
     const size_t smem = b.dev.need_ln ? LN_SMEM_BYTES : 0;
     const bool conv = b.tun.advance_variant == 0;  // convergent state machine or one-lane loop
+    // both advance forms every round: each reads the live lineage count and
+    // returns at once unless the round is its own (more than coop_lineages
+    // lineages: one lane per lineage; else one warp per lineage), so that the
+    // choice is made per round inside captured chunks
     if (b.dev.count_unique) {
-        if (b.wide) launch_coop<true>(b, smem, s);
-        else if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        CK(cudaGetLastError());
+        launch_coop<true>(b, smem, s);
     } else {
-        if (b.wide) launch_coop<false>(b, smem, s);
-        else if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        CK(cudaGetLastError());
+        launch_coop<false>(b, smem, s);
     }
-    CKL();
+    CK(cudaGetLastError());
     if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));
     k_compact<<<b.cmp_blocks, 256, 0, s>>>(b.dev);
-    CKL();
+    CK(cudaGetLastError());
+    if (!capturing) g_launches.fetch_add(LAUNCHES_PER_ROUND);  // a captured chunk counts when it runs
     return IND_OK;
 }
 
 static ind_status batch_rounds(Batch& b, uint32_t rounds) {
     if (b.tun.use_graph) {
-        const int v = b.wide ? 1 : 0;
-        if (!b.graph[v] || b.graph_rounds[v] != rounds) {
-            if (b.graph[v]) {
-                cudaGraphExecDestroy(b.graph[v]);
-                b.graph[v] = nullptr;
+        if (!b.graph || b.graph_rounds != rounds) {
+            if (b.graph) {
+                cudaGraphExecDestroy(b.graph);
+                b.graph = nullptr;
             }
             cudaGraph_t g;
             if (!b.cap_stream) CK(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
@@ -2106,12 +2135,12 @@ static ind_status batch_rounds(Batch& b, uint32_t rounds) {
                 }
             }
             CK(cudaStreamEndCapture(b.cap_stream, &g));
-            CK(cudaGraphInstantiate(&b.graph[v], g, 0));
+            CK(cudaGraphInstantiate(&b.graph, g, 0));
             cudaGraphDestroy(g);
-            b.graph_rounds[v] = rounds;
+            b.graph_rounds = rounds;
         }
-        CK(cudaGraphLaunch(b.graph[v], b.stream));
-        g_launches.fetch_add(2ull * rounds);
+        CK(cudaGraphLaunch(b.graph, b.stream));
+        g_launches.fetch_add(LAUNCHES_PER_ROUND * rounds);
         return IND_OK;
     }
     for (uint32_t r = 0; r < rounds; ++r) {
@@ -2272,8 +2301,6 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
             }
             chunk = (uint32_t)std::min<uint64_t>(chunk, round_budget - done_rounds);
         }
-        // few active lineages: the warp-cooperative (latency) variant
-        b.wide = (b.h_g_valid ? b.h_g->n_total : b.n_lin) <= b.tun.coop_lineages;
         ind_status st = batch_rounds(b, chunk);
         if (st != IND_OK) return st;
         done_rounds += chunk;
@@ -2309,6 +2336,7 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
         m->stats.advance_launches = b.advance_launches;
         m->stats.busiest_launch_ms = b.best_launch_ms;
         m->stats.busiest_launch_events = b.best_launch_events;
+        m->stats.critical_events = b.h_g_valid ? b.h_g->critical_events : 0;
     }
     return result;
 }
@@ -3215,6 +3243,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     d.n_sims = max_sims;
     d.lpl = b.tun.lineages_per_lane;
     d.events_per_visit = b.tun.events_per_visit;
+    d.coop_lineages = b.tun.coop_lineages;
     d.dedup = b.tun.dedup ? 1 : 0;
     d.count_unique = 0;  // exact counting is a batch-only measurement mode
     d.need_ln = 1;       // requests of either sampler may arrive
@@ -3300,7 +3329,6 @@ ind_status srv_step(ind_server* sv, uint32_t rounds, uint64_t* finished, uint32_
     if (st != IND_OK) return st;
     // 3. launch the next chunk of rounds on the main stream
     if (sv->n_total > 0) {
-        b.wide = sv->n_total <= b.tun.coop_lineages;
         st = batch_rounds(b, rounds);
         if (st != IND_OK) return st;
         sv->chunk_in_flight = true;
