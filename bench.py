@@ -37,6 +37,13 @@ PHILOX_OPS = 100          # 10 rounds x (2 mul.lo + 2 mul.hi + 4 xor + 2 key add
 EXP_DRAW_OPS = 110        # fixed-point -ln U of one draw, incl. conversion to binary64
 EVENT_FIXED_OPS = 40      # speciation compare, dispersal index arithmetic, wrap, bookkeeping
 INT32_LANES_PER_SM = 128  # Blackwell: 128 INT32-capable lanes per SM per clock
+# DRAM bytes (read + write) of the advance launches of one round of the
+# default workload, measured with ncu on this kernel build:
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum \
+#       --clock-control none -k regex:k_advance -c 200 --csv \
+#       python -m paper_2108_05815_b300.cases config2
+# (21.5 MB over 48 rounds).  Not measured for the Poisson sampler.
+TRAFFIC_PER_ROUND = {"exp": 448e3}
 
 
 def parse():
@@ -336,10 +343,13 @@ def run_ours(args, rank, world, local, pg):
                    "species": K, "tuning": ind.default_tuning()},
         "latency_ms": {"p50": pct(lat_ms, 50), "p99": pct(lat_ms, 99), "what": "step start to species count on host"},
         "raw_events_per_s": raw_per_step * world / (ms_step_max * 1e-3),
-        "roofline": {"bound": "alu", "kernel": "k_advance", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s (32-bit integer)", "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": "k_advance_coop + k_advance (one round: both launched, one works)",
+                     "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
+                     "traffic": TRAFFIC_PER_ROUND.get(args.sampler),
                      "ops_per_event": ops_per_event, "events_per_launch": events_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
+                     "dominant": "k_advance_coop, 94 % of the step (ncu launch list): latency-bound, see latency_bound",
                      "busiest_launch": busiest(best or {}, ops_per_event, peak),
                      "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived)"},
         "latency_bound": latency,
@@ -521,6 +531,7 @@ def run_served(args, rank, world, local, pg):
     srv = ind.Server(150 * 10 ** 9, max_sims=4096, stream=srv_stream)
     clocks = ClockSampler(local)
     clocks.start()
+    launches0 = ind.kernel_launches()
     sims, lat, arrival, tickets = {}, [], {}, {}
     nxt, done = 0, 0
     t0 = time.perf_counter()
@@ -560,7 +571,7 @@ def run_served(args, rank, world, local, pg):
                                % args.window, "requests": len(reqs), "event_sampler": args.sampler},
         "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat),
                       "what": "arrival to species identities on the device"},
-        "server": st, "clocks": clk,
+        "server": st, "clocks": clk, "gpu_launches": ind.kernel_launches() - launches0,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
