@@ -621,12 +621,16 @@ __device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau
 // speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index),
 // each axis a discretised normal by inversion, -half + #{k : cdf[k] <= d};
 // map d1 (alias column and threshold), d2 (deme index)
+// (KIND: the landscape kind when the caller knows it at compile time, -1
+// for the simulation's own)
+template <int KIND = -1>
 __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* __restrict__ P, uint64_t loc,
                                             uint64_t d1, uint64_t d2, uint64_t d3) {
-    if (c.kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
+    const int kind = KIND >= 0 ? KIND : c.kind;
+    if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
     const SimParams* p = P + c.sim;
     const uint32_t x = loc_x(loc), y = loc_y(loc);
-    if (c.kind == KIND_TORUS) {
+    if (kind == KIND_TORUS) {
         // both guide entries first, so that the two loads overlap; a table
         // scan only for draws in a bucket that holds a threshold
         const uint32_t ex = __ldg(c.gauss_guide + (d1 >> (64 - GUIDE_BITS)));
@@ -672,6 +676,28 @@ __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __re
     const u64x2 b1 = stream_block(c.sk0, c.sk1, loc, tk, 1, TAG_EVENT);
     if ((b0.lo >> 11) < c.nu_thr) return true;
     loc = disperse(c, P, loc, b0.hi, b1.lo, b1.hi);
+    return false;
+}
+
+// do_event for one lineage per warp: lanes of even and odd index compute
+// the event stream's blocks 0 and 1 side by side, then every lane takes the
+// four draws by shuffle (one block's latency instead of two interleaved)
+template <int KIND>
+__device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
+                                              double tau, uint32_t lane) {
+    const int kind = KIND >= 0 ? KIND : c.kind;
+    const uint64_t tk = (uint64_t)__double_as_longlong(tau);
+    if (kind == KIND_NONSPATIAL) {
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
+        if ((b0.lo >> 11) < c.nu_thr) return true;
+        loc = disperse<KIND_NONSPATIAL>(c, P, loc, b0.hi, 0ull, 0ull);
+        return false;
+    }
+    const u64x2 b = stream_block(c.sk0, c.sk1, loc, tk, lane & 1u, TAG_EVENT);
+    const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0), d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
+    const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1), d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
+    if ((d0 >> 11) < c.nu_thr) return true;
+    loc = disperse<KIND>(c, P, loc, d1, d2, d3);
     return false;
 }
 
@@ -1127,10 +1153,10 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 // another.  Lane 0 writes the results.
 // MODE 1: every simulation sums exponentials with lambda = 1 on the short
 // search; MODE 2: every simulation draws Poisson points on the short search;
-// MODE 0: any mix (the search chosen per lineage).  The specialised kernels
-// are smaller, which matters where one warp runs alone and waits on
-// instruction fetch.
-template <bool COUNT, int MODE>
+// MODE 0: any mix (the search chosen per lineage).  KIND: the landscape kind
+// shared by every simulation, or -1.  The specialised kernels are smaller,
+// which matters where one warp runs alone and waits on instruction fetch.
+template <bool COUNT, int MODE, int KIND>
 __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
@@ -1177,7 +1203,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
             ++ev_raw;
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
-            if (do_event(c, B.P, loc, tn)) {
+            if (do_event_warp<KIND>(c, B.P, loc, tn, lane)) {
                 if (lane == 0) {
                     B.key_loc[gid] = loc;
                     B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
@@ -1855,6 +1881,7 @@ struct Batch {
     cudaGraphExec_t graph = nullptr;  // captured chunk of rounds
     uint32_t graph_rounds = 0;
     int coop_mode = 0;                               // its specialisation (k_advance_coop MODE)
+    int coop_kind = -1;                              // the landscape kind all simulations share, or -1
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -1932,24 +1959,43 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.n_slots = (double)m->n_slots;
 }
 
+template <bool COUNT, int MODE, int KIND>
+static cudaError_t set_smem_one() {
+    return cudaFuncSetAttribute(k_advance_coop<COUNT, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LN_SMEM_BYTES);
+}
+
+// the instantiations launch_coop uses: with counting (measurement runs) only
+// the generic kind
 template <bool COUNT>
 static cudaError_t set_coop_smem() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_advance_coop<COUNT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)LN_SMEM_BYTES)) ||
-        (e = cudaFuncSetAttribute(k_advance_coop<COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)LN_SMEM_BYTES)) ||
-        (e = cudaFuncSetAttribute(k_advance_coop<COUNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)LN_SMEM_BYTES)))
+    if ((e = set_smem_one<COUNT, 0, -1>()) || (e = set_smem_one<COUNT, 1, -1>()) ||
+        (e = set_smem_one<COUNT, 2, -1>()))
         return e;
+    if (!COUNT) {
+        if ((e = set_smem_one<COUNT, 1, 0>()) || (e = set_smem_one<COUNT, 1, 1>()) ||
+            (e = set_smem_one<COUNT, 1, 2>()) || (e = set_smem_one<COUNT, 2, 0>()) ||
+            (e = set_smem_one<COUNT, 2, 1>()) || (e = set_smem_one<COUNT, 2, 2>()))
+            return e;
+    }
     return cudaSuccess;
+}
+
+template <bool COUNT, int MODE>
+static void launch_coop_kind(const Batch& b, size_t smem, cudaStream_t s) {
+    const dim3 g(b.adv_blocks), t(b.adv_threads);
+    if (COUNT || b.coop_kind < 0) k_advance_coop<COUNT, MODE, -1><<<g, t, smem, s>>>(b.dev);
+    else if (b.coop_kind == KIND_NONSPATIAL) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 0)><<<g, t, smem, s>>>(b.dev);
+    else if (b.coop_kind == KIND_TORUS) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 1)><<<g, t, smem, s>>>(b.dev);
+    else k_advance_coop<COUNT, MODE, (COUNT ? -1 : 2)><<<g, t, smem, s>>>(b.dev);
 }
 
 template <bool COUNT>
 static void launch_coop(const Batch& b, size_t smem, cudaStream_t s) {
-    if (b.coop_mode == 1) k_advance_coop<COUNT, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-    else if (b.coop_mode == 2) k_advance_coop<COUNT, 2><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-    else k_advance_coop<COUNT, 0><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+    if (b.coop_mode == 1) launch_coop_kind<COUNT, 1>(b, smem, s);
+    else if (b.coop_mode == 2) launch_coop_kind<COUNT, 2>(b, smem, s);
+    else k_advance_coop<COUNT, 0, -1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
 }
 
 static ind_status batch_build(Batch& b) {
@@ -2034,6 +2080,9 @@ static ind_status batch_build(Batch& b) {
         all_pois &= hp[si].sampler == IND_SAMPLER_POISSON && hp[si].coop_short;
     }
     b.coop_mode = all_exp1 ? 1 : all_pois ? 2 : 0;
+    b.coop_kind = b.n_sims > 0 ? hp[0].kind : -1;
+    for (uint32_t si = 1; si < b.n_sims; ++si)
+        if (hp[si].kind != b.coop_kind) b.coop_kind = -1;
     cudaStream_t s = b.stream;
     CK(cudaMemcpyAsync(b.d_params, hp.data(), sizeof(SimParams) * b.n_sims, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b.d_gid_base, gid_base.data(), sizeof(uint32_t) * b.n_sims, cudaMemcpyHostToDevice, s));
@@ -2389,7 +2438,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->occupancy_step = 0.25;
     t->tail_events = 128.0;
     t->busy_lineages = 32768.0;
-    t->max_step_events = 1024.0;
+    t->max_step_events = 16384.0;
 }
 
 static bool tuning_ok(const ind_tuning* t) {
