@@ -27,7 +27,7 @@ import numpy as np
 
 from . import tables
 
-NONSPATIAL, TORUS, MAP = 0, 1, 2
+NONSPATIAL, TORUS, MAP, IMPLICIT = 0, 1, 2, 3
 TAG_INTERVAL, TAG_EVENT, TAG_MAP, TAG_SAMPLE = 1, 2, 3, 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -64,7 +64,8 @@ class _Model(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("gauss_half", ctypes.c_int32),
                 ("gauss_cdf", ctypes.c_void_p), ("radius", ctypes.c_int32),
                 ("kw", ctypes.c_void_p), ("ln", ctypes.c_void_p), ("sampler", ctypes.c_int32),
-                ("pois_n", ctypes.c_int32), ("pois_cdf", ctypes.c_void_p)]
+                ("pois_n", ctypes.c_int32), ("pois_cdf", ctypes.c_void_p),
+                ("migration", ctypes.c_double), ("meta_size", ctypes.c_uint64), ("meta_nu", ctypes.c_double)]
 
 
 def lib():
@@ -183,10 +184,14 @@ class Model:
     cells of ``deme`` individuals, discretised N(0, sigma^2) dispersal per
     axis) or MAP (deme_map of demes, dispersal by a per-cell alias table over
     the disk of ``radius`` with Gaussian weights of ``sigma`` times the target
-    deme, torus-wrapped)."""
+    deme, torus-wrapped) or IMPLICIT (the spatially implicit scenario: a
+    local community of J = deme individuals, non-spatial, whose parent lives
+    with probability ``migration`` per event in a static non-spatial
+    metacommunity of ``meta_size`` individuals with speciation probability
+    ``meta_nu``; nu is the local speciation probability and may be 0)."""
 
     def __init__(self, kind, width, height, deme, nu, seed, lam=1.0, delta_t=1.0,
-                 sigma=None, radius=None, deme_map=None, sampler=0):
+                 sigma=None, radius=None, deme_map=None, sampler=0, migration=0.0, meta_size=0, meta_nu=0.0):
         self.kind, self.width, self.height = kind, int(width), int(height)
         self.nu, self.seed, self.lam, self.delta_t = float(nu), int(seed), float(lam), float(delta_t)
         self._keep = []
@@ -213,6 +218,9 @@ class Model:
             self._keep.append(ca)
             m.gauss_cdf = ca.ctypes.data
             m.gauss_half = half
+        if kind == IMPLICIT:
+            assert self.width == 1 and self.height == 1 and 1 <= int(meta_size) <= (1 << 31)
+            m.migration, m.meta_size, m.meta_nu = float(migration), int(meta_size), float(meta_nu)
         m.sampler = int(sampler)
         if sampler == 1:
             cdf, _ = tables.poisson_cdf(self.lam * self.delta_t)

@@ -24,7 +24,12 @@
  *     individual speciates with probability nu, else disperses (summary
  *     listing of the Independent algorithm);
  *   - species identity = the speciation event an individual's lineage ends in
- *     (section "A Neutral Coalescence-based Simulation").
+ *     (section "A Neutral Coalescence-based Simulation");
+ *   - the spatially implicit scenario (background section "Spatially
+ *     Implicit", appendix of the neutral scenarios): a non-spatial local
+ *     community of J individuals whose parents live, with probability m per
+ *     event, in a static non-spatial metacommunity of J_meta individuals with
+ *     its own speciation probability nu_meta.
  *
  * Mode P (or_trace*) is the plain definition: one lineage, no interaction.
  * Mode M (or_run_merge) processes all events of all lineages in global time
@@ -51,6 +56,7 @@ typedef __int128 i128;
 #define OR_NONSPATIAL 0
 #define OR_TORUS 1
 #define OR_MAP 2
+#define OR_IMPLICIT 3
 
 /* ------------------------------------------------------------------------
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -203,6 +209,12 @@ typedef struct {
     int32_t sampler;
     int32_t pois_n;
     const uint64_t* pois_cdf;
+    /* spatially implicit: migration probability per event of a local
+     * lineage, metacommunity size J_meta (<= 2^31) and its speciation
+     * probability; the local community is the deme of J = deme individuals */
+    double migration;
+    uint64_t meta_size;
+    double meta_nu;
 } or_model;
 
 static uint64_t pack_loc(uint64_t x, uint64_t y, uint64_t i)
@@ -212,6 +224,13 @@ static uint64_t pack_loc(uint64_t x, uint64_t y, uint64_t i)
 static uint32_t loc_x(uint64_t l) { return (uint32_t)(l & 0xFFFFFu); }
 static uint32_t loc_y(uint64_t l) { return (uint32_t)((l >> 20) & 0xFFFFFu); }
 static uint32_t loc_i(uint64_t l) { return (uint32_t)(l >> 40); }
+
+/* spatially implicit locations: local individual i at (0, 0, i);
+ * metacommunity individual i at y = 1, with i's low 20 bits in x and the
+ * rest in the deme index */
+static int in_meta(uint64_t l) { return loc_y(l) == 1u; }
+static uint64_t meta_loc(uint64_t i) { return pack_loc(i & 0xFFFFFu, 1, i >> 20); }
+static uint64_t meta_index(uint64_t l) { return ((uint64_t)loc_i(l) << 20) | loc_x(l); }
 
 static uint64_t dbl_bits(double d)
 {
@@ -394,6 +413,16 @@ static uint64_t disperse(const or_model* m, uint32_t sk[2], uint64_t loc, double
     or_draw_pair(sk, loc, tkey, OR_TAG_EVENT, 1, v + 2);
     if (m->kind == OR_NONSPATIAL)
         return pack_loc(0, 0, mulhi64(v[1], m->deme));
+    if (m->kind == OR_IMPLICIT) {
+        /* in the metacommunity: a uniform parent there (draw 1); locally:
+         * migration iff draw 1 says so, then the parent's index (draw 2) in
+         * the metacommunity or the local community */
+        if (in_meta(loc))
+            return meta_loc(mulhi64(v[1], m->meta_size));
+        if ((v[1] >> 11) < (uint64_t)ceil(m->migration * 0x1p53))
+            return meta_loc(mulhi64(v[2], m->meta_size));
+        return pack_loc(0, 0, mulhi64(v[2], m->deme));
+    }
     int64_t x = loc_x(loc), y = loc_y(loc);
     if (m->kind == OR_TORUS) {
         int64_t tx = wrap(x + gauss_offset(m, v[1]), m->width);
@@ -412,7 +441,8 @@ static uint64_t disperse(const or_model* m, uint32_t sk[2], uint64_t loc, double
 
 static int speciates(const or_model* m, uint32_t sk[2], uint64_t loc, double tau)
 {
-    double thr_d = ceil(m->nu * 0x1p53);
+    double nu = (m->kind == OR_IMPLICIT && in_meta(loc)) ? m->meta_nu : m->nu;
+    double thr_d = ceil(nu * 0x1p53);
     uint64_t thr = (uint64_t)thr_d;
     uint64_t v0 = or_draw(sk, loc, dbl_bits(tau), OR_TAG_EVENT, 0);
     return (v0 >> 11) < thr;
@@ -534,6 +564,8 @@ static or_heap_item heap_pop(or_heap_item* h, uint64_t* n)
 
 static uint64_t slot_of(const or_model* m, uint64_t loc)
 {
+    if (m->kind == OR_IMPLICIT)
+        return in_meta(loc) ? (uint64_t)m->deme + meta_index(loc) : loc_i(loc);
     return ((uint64_t)loc_y(loc) * m->width + loc_x(loc)) * (uint64_t)m->deme + loc_i(loc);
 }
 
@@ -547,7 +579,8 @@ int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t m
 {
     uint32_t sk[2];
     or_seed_key(m->seed, sk);
-    uint64_t n_slots = (uint64_t)m->width * m->height * m->deme;
+    uint64_t n_slots = m->kind == OR_IMPLICIT ? (uint64_t)m->deme + m->meta_size
+                                               : (uint64_t)m->width * m->height * m->deme;
     int64_t* occupant = (int64_t*)malloc(n_slots * sizeof(int64_t));
     double* pending = (double*)malloc(n_slots * sizeof(double));
     uint64_t* loc_of = (uint64_t*)malloc(n * sizeof(uint64_t));

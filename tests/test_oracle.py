@@ -477,3 +477,172 @@ def test_samplers_give_different_streams_same_law():
     kb = [_nonspatial_K(500, 2e-2, s, 1) for s in range(1, 121)]
     assert stats.mannwhitneyu(ka, kb).pvalue > 1e-3
     assert (a, b) != (None, None)
+
+
+# --------------------------------------------------------------------------
+# Spatially implicit scenario (background section "Spatially Implicit";
+# appendix of the neutral scenarios): a local community of J individuals
+# whose parent lives with probability m per event in a static metacommunity
+# of J_meta individuals with speciation probability nu_meta.
+# --------------------------------------------------------------------------
+META = (1 << 31) - 1
+
+
+def _implicit(J, nu, seed, m, meta_size, meta_nu, sampler=0):
+    return O.Model(O.IMPLICIT, 1, 1, J, nu, seed, migration=m, meta_size=meta_size, meta_nu=meta_nu,
+                   sampler=sampler)
+
+
+def _meta_index(loc):
+    x, y, i = O.unpack_loc(loc)
+    assert y == 1
+    return (i << 20) | x
+
+
+def test_implicit_dispersal_draws():
+    """a local lineage's parent lives in the metacommunity with probability m,
+    uniform there; otherwise it is uniform over the J local individuals; a
+    metacommunity lineage's parent is uniform over the metacommunity"""
+    J, meta, mig = 40, 30, 0.3
+    m = _implicit(J, 0.0, 9, mig, meta, 0.1)
+    rng = np.random.default_rng(5)
+    local, metah, n = np.zeros(J), np.zeros(meta), 30000
+    for t in rng.uniform(0, 1e4, size=n):
+        loc = m.disperse(O.pack_loc(0, 0, 7), t)
+        x, y, i = O.unpack_loc(loc)
+        if y == 1:
+            metah[_meta_index(loc)] += 1
+        else:
+            assert x == 0 and y == 0
+            local[i] += 1
+    assert abs(metah.sum() / n - mig) < 5 * math.sqrt(mig * (1 - mig) / n)
+    assert stats.chisquare(local).pvalue > 1e-3 and stats.chisquare(metah).pvalue > 1e-3
+    # inside the metacommunity: uniform, never back to the local community
+    hits = np.zeros(meta)
+    for t in rng.uniform(0, 1e4, size=15000):
+        hits[_meta_index(m.disperse(O.pack_loc(11, 1, 0), t))] += 1
+    assert stats.chisquare(hits).pvalue > 1e-3
+    # large metacommunity indices split over x (low 20 bits) and the deme index
+    big = _implicit(J, 0.0, 9, 1.0, META, 0.1)
+    idx = [_meta_index(big.disperse(O.pack_loc(0, 0, 3), t)) for t in rng.uniform(0, 1e4, size=4000)]
+    assert max(idx) < META and max(idx) > (1 << 30) and stats.kstest(np.array(idx) / META, "uniform").pvalue > 1e-3
+
+
+def test_implicit_speciation_by_community():
+    """speciation uses nu locally and nu_meta in the metacommunity"""
+    m = _implicit(20, 0.1, 4, 0.5, 1000, 0.6)
+    rng = np.random.default_rng(6)
+    ts = rng.uniform(0, 1e4, size=20000)
+    loc_rate = np.mean([m.speciates(O.pack_loc(0, 0, 5), t) for t in ts])
+    meta_rate = np.mean([m.speciates(O.pack_loc(123, 1, 0), t) for t in ts])
+    assert abs(loc_rate - 0.1) < 5 * math.sqrt(0.1 * 0.9 / len(ts))
+    assert abs(meta_rate - 0.6) < 5 * math.sqrt(0.6 * 0.4 / len(ts))
+
+
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_implicit_immigrant_ancestors(sampler):
+    """nu_local = 0 and nu_meta = 1: every immigrant ancestor founds its own
+    species at its first event in a metacommunity too large for two of them
+    to meet, so the richness is the number of immigrant ancestors.  That is
+    the theta -> infinity limit of the closed form (appendix "Spatially
+    Implicit"): its law is Ewens' with gamma = J m / (1 - m) in place of
+    theta, E S = sum_{i < J} gamma / (gamma + i) (self-replacement allowed,
+    as for theta in the non-spatial pin)"""
+    J, mig = 500, 0.05
+    Ks = []
+    for seed in range(1, 201):
+        m = _implicit(J, 0.0, seed, mig, META, 1.0, sampler)
+        kl, kt, _ = m.trace(m.sample())
+        Ks.append(O.species_ids(kl, kt)[1])
+    Ks = np.array(Ks)
+    g = J * mig / (1 - mig)
+    expected = sum(g / (g + i) for i in range(J))
+    assert abs(expected - g * (special.digamma(g + J) - special.digamma(g))) < 1e-9
+    se = Ks.std(ddof=1) / math.sqrt(len(Ks))
+    assert abs(Ks.mean() - expected) < 3 * se, (Ks.mean(), expected, se)
+    sd = math.sqrt(sum(g * i / (g + i) ** 2 for i in range(J)))
+    assert 0.75 * sd < Ks.std(ddof=1) < 1.3 * sd
+
+
+def test_implicit_closed_community_is_ewens():
+    """m = 0: the local community is closed and the model is the non-spatial
+    one (Ewens, theta = J nu / (1 - nu)), drawn from different draws"""
+    J, nu = 1000, 0.01
+    Ks = []
+    for seed in range(1, 201):
+        m = _implicit(J, nu, seed, 0.0, 1000, 0.5)
+        kl, kt, _ = m.run_merge(m.sample())
+        Ks.append(O.species_ids(kl, kt)[1])
+    Ks = np.array(Ks)
+    theta = J * nu / (1 - nu)
+    expected = theta * (special.digamma(theta + J) - special.digamma(theta))
+    se = Ks.std(ddof=1) / math.sqrt(len(Ks))
+    assert abs(Ks.mean() - expected) < 3 * se, (Ks.mean(), expected, se)
+
+
+def test_implicit_forward_brute_force():
+    """the forward-time model simulated directly -- J local and J_meta
+    metacommunity individuals, each replaced at rate 1; a local death takes a
+    new species (nu), a metacommunity parent (m) or a local parent (self
+    allowed); a metacommunity death takes a new species (nu_meta) or a
+    metacommunity parent; the metacommunity never sees the local community --
+    has the richness law of the backward oracle"""
+    J, meta, nu, mig, nu_m = 3, 2, 0.05, 0.3, 0.2
+    rng = np.random.default_rng(21)
+    labels = np.arange(J + meta, dtype=np.int64)
+    fresh = J + meta
+    burn, spacing, samples = 3000, 50, 12000
+    steps = burn + spacing * samples
+    u = rng.random((steps, 4))
+    fwd = np.zeros(J)
+    for step in range(steps):
+        dying = int(u[step, 0] * (J + meta))
+        if dying < J:
+            if u[step, 1] < nu:
+                labels[dying] = fresh
+                fresh += 1
+            elif u[step, 2] < mig:
+                labels[dying] = labels[J + int(u[step, 3] * meta)]
+            else:
+                labels[dying] = labels[int(u[step, 3] * J)]
+        else:
+            if u[step, 1] < nu_m:
+                labels[dying] = fresh
+                fresh += 1
+            else:
+                labels[dying] = labels[J + int(u[step, 3] * meta)]
+        if step >= burn and (step - burn) % spacing == 0:
+            fwd[len(set(labels[:J].tolist())) - 1] += 1
+    bwd = np.zeros(J)
+    for seed in range(1, samples + 1):
+        m = _implicit(J, nu, seed, mig, meta, nu_m)
+        kl, kt, _ = m.run_merge(m.sample())
+        bwd[O.species_ids(kl, kt)[1] - 1] += 1
+    assert stats.chi2_contingency(np.vstack([fwd, bwd]))[1] > 1e-3
+
+
+def test_implicit_special_cases():
+    # nu = 1: every lineage speciates at its first (local) event -> S = n
+    m = _implicit(80, 1.0, 3, 0.5, 1000, 0.5)
+    kl, kt, U = m.run_merge(m.sample())
+    assert O.species_ids(kl, kt)[1] == 80 and U == 80
+    # m = 1, nu_meta = 1, no local speciation: every lineage migrates at its
+    # first event and founds a species at its second -> S = n, 2n events
+    m = _implicit(80, 0.0, 3, 1.0, META, 1.0)
+    kl, kt, ne = m.trace(m.sample())
+    assert O.species_ids(kl, kt)[1] == 80 and np.all(ne == 2)
+    assert all(O.unpack_loc(int(l))[1] == 1 for l in kl)
+    # a local community of one individual: S = 1
+    m = _implicit(1, 0.0, 3, 0.2, 5, 0.01)
+    kl, kt, _ = m.run_merge(m.sample())
+    assert O.species_ids(kl, kt)[1] == 1
+
+
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_implicit_mode_p_equals_mode_m(sampler):
+    m = _implicit(700, 1e-3, 42, 0.05, 5000, 0.02, sampler)
+    locs = m.sample()
+    kl, kt, U = m.run_merge(locs)
+    pl, pt, ne = m.trace(locs)
+    assert np.array_equal(kl, pl) and np.array_equal(kt, pt)
+    assert ne.sum() >= U
