@@ -58,7 +58,7 @@ typedef enum {
 } ind_status;
 
 /* landscape kinds */
-enum { IND_NONSPATIAL = 0, IND_TORUS = 1, IND_MAP = 2 };
+enum { IND_NONSPATIAL = 0, IND_TORUS = 1, IND_MAP = 2, IND_IMPLICIT = 3 };
 /* dispersal kinds */
 enum { IND_DISPERSAL_UNIFORM = 0, IND_DISPERSAL_GAUSSIAN = 1, IND_DISPERSAL_ALIAS_GAUSSIAN = 2 };
 
@@ -70,6 +70,20 @@ enum { IND_DISPERSAL_UNIFORM = 0, IND_DISPERSAL_GAUSSIAN = 1, IND_DISPERSAL_ALIA
  *    requires IND_DISPERSAL_GAUSSIAN.
  *  IND_MAP: width x height cells, deme_map[y * width + x] individuals in each
  *    (0 = not habitable), wrapped; requires IND_DISPERSAL_ALIAS_GAUSSIAN.
+ *  IND_IMPLICIT: the spatially implicit scenario (section "Spatially
+ *    Implicit"): a local community of J = deme individuals (width = height
+ *    = 1), closed by a static metacommunity of meta_size individuals.  At
+ *    an event of a local lineage the stream's draw 0 decides speciation
+ *    (nu), draw 1 migration (probability `migration`), and draw 2 the
+ *    parent's index: uniform over the metacommunity after a migration,
+ *    else uniform over the J local individuals (the parent's own included).
+ *    In the metacommunity, draw 0 decides speciation (meta_nu) and draw 1
+ *    picks a uniform metacommunity parent; lineages never return.  Local
+ *    individual i sits at location (0, 0, i); metacommunity individual i at
+ *    x = i mod 2^20, y = 1, deme index i >> 20.  Only local individuals are
+ *    sampled.  Requires IND_DISPERSAL_UNIFORM; 0 <= migration <= 1;
+ *    1 <= meta_size <= 2^31; 0 < meta_nu <= 1; nu may be 0 here (but not
+ *    together with migration = 0).
  * Limits: width, height <= 2^20; deme <= 2^23 - 1 (non-spatial J likewise);
  * width * height * deme < 2^32 (map: width * height * 255); lambda > 0 and
  * finite; delta_t a power of two in [2^-20, 2^20]; lambda * delta_t >= 2^-20.
@@ -90,6 +104,10 @@ typedef struct {
      *    in the interval (section "Homogeneous Poisson Point Process");
      *    requires lambda * delta_t <= 64. */
     int32_t event_sampler;
+    /* IND_IMPLICIT only (ignored otherwise): */
+    double migration;   /* probability that a local lineage's parent lives in the metacommunity */
+    uint64_t meta_size; /* metacommunity individuals */
+    double meta_nu;     /* speciation probability per event in the metacommunity */
 } ind_landscape;
 
 enum { IND_SAMPLER_EXP = 0, IND_SAMPLER_POISSON = 1 };
@@ -177,7 +195,8 @@ void ind_default_tuning(ind_tuning* out);
 /* Create a simulation: validates the arguments, copies the deme map,
  * derives the stream key from seed, and builds the dispersal tables on the
  * device (for IND_MAP: one alias row per habitable cell, 8 bytes per disk
- * offset).  nu is the speciation probability per event, 0 < nu <= 1.
+ * offset).  nu is the speciation probability per event, 0 < nu <= 1 (IND_IMPLICIT:
+ * the local community's, 0 <= nu <= 1).
  * cuda_stream is a cudaStream_t (NULL: legacy default stream). */
 ind_status sim_create(const ind_landscape* landscape, const ind_dispersal* dispersal, double nu,
                       uint64_t seed, void* cuda_stream, ind_sim** out);

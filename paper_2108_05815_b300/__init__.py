@@ -16,7 +16,7 @@ import threading
 
 import numpy as np
 
-NONSPATIAL, TORUS, MAP = 0, 1, 2
+NONSPATIAL, TORUS, MAP, IMPLICIT = 0, 1, 2, 3
 SAMPLER_EXP, SAMPLER_POISSON = 0, 1
 DISPERSAL_UNIFORM, DISPERSAL_GAUSSIAN, DISPERSAL_ALIAS_GAUSSIAN = 0, 1, 2
 
@@ -38,7 +38,8 @@ class IndError(RuntimeError):
 class Landscape(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("deme", ctypes.c_uint32), ("deme_map", ctypes.c_void_p), ("lambda_", ctypes.c_double),
-                ("delta_t", ctypes.c_double), ("event_sampler", ctypes.c_int32)]
+                ("delta_t", ctypes.c_double), ("event_sampler", ctypes.c_int32),
+                ("migration", ctypes.c_double), ("meta_size", ctypes.c_uint64), ("meta_nu", ctypes.c_double)]
 
 
 class Dispersal(ctypes.Structure):
@@ -185,10 +186,16 @@ def _tuning(kw):
     return t
 
 
-def landscape(kind, width=1, height=1, deme=1, deme_map=None, lam=1.0, delta_t=1.0, sampler=0):
+_DISPERSAL_OF = {NONSPATIAL: DISPERSAL_UNIFORM, TORUS: DISPERSAL_GAUSSIAN, MAP: DISPERSAL_ALIAS_GAUSSIAN,
+                 IMPLICIT: DISPERSAL_UNIFORM}
+
+
+def landscape(kind, width=1, height=1, deme=1, deme_map=None, lam=1.0, delta_t=1.0, sampler=0,
+              migration=0.0, meta_size=0, meta_nu=0.0):
     L = Landscape()
     L.kind, L.width, L.height, L.deme, L.lambda_, L.delta_t = kind, width, height, deme, lam, delta_t
     L.event_sampler = sampler
+    L.migration, L.meta_size, L.meta_nu = float(migration), int(meta_size), float(meta_nu)
     keep = None
     if deme_map is not None:
         if hasattr(deme_map, "data_ptr"):
@@ -210,10 +217,12 @@ class Simulation:
     """One simulation (sim_create ... sim_destroy)."""
 
     def __init__(self, kind, nu, seed, width=1, height=1, deme=1, sigma=0.0, radius=0, deme_map=None,
-                 lam=1.0, delta_t=1.0, stream=None, tuning=None, sampler=0):
+                 lam=1.0, delta_t=1.0, stream=None, tuning=None, sampler=0, migration=0.0, meta_size=0,
+                 meta_nu=0.0):
         use_torch_allocator()
-        L, keep = landscape(kind, width, height, deme, deme_map, lam, delta_t, sampler)
-        dk = {NONSPATIAL: DISPERSAL_UNIFORM, TORUS: DISPERSAL_GAUSSIAN, MAP: DISPERSAL_ALIAS_GAUSSIAN}[kind]
+        L, keep = landscape(kind, width, height, deme, deme_map, lam, delta_t, sampler, migration, meta_size,
+                            meta_nu)
+        dk = _DISPERSAL_OF[kind]
         D = dispersal(dk, sigma, radius)
         self._h = ctypes.c_void_p()
         self._stream = _stream(stream)
@@ -345,9 +354,11 @@ def habitat(map_seed, width, height, p_habitable=0.6, max_deme=8, out=None, stre
     return out
 
 
-def mem_estimate(kind, width=1, height=1, deme=1, sigma=0.0, radius=0, fraction=1.0, lam=1.0, delta_t=1.0):
-    dk = {NONSPATIAL: DISPERSAL_UNIFORM, TORUS: DISPERSAL_GAUSSIAN, MAP: DISPERSAL_ALIAS_GAUSSIAN}[kind]
-    L, _ = landscape(kind, width, height, deme, np.ones(1, np.uint8) if kind == MAP else None, lam, delta_t)
+def mem_estimate(kind, width=1, height=1, deme=1, sigma=0.0, radius=0, fraction=1.0, lam=1.0, delta_t=1.0,
+                 migration=0.0, meta_size=1, meta_nu=1.0):
+    dk = _DISPERSAL_OF[kind]
+    L, _ = landscape(kind, width, height, deme, np.ones(1, np.uint8) if kind == MAP else None, lam, delta_t, 0,
+                     migration, meta_size, meta_nu)
     D = dispersal(dk, sigma, radius)
     return int(lib().sim_mem_estimate(ctypes.byref(L), ctypes.byref(D), float(fraction)))
 

@@ -18,6 +18,7 @@ constexpr uint32_t TAG_SAMPLE = 4u;
 constexpr int KIND_NONSPATIAL = 0;
 constexpr int KIND_TORUS = 1;
 constexpr int KIND_MAP = 2;
+constexpr int KIND_IMPLICIT = 3;  // local community + static metacommunity
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -186,6 +187,15 @@ __host__ __device__ __forceinline__ uint64_t pack_loc(uint64_t x, uint64_t y, ui
 __host__ __device__ __forceinline__ uint32_t loc_x(uint64_t l) { return (uint32_t)(l & 0xFFFFFu); }
 __host__ __device__ __forceinline__ uint32_t loc_y(uint64_t l) { return (uint32_t)((l >> 20) & 0xFFFFFu); }
 __host__ __device__ __forceinline__ uint32_t loc_i(uint64_t l) { return (uint32_t)(l >> 40); }
+
+// spatially implicit model: local individual i at (0, 0, i); metacommunity
+// individual i at y = 1 with i's low 20 bits in x and the rest in the deme
+// index
+__host__ __device__ __forceinline__ bool in_meta(uint64_t l) { return loc_y(l) != 0u; }
+__host__ __device__ __forceinline__ uint64_t meta_loc(uint64_t i) { return pack_loc(i & 0xFFFFFu, 1, i >> 20); }
+__host__ __device__ __forceinline__ uint64_t meta_index(uint64_t l) {
+    return ((uint64_t)loc_i(l) << 20) | loc_x(l);
+}
 
 __device__ __forceinline__ uint32_t wrap_add(uint32_t x, int32_t d, uint32_t n) {
     // (x + d) mod n for |d| < 2^24, x < n <= 2^20

@@ -177,6 +177,9 @@ struct SimParams {
     uint64_t slot_base;        // first global slot index of this simulation
     uint32_t gid_base;         // first global lineage id of this simulation
     uint32_t coop_short;       // lambda dt <= 2: the warp-cooperative searches look 4 intervals ahead
+    uint64_t meta_size;        // spatially implicit: metacommunity individuals
+    uint64_t m_thr;            // spatially implicit: ceil(migration 2^53)
+    uint64_t meta_nu_thr;      // spatially implicit: ceil(meta_nu 2^53)
     const uint64_t* sample_loc;  // n_lineages sampled locations
     double events_per_round;
     double min_events;
@@ -620,7 +623,9 @@ __device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau
 // dispersal target from the event stream's draws 1, 2, 3 (draw 0 decided
 // speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index),
 // each axis a discretised normal by inversion, -half + #{k : cdf[k] <= d};
-// map d1 (alias column and threshold), d2 (deme index)
+// map d1 (alias column and threshold), d2 (deme index); spatially implicit
+// d1 (migration, or the metacommunity parent), d2 (parent after migration
+// or locally)
 // (KIND: the landscape kind when the caller knows it at compile time, -1
 // for the simulation's own)
 template <int KIND = -1>
@@ -629,6 +634,15 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     const int kind = KIND >= 0 ? KIND : c.kind;
     if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
     const SimParams* p = P + c.sim;
+    if (kind == KIND_IMPLICIT) {
+        // in the metacommunity: a uniform parent there (d1); locally:
+        // migration iff d1 says so, then the parent's index (d2) in the
+        // metacommunity or the local community
+        const uint64_t meta_n = __ldg(&p->meta_size);
+        if (in_meta(loc)) return meta_loc(umulhi64(d1, meta_n));
+        if ((d1 >> 11) < __ldg(&p->m_thr)) return meta_loc(umulhi64(d2, meta_n));
+        return pack_loc(0, 0, umulhi64(d2, c.D));
+    }
     const uint32_t x = loc_x(loc), y = loc_y(loc);
     if (kind == KIND_TORUS) {
         // both guide entries first, so that the two loads overlap; a table
@@ -662,14 +676,21 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     return pack_loc(tx, ty, umulhi64(d2, d));
 }
 
+// speciation threshold at loc: the metacommunity's in the spatially
+// implicit model, else the simulation's
+__device__ __forceinline__ uint64_t spec_thr(const LaneSim& c, const SimParams* __restrict__ P, int kind,
+                                             uint64_t loc) {
+    return (kind == KIND_IMPLICIT && in_meta(loc)) ? __ldg(&P[c.sim].meta_nu_thr) : c.nu_thr;
+}
+
 // one event at (loc, tau); returns true if the lineage speciated, else
 // moves loc to the dispersal target
 __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
                                          double tau) {
     const uint64_t tk = (uint64_t)__double_as_longlong(tau);
     const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
-    if (c.kind == KIND_NONSPATIAL) {
-        if ((b0.lo >> 11) < c.nu_thr) return true;
+    if (c.kind == KIND_NONSPATIAL || (c.kind == KIND_IMPLICIT && in_meta(loc))) {
+        if ((b0.lo >> 11) < spec_thr(c, P, c.kind, loc)) return true;
         loc = disperse(c, P, loc, b0.hi, 0ull, 0ull);
         return false;
     }
@@ -696,14 +717,24 @@ __device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams*
     const u64x2 b = stream_block(c.sk0, c.sk1, loc, tk, lane & 1u, TAG_EVENT);
     const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0), d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
     const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1), d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
-    if ((d0 >> 11) < c.nu_thr) return true;
+    if ((d0 >> 11) < spec_thr(c, P, kind, loc)) return true;
     loc = disperse<KIND>(c, P, loc, d1, d2, d3);
     return false;
 }
 
+// global slot index of a location: cells row-major x slot_deme + deme
+// index, after the simulation's slot_base; the spatially implicit model
+// numbers its J local individuals first, then the metacommunity
+__device__ __forceinline__ uint64_t slot_index(const SimParams* __restrict__ p, uint64_t loc) {
+    const uint64_t base = __ldg(&p->slot_base);
+    if (__ldg(&p->kind) == KIND_IMPLICIT)
+        return base + (in_meta(loc) ? (uint64_t)__ldg(&p->D) + meta_index(loc) : (uint64_t)loc_i(loc));
+    const uint64_t cell = (uint64_t)loc_y(loc) * __ldg(&p->W) + loc_x(loc);
+    return base + cell * __ldg(&p->slot_deme) + loc_i(loc);
+}
+
 __device__ __forceinline__ uint64_t slot_key(const SimParams* __restrict__ P, const LaneSim& c, uint64_t loc) {
-    const uint64_t cell = (uint64_t)loc_y(loc) * c.W + loc_x(loc);
-    return __ldg(&P[c.sim].slot_base) + cell * __ldg(&P[c.sim].slot_deme) + loc_i(loc);
+    return slot_index(P + c.sim, loc);
 }
 
 // exact distinct-event counting: insert (slot, time bits); true if new
@@ -1073,12 +1104,12 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
             ++ev_raw;
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
-            if ((b.lo >> 11) < c.nu_thr) {
+            if ((b.lo >> 11) < spec_thr(c, B.P, c.kind, loc)) {
                 B.key_loc[gid] = loc;
                 B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
                 L.gid[idx] = gid | DONE_BIT;
                 st = SM_IDLE;
-            } else if (c.kind == KIND_NONSPATIAL) {
+            } else if (c.kind == KIND_NONSPATIAL || (c.kind == KIND_IMPLICIT && in_meta(loc))) {
                 loc = disperse(c, B.P, loc, b.hi, 0ull, 0ull);
                 begin_search();
             } else {
@@ -1276,10 +1307,7 @@ __global__ void k_compact(BatchDev B) {
                 tn = in.tn[i];
                 survive = true;
                 if (B.dedup) {
-                    const SimParams* p = B.P + s;
-                    const uint64_t cell = (uint64_t)loc_y(loc) * p->W + loc_x(loc);
-                    const uint64_t sk = p->slot_base + cell * p->slot_deme + loc_i(loc);
-                    const uint32_t w = dedup_lookup(B, t, sk);
+                    const uint32_t w = dedup_lookup(B, t, slot_index(B.P + s, loc));
                     if (w != g && w != 0xFFFFFFFFu) {
                         B.parent[g] = w;
                         survive = false;
@@ -1921,6 +1949,12 @@ static std::vector<uint32_t> fine_guide(const std::vector<uint64_t>& cdf) {
     return g;
 }
 
+// slots a simulation takes in a batch's numbering of indexed locations
+static uint64_t slot_span(const ind_sim* m) {
+    if (m->land.kind == IND_IMPLICIT) return (uint64_t)m->land.deme + m->land.meta_size;
+    return (uint64_t)m->land.width * m->land.height * m->slot_deme;
+}
+
 // the per-simulation device parameters shared by batches and the server
 static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     memset(&p, 0, sizeof(p));
@@ -1949,6 +1983,11 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.n_off = m->n_off;
     const double mu = m->land.lambda * m->land.delta_t;  // mean points per re-prime interval
     p.coop_short = mu <= 2.0 && (m->land.event_sampler != IND_SAMPLER_POISSON || mu >= 0.5) ? 1u : 0u;
+    if (m->land.kind == IND_IMPLICIT) {
+        p.meta_size = m->land.meta_size;
+        p.m_thr = (uint64_t)std::ceil(m->land.migration * 0x1p53);
+        p.meta_nu_thr = (uint64_t)std::ceil(m->land.meta_nu * 0x1p53);
+    }
     p.sample_loc = m->d_sample;
     p.events_per_round = tun.events_per_round;
     p.min_events = tun.min_events_per_lineage;
@@ -1985,7 +2024,8 @@ static cudaError_t set_coop_smem() {
 template <bool COUNT, int MODE>
 static void launch_coop_kind(const Batch& b, size_t smem, cudaStream_t s) {
     const dim3 g(b.adv_blocks), t(b.adv_threads);
-    if (COUNT || b.coop_kind < 0) k_advance_coop<COUNT, MODE, -1><<<g, t, smem, s>>>(b.dev);
+    if (COUNT || b.coop_kind < 0 || b.coop_kind > KIND_MAP)  // counting runs and mixed or implicit batches
+        k_advance_coop<COUNT, MODE, -1><<<g, t, smem, s>>>(b.dev);
     else if (b.coop_kind == KIND_NONSPATIAL) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 0)><<<g, t, smem, s>>>(b.dev);
     else if (b.coop_kind == KIND_TORUS) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 1)><<<g, t, smem, s>>>(b.dev);
     else k_advance_coop<COUNT, MODE, (COUNT ? -1 : 2)><<<g, t, smem, s>>>(b.dev);
@@ -2013,7 +2053,7 @@ static ind_status batch_build(Batch& b) {
         p.gid_base = (uint32_t)lin;
         gid_base[s] = (uint32_t)lin;
         lin += m->n_sampled;
-        slots += (uint64_t)m->land.width * m->land.height * m->slot_deme;
+        slots += slot_span(m);
     }
     if (lin >= (1ull << 31)) return IND_ERR_ARG;
     b.n_lin = (uint32_t)lin;
@@ -2463,7 +2503,9 @@ static int pow2_log2(double v, bool* ok) {
 
 static ind_status validate(const ind_landscape* L, const ind_dispersal* D, double nu, int* dt_log2) {
     if (!L || !D) return IND_ERR_ARG;
-    if (!(nu > 0.0 && nu <= 1.0)) return IND_ERR_ARG;
+    // the spatially implicit model may leave speciation to its metacommunity
+    const bool nu_ok = L->kind == IND_IMPLICIT ? (nu >= 0.0 && nu <= 1.0) : (nu > 0.0 && nu <= 1.0);
+    if (!nu_ok) return IND_ERR_ARG;
     if (!(L->lambda > 0.0) || !std::isfinite(L->lambda)) return IND_ERR_ARG;
     bool ok = false;
     *dt_log2 = pow2_log2(L->delta_t, &ok);
@@ -2483,6 +2525,13 @@ static ind_status validate(const ind_landscape* L, const ind_dispersal* D, doubl
         if (!L->deme_map) return IND_ERR_ARG;
         if (D->kind != IND_DISPERSAL_ALIAS_GAUSSIAN) return IND_ERR_ARG;
         if (!(D->sigma > 0.0 && D->sigma <= 64.0) || D->radius < 1 || D->radius > 40) return IND_ERR_ARG;
+    } else if (L->kind == IND_IMPLICIT) {
+        if (L->width != 1 || L->height != 1 || L->deme < 1 || L->deme >= (1u << 23)) return IND_ERR_ARG;
+        if (D->kind != IND_DISPERSAL_UNIFORM) return IND_ERR_ARG;
+        if (!(L->migration >= 0.0 && L->migration <= 1.0)) return IND_ERR_ARG;
+        if (L->meta_size < 1 || L->meta_size > (1ull << 31)) return IND_ERR_ARG;
+        if (!(L->meta_nu > 0.0 && L->meta_nu <= 1.0)) return IND_ERR_ARG;
+        if (nu == 0.0 && L->migration == 0.0) return IND_ERR_ARG;  // no lineage could ever end
     } else {
         return IND_ERR_ARG;
     }

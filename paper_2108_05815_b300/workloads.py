@@ -22,7 +22,7 @@ import math
 
 import numpy as np
 
-NONSPATIAL, TORUS, MAP = 0, 1, 2
+NONSPATIAL, TORUS, MAP, IMPLICIT = 0, 1, 2, 3
 
 
 def config1(seed=42):

@@ -74,6 +74,24 @@ def test_invalid_arguments_are_rejected(lib, case):
     assert _create(lib, L, D, case["nu"]) == -1
 
 
+@pytest.mark.parametrize("case", [
+    dict(nu=0.0, migration=0.0, meta_size=10, meta_nu=0.5),              # no lineage could ever end
+    dict(nu=1e-3, migration=0.1, meta_size=0, meta_nu=0.5),              # empty metacommunity
+    dict(nu=1e-3, migration=0.1, meta_size=(1 << 31) + 1, meta_nu=0.5),  # metacommunity too large
+    dict(nu=1e-3, migration=1.5, meta_size=10, meta_nu=0.5),             # migration > 1
+    dict(nu=1e-3, migration=-0.1, meta_size=10, meta_nu=0.5),
+    dict(nu=1e-3, migration=0.1, meta_size=10, meta_nu=0.0),             # meta_nu = 0
+    dict(nu=-1e-3, migration=0.1, meta_size=10, meta_nu=0.5),
+    dict(nu=1e-3, migration=0.1, meta_size=10, meta_nu=0.5, width=2),    # the local community is 1 x 1
+    dict(nu=1e-3, migration=0.1, meta_size=10, meta_nu=0.5, dk=1),       # dispersal must be uniform
+])
+def test_implicit_invalid_arguments_are_rejected(lib, case):
+    L, _ = ind.landscape(ind.IMPLICIT, case.get("width", 1), 1, 100, None, 1.0, 1.0, 0, case["migration"],
+                         case["meta_size"], case["meta_nu"])
+    D = ind.dispersal(case.get("dk", 0), 1.0)
+    assert _create(lib, L, D, case["nu"]) == -1
+
+
 def test_null_arguments(lib):
     assert lib.sim_create(None, None, 0.5, 1, None, None) == -1
     assert lib.sim_sample(None, 1.0, 0, None) == -1

@@ -29,7 +29,9 @@ def _gpu():
 def gpu_sim(cfg, deme_map=None, tuning=None):
     kw = dict(width=cfg.get("width", 1), height=cfg.get("height", 1), deme=cfg.get("deme", 1),
               sigma=cfg.get("sigma", 0.0), radius=cfg.get("radius", 0), lam=cfg.get("lam", 1.0),
-              delta_t=cfg.get("delta_t", 1.0), tuning=tuning, sampler=cfg.get("sampler", 0))
+              delta_t=cfg.get("delta_t", 1.0), tuning=tuning, sampler=cfg.get("sampler", 0),
+              migration=cfg.get("migration", 0.0), meta_size=cfg.get("meta_size", 0),
+              meta_nu=cfg.get("meta_nu", 0.0))
     if cfg["kind"] == W.MAP:
         kw["deme_map"] = deme_map
     return ind.Simulation(cfg["kind"], cfg["nu"], cfg["seed"], **kw)
@@ -39,7 +41,8 @@ def oracle_model(cfg, deme_map=None):
     return O.Model(cfg["kind"], cfg.get("width", 1), cfg.get("height", 1), cfg.get("deme", 1), cfg["nu"],
                    cfg["seed"], lam=cfg.get("lam", 1.0), delta_t=cfg.get("delta_t", 1.0),
                    sigma=cfg.get("sigma"), radius=cfg.get("radius"), deme_map=deme_map,
-                   sampler=cfg.get("sampler", 0))
+                   sampler=cfg.get("sampler", 0), migration=cfg.get("migration", 0.0),
+                   meta_size=cfg.get("meta_size", 0), meta_nu=cfg.get("meta_nu", 0.0))
 
 
 def run_gpu(cfg, deme_map=None, tuning=None, fraction=1.0, sample_seed=0):
@@ -206,7 +209,11 @@ def test_batch_equals_alone():
             dict(kind=W.TORUS, width=20, height=20, deme=4, sigma=1.0, nu=1e-1, seed=7),
             dict(kind=W.NONSPATIAL, width=1, height=1, deme=1, nu=1e-4, seed=8),
             dict(kind=W.TORUS, width=70, height=50, deme=2, sigma=2.0, nu=2e-3, seed=9, sampler=1),
-            dict(kind=W.NONSPATIAL, width=1, height=1, deme=5000, nu=1e-3, seed=10, sampler=1)]
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=5000, nu=1e-3, seed=10, sampler=1),
+            dict(kind=W.IMPLICIT, width=1, height=1, deme=3000, nu=0.0, seed=11, migration=0.02,
+                 meta_size=4000, meta_nu=3e-3),
+            dict(kind=W.IMPLICIT, width=1, height=1, deme=800, nu=1e-3, seed=12, migration=0.1,
+                 meta_size=(1 << 31), meta_nu=0.5, sampler=1)]
     alone = [run_gpu(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
     sims = [gpu_sim(c, dm if c["kind"] == W.MAP else None) for c in cfgs]
     for s in sims:
@@ -332,3 +339,61 @@ def test_cooperative_map_parity():
     for sampler in (0, 1):
         cfg = dict(kind=W.MAP, width=50, height=50, sigma=3.0, radius=9, nu=8e-3, seed=33, sampler=sampler)
         assert_same(run_gpu(cfg, dm, tuning=dict(coop_lineages=1 << 30)), run_oracle(cfg, dm))
+
+
+# --------------------------------------------------------------------------
+# spatially implicit scenario (local community + static metacommunity)
+# --------------------------------------------------------------------------
+IMPLICIT_CFGS = [
+    # immigrant-ancestor regime of the oracle pin (every ancestor its own species)
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=500, nu=0.0, seed=7, migration=0.05, meta_size=(1 << 31) - 1,
+         meta_nu=1.0),
+    # coalescence in a small metacommunity, local speciation too
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=2000, nu=1e-4, seed=8, migration=0.02, meta_size=5000,
+         meta_nu=2e-3),
+    # metacommunity indices above 2^20 (split over x and the deme index)
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=3000, nu=0.0, seed=9, migration=0.3, meta_size=3 << 28,
+         meta_nu=1e-3),
+    # closed local community (m = 0), and every lineage leaving at once (m = 1)
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=1500, nu=2e-3, seed=10, migration=0.0, meta_size=10, meta_nu=0.5),
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=400, nu=0.0, seed=11, migration=1.0, meta_size=600, meta_nu=1e-2),
+    # other rates and re-prime intervals
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=700, nu=5e-4, seed=12, migration=0.05, meta_size=900, meta_nu=5e-3,
+         lam=2.5, delta_t=0.5),
+]
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+@pytest.mark.parametrize("idx", range(len(IMPLICIT_CFGS)))
+def test_implicit_parity(idx, sampler):
+    """species identities, keys and the exact unique-event count equal the
+    oracle's, for both event-time samplers"""
+    cfg = dict(IMPLICIT_CFGS[idx], sampler=sampler)
+    if cfg["meta_size"] > (1 << 24):
+        # too many indexed locations for the oracle's event-ordered mode:
+        # compare with its per-lineage traces
+        m = oracle_model(cfg)
+        locs = m.sample()
+        kl, kt, _ = m.trace(locs)
+        ids, K = O.species_ids(kl, kt)
+        o = dict(n=len(locs), ids=ids, K=K, kl=kl, kt=kt)
+        assert_same(run_gpu(cfg), o)
+        return
+    o = run_oracle(cfg)
+    g = run_gpu(cfg, tuning=dict(count_unique=1))
+    assert_same(g, o)
+    assert g["stats"]["unique_events"] == o["U"]
+
+
+@pytest.mark.parametrize("tuning", [dict(coop_lineages=0), dict(coop_lineages=1 << 30),
+                                    dict(advance_variant=0, coop_lineages=0), dict(dedup=0),
+                                    dict(occupancy_step=4.0, tail_events=4096.0)])
+def test_implicit_tunings(tuning):
+    cfg = IMPLICIT_CFGS[1]
+    assert_same(run_gpu(cfg, tuning=tuning), run_oracle(cfg))
+
+
+def test_implicit_sampled_fraction():
+    cfg = IMPLICIT_CFGS[1]
+    assert_same(run_gpu(cfg, fraction=0.3, sample_seed=5), run_oracle(cfg, fraction=0.3, sample_seed=5))
+

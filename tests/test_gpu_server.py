@@ -29,12 +29,15 @@ REQUESTS = [
     dict(kind=W.TORUS, width=200, height=200, deme=1, sigma=3.0, nu=3e-4, seed=16, fraction=0.05, sample_seed=5),
     dict(kind=W.NONSPATIAL, width=1, height=1, deme=20000, nu=1e-3, seed=17, fraction=0.3, sample_seed=6),
     dict(kind=W.TORUS, width=50, height=40, deme=3, sigma=7.5, nu=5e-2, seed=18, fraction=1.0, sample_seed=0),
+    dict(kind=W.IMPLICIT, width=1, height=1, deme=1500, nu=0.0, seed=19, fraction=0.7, sample_seed=2,
+         migration=0.03, meta_size=4000, meta_nu=4e-3),
 ]
 
 
 def make(r):
     s = ind.Simulation(r["kind"], r["nu"], r["seed"], width=r["width"], height=r["height"], deme=r["deme"],
-                       sigma=r.get("sigma", 0.0))
+                       sigma=r.get("sigma", 0.0), migration=r.get("migration", 0.0),
+                       meta_size=r.get("meta_size", 0), meta_nu=r.get("meta_nu", 0.0))
     s.sample(r["fraction"], r["sample_seed"])
     return s
 
@@ -75,7 +78,7 @@ def serve(reqs, budget, max_sims, rounds, arrivals):
 
 def test_served_mix_equals_alone():
     ref = [alone(r) for r in REQUESTS]
-    arrivals = [0, 0, 1, 3, 3, 5, 8, 13]
+    arrivals = [0, 0, 1, 3, 3, 5, 8, 13, 4]
     got, st = serve(REQUESTS, budget=1 << 33, max_sims=64, rounds=4, arrivals=arrivals)
     assert st["finished"] == len(REQUESTS) and st["resident"] == 0 and st["queued"] == 0
     for k in range(len(REQUESTS)):
@@ -97,7 +100,8 @@ def test_served_matches_oracle_under_tight_budget():
     got, st = serve(reqs, budget=budget, max_sims=3, rounds=2, arrivals=[0] * len(reqs))
     assert st["finished"] == len(reqs)
     for k, r in enumerate(reqs):
-        m = O.Model(r["kind"], r["width"], r["height"], r["deme"], r["nu"], r["seed"], sigma=r.get("sigma"))
+        m = O.Model(r["kind"], r["width"], r["height"], r["deme"], r["nu"], r["seed"], sigma=r.get("sigma"),
+                    migration=r.get("migration", 0.0), meta_size=r.get("meta_size", 0), meta_nu=r.get("meta_nu", 0.0))
         kl, kt, _ = m.run_merge(m.sample(r["fraction"], r["sample_seed"]))
         oids, oK = O.species_ids(kl, kt)
         ids, K, gkl, gkt = got[k]
