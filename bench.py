@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="simulations in the batched-vs-plain comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
-    ap.add_argument("--workload", default="config2", choices=["config2", "batch", "served"])
+    ap.add_argument("--workload", default="config2", choices=["config2", "batch", "served", "implicit"])
     ap.add_argument("--sampler", default="exp", choices=["exp", "poisson"],
                     help="event-time sampler of the headline (the other is reported beside it)")
     ap.add_argument("--window", type=float, default=60.0, help="served: arrival window in seconds")
@@ -161,11 +161,28 @@ SAMPLER = {"exp": 0, "poisson": 1}
 _sampler = 0
 
 
-def make_sim(ind, seed=42, tuning=None, sampler=None):
+IMPLICIT_WORKLOAD = ("implicit: spatially implicit local community of 100000 individuals (all sampled), "
+                     "migration 0.01 per event, static metacommunity of 1e9 individuals with nu_meta=1e-4, "
+                     "local nu=0, lambda=1, delta_t=1, seed=42")
+# the single-simulation workload of this run: (parameters of seed, description,
+# sampled individuals, host-to-device bytes of the tables and parameters)
+_single = {}
+
+
+def single_workload(name):
     from paper_2108_05815_b300 import workloads as W
-    c = W.config2(seed)
+    if name == "implicit":
+        return dict(params=W.implicit, desc=IMPLICIT_WORKLOAD, n=100000, h2d=400, dataset="implicit")
+    # discretised-normal table (2 x 20 x 8 B) + simulation parameters
+    return dict(params=W.config2, desc=WORKLOAD, n=65536, h2d=8 * 2 * 20 + 400, dataset="config2")
+
+
+def make_sim(ind, seed=42, tuning=None, sampler=None):
+    c = _single["params"](seed)
     return ind.Simulation(c["kind"], c["nu"], c["seed"], width=c["width"], height=c["height"], deme=c["deme"],
-                          sigma=c["sigma"], tuning=tuning, sampler=_sampler if sampler is None else sampler)
+                          sigma=c.get("sigma", 0.0), migration=c.get("migration", 0.0),
+                          meta_size=c.get("meta_size", 0), meta_nu=c.get("meta_nu", 0.0), tuning=tuning,
+                          sampler=_sampler if sampler is None else sampler)
 
 
 def unique_events(ind, seed, sampler=None):
@@ -189,7 +206,8 @@ def run_ours(args, rank, world, local, pg):
 
     sim = make_sim(ind, 42, tuning=dict(profile=1))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    ids = torch.empty(65536, dtype=torch.int64, device=dev)
+    n_ind = _single["n"]
+    ids = torch.empty(n_ind, dtype=torch.int64, device=dev)
 
     def step():
         sim.sample()
@@ -240,7 +258,7 @@ def run_ours(args, rank, world, local, pg):
     value = U * world / (ms_step_max * 1e-3)
 
     # end to end through the public API with host buffers
-    host_ids = torch.empty(65536, dtype=torch.int64, pin_memory=True)
+    host_ids = torch.empty(n_ind, dtype=torch.int64, pin_memory=True)
     e2e_ms = []
     for _ in range(max(3, args.steps // 2)):
         torch.cuda.synchronize()
@@ -253,8 +271,8 @@ def run_ours(args, rank, world, local, pg):
         s2.close()
         e2e_ms.append((h1 - h0) * 1e3)
     e2e_ms_max = allreduce_max(pg, statistics.median(e2e_ms))
-    h2d = 8 * 2 * 20 + 400  # discretised-normal table (2 x 20 x 8 B) + simulation parameters
-    d2h = 65536 * 8 + 64    # species identities + completion flags
+    h2d = _single["h2d"]
+    d2h = n_ind * 8 + 64    # species identities + completion flags
 
     # batched vs plain on `batch` independent replicas of the workload
     seeds = [42 + k for k in range(args.batch)]
@@ -311,7 +329,7 @@ def run_ours(args, rank, world, local, pg):
     # events).
     crit = st["critical_events"]
     lone = make_sim(ind, 42, tuning=dict(profile=1))
-    lone.sample(8.0 / 65536.0, 1)
+    lone.sample(8.0 / n_ind, 1)
     assert lone.run()
     ls = lone.stats()
     lone.close()
@@ -331,12 +349,14 @@ def run_ours(args, rank, world, local, pg):
     achieved = events_per_launch * ops_per_event / (avg_launch_ms * 1e-3) / 1e12
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sm_count * INT32_LANES_PER_SM * 2032e6 / 1e12
-    cpu = cpu_baseline(args.cpu_seconds) if rank == 0 else None
+    cpu = None
+    if rank == 0:
+        cpu = cpu_baseline_traces(args.cpu_seconds) if _single["dataset"] == "implicit" else cpu_baseline(args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "event_sampler": args.sampler,
+        "config": {"workload": _single["desc"], "event_sampler": args.sampler,
                    "parallelism": "replicas (one independent simulation per GPU)",
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "unique_events_per_step": U, "raw_events_per_step": raw_per_step,
@@ -346,10 +366,11 @@ def run_ours(args, rank, world, local, pg):
         "roofline": {"bound": "alu", "kernel": "k_advance_coop + k_advance (one round: both launched, one works)",
                      "achieved": achieved, "peak": peak,
                      "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
-                     "traffic": TRAFFIC_PER_ROUND.get(args.sampler),
+                     "traffic": TRAFFIC_PER_ROUND.get(args.sampler) if _single["dataset"] == "config2" else None,
                      "ops_per_event": ops_per_event, "events_per_launch": events_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
-                     "dominant": "k_advance_coop, 94 % of the step (ncu launch list): latency-bound, see latency_bound",
+                     "dominant": ("k_advance_coop, 94 % of the step (ncu launch list): latency-bound, see latency_bound"
+                                  if _single["dataset"] == "config2" else None),
                      "busiest_launch": busiest(best or {}, ops_per_event, peak),
                      "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived)"},
         "latency_bound": latency,
@@ -357,7 +378,7 @@ def run_ours(args, rank, world, local, pg):
         "e2e": {"value": U * world / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max,
                 "what": "sim_create + sim_sample + sim_run + sim_species into pinned host memory"},
-        "batched": {"sims": args.batch, "workload": "config2 replicas, seeds 42..%d" % (41 + args.batch),
+        "batched": {"sims": args.batch, "workload": "%s replicas, seeds 42..%d" % (_single["dataset"], 41 + args.batch),
                     "unique_events": sum(Us), "batched_events_per_s": sum(Us) / batch_s,
                     "plain_events_per_s": sum(Us) / plain_s, "speedup": plain_s / batch_s},
         "other_sampler": other_line,
@@ -584,7 +605,7 @@ def oracle_run(seed=42):
     import oracle as O
     from paper_2108_05815_b300 import workloads as W
     c = W.config2(seed)
-    m = O.Model(c["kind"], c["width"], c["height"], c["deme"], c["nu"], c["seed"], sigma=c["sigma"])
+    m = O.Model(c["kind"], c["width"], c["height"], c["deme"], c["nu"], c["seed"], sigma=c["sigma"], sampler=_sampler)
     locs = m.sample()
     t0 = time.perf_counter()
     kl, kt, U = m.run_merge(locs)
@@ -602,6 +623,30 @@ def cpu_baseline(seconds):
     return {"value": total_u / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d full config2 simulations (seeds 42..%d), event-ordered merge mode, one thread"
                       % (runs, 41 + runs)}
+
+
+def cpu_baseline_traces(seconds):
+    """the oracle on the spatially implicit workload: its event-ordered mode
+    would need a slot per metacommunity individual (10^9), so lineages are
+    traced one by one (mode P) in order until the time is used; each traced
+    event costs what a unique event costs in the event-ordered mode"""
+    import oracle as O
+    from paper_2108_05815_b300 import workloads as W
+    c = W.implicit(42)
+    m = O.Model(c["kind"], 1, 1, c["deme"], c["nu"], c["seed"], sampler=_sampler, migration=c["migration"],
+                meta_size=c["meta_size"], meta_nu=c["meta_nu"])
+    locs = m.sample()
+    events, lineages, t = 0, 0, 0.0
+    while (t < seconds or lineages == 0) and lineages < len(locs):
+        chunk = locs[lineages:lineages + 64]
+        t0 = time.perf_counter()
+        _, _, ne = m.trace(chunk)
+        t += time.perf_counter() - t0
+        events += int(ne.sum())
+        lineages += len(chunk)
+    return {"value": events / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d lineages traced one by one (mode P, %d events), one thread"
+                      % (lineages, len(locs), events)}
 
 
 def run_reference(args, rank, world, local, pg):
@@ -627,14 +672,15 @@ def run_reference(args, rank, world, local, pg):
 
 def main():
     args = parse()
+    global _sampler, _single
+    _sampler = SAMPLER[args.sampler]
+    _single = single_workload(args.workload)
     if args.impl == "reference":
         # the oracle runs on the host cores of rank 0 only; other ranks exit
         rank = int(os.environ.get("RANK", "0"))
         if rank == 0:
             run_reference(args, 0, int(os.environ.get("WORLD_SIZE", "1")), 0, None)
         return
-    global _sampler
-    _sampler = SAMPLER[args.sampler]
     rank, world, local, pg = dist_setup(args)
     if args.workload == "batch":
         run_batch(args, rank, world, local, pg)

@@ -38,6 +38,14 @@ def config3(seed=42, side=1024):
                 radius=16, nu=1e-5, seed=seed, fraction=1.0)
 
 
+def implicit(seed=42):
+    """spatially implicit stand-in: a local community of 10^5 individuals (all
+    sampled), migration probability 0.01 per event, a static metacommunity of
+    10^9 individuals with speciation probability 10^-4, no local speciation"""
+    return dict(kind=IMPLICIT, width=1, height=1, deme=100000, nu=0.0, seed=seed, fraction=1.0, migration=0.01,
+                meta_size=10 ** 9, meta_nu=1e-4)
+
+
 def _loguniform(rng, lo, hi, size=None):
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size=size))
 
