@@ -57,6 +57,14 @@ class _LnTables(ctypes.Structure):
                 ("c3", ctypes.c_int64)]
 
 
+class _EventLog(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_uint64), ("n", ctypes.c_uint64), ("time_bits", ctypes.c_void_p),
+                ("prior_bits", ctypes.c_void_p), ("loc", ctypes.c_void_p), ("target", ctypes.c_void_p),
+                ("lineage", ctypes.c_void_p), ("co_cap", ctypes.c_uint64), ("n_co", ctypes.c_uint64),
+                ("co_loc", ctypes.c_void_p), ("co_time_bits", ctypes.c_void_p), ("co_parent", ctypes.c_void_p),
+                ("co_child", ctypes.c_void_p)]
+
+
 class _Model(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("deme", ctypes.c_uint32), ("deme_map", ctypes.c_void_p),
@@ -86,6 +94,7 @@ def lib():
                 "or_trace": (ctypes.c_int, [vp, u64, u64, vp, vp, vp]),
                 "or_trace_many": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp]),
                 "or_run_merge": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp]),
+                "or_run_merge_events": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp, vp]),
                 "or_habitat": (None, [u64, u32, u32, dbl, u32, vp]),
                 "or_sample": (u64, [vp, dbl, u64, vp]),
                 "or_gauss_offset": (u64, [vp, u64]),
@@ -266,6 +275,38 @@ class Model:
         if st != 0:
             raise RuntimeError("oracle merge run failed with status %d" % st)
         return kl, kt, int(nu.value)
+
+    def run_merge_events(self, locs, max_events=1 << 40):
+        """Mode M with its event stream: (key_loc, key_time_bits, n_unique,
+        events, coalescences).  events: dict of arrays time_bits, prior_bits,
+        loc, target (~0 for a speciation) and lineage, one entry per executed
+        event in time order; coalescences: dict of arrays loc, time_bits,
+        parent, child (the child dispersed at time into the parent's
+        location)."""
+        locs = np.ascontiguousarray(locs, dtype=np.uint64)
+        n = locs.size
+        _, _, U = self.run_merge(locs, max_events)
+        ev = {k: np.zeros(max(U, 1), dtype=np.uint64) for k in ("time_bits", "prior_bits", "loc", "target")}
+        ev["lineage"] = np.zeros(max(U, 1), dtype=np.int64)
+        co = {k: np.zeros(max(n, 1), dtype=np.uint64) for k in ("loc", "time_bits")}
+        co["parent"] = np.zeros(max(n, 1), dtype=np.int64)
+        co["child"] = np.zeros(max(n, 1), dtype=np.int64)
+        lg = _EventLog()
+        lg.cap, lg.co_cap = U, n
+        lg.time_bits, lg.prior_bits, lg.loc = _ptr(ev["time_bits"]), _ptr(ev["prior_bits"]), _ptr(ev["loc"])
+        lg.target, lg.lineage = _ptr(ev["target"]), _ptr(ev["lineage"])
+        lg.co_loc, lg.co_time_bits = _ptr(co["loc"]), _ptr(co["time_bits"])
+        lg.co_parent, lg.co_child = _ptr(co["parent"]), _ptr(co["child"])
+        kl = np.zeros(n, dtype=np.uint64)
+        kt = np.zeros(n, dtype=np.uint64)
+        nu = ctypes.c_uint64(0)
+        st = lib().or_run_merge_events(self._mp, _ptr(locs), n, max_events, _ptr(kl), _ptr(kt),
+                                       ctypes.byref(nu), ctypes.byref(lg))
+        if st != 0:
+            raise RuntimeError("oracle merge run failed with status %d" % st)
+        ev = {k: v[:lg.n] for k, v in ev.items()}
+        co = {k: v[:lg.n_co] for k, v in co.items()}
+        return kl, kt, int(nu.value), ev, co
 
     def trace_log(self, loc, cap=1 << 24):
         """Mode P event log of one lineage: arrays of (location, time bits)."""

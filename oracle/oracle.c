@@ -574,8 +574,44 @@ static uint64_t slot_of(const or_model* m, uint64_t loc)
  * the occupant's pending event time (not handled), -4 on out-of-memory.
  * key_loc/key_time receive every lineage's species key; *n_unique the number
  * of events executed (each is unique). */
+/* The event stream of mode M (section "Reporting Coalescence Events
+ * Independently"): every executed event -- (time, the lineage's prior event
+ * time, location, dispersal target or ~0 for a speciation, lineage) -- in
+ * global time order, and every coalescence: a lineage (child) dispersing at
+ * time t into the location of another (parent). */
+typedef struct {
+    uint64_t cap, n;
+    uint64_t* time_bits;
+    uint64_t* prior_bits;
+    uint64_t* loc;
+    uint64_t* target;
+    int64_t* lineage;
+    uint64_t co_cap, n_co;
+    uint64_t* co_loc;
+    uint64_t* co_time_bits;
+    int64_t* co_parent;
+    int64_t* co_child;
+} or_event_log;
+
+static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
+                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log);
+
 int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
                  uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique)
+{
+    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, 0);
+}
+
+/* mode M with its event stream; -5 if the log's arrays are too small */
+int or_run_merge_events(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
+                        uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log)
+{
+    log->n = log->n_co = 0;
+    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, log);
+}
+
+static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
+                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log)
 {
     uint32_t sk[2];
     or_seed_key(m->seed, sk);
@@ -585,9 +621,10 @@ int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t m
     double* pending = (double*)malloc(n_slots * sizeof(double));
     uint64_t* loc_of = (uint64_t*)malloc(n * sizeof(uint64_t));
     int64_t* parent = (int64_t*)malloc(n * sizeof(int64_t));
+    double* last = (double*)malloc(n * sizeof(double)); /* each lineage's prior event time */
     or_heap_item* heap = (or_heap_item*)malloc((n + 1) * sizeof(or_heap_item));
     int status = 0;
-    if (!occupant || !pending || !loc_of || !parent || !heap) {
+    if (!occupant || !pending || !loc_of || !parent || !last || !heap) {
         status = -4;
         goto done;
     }
@@ -598,6 +635,7 @@ int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t m
         uint64_t slot = slot_of(m, loc0[a]);
         parent[a] = -1;
         loc_of[a] = loc0[a];
+        last[a] = 0.0;
         if (occupant[slot] >= 0) { /* duplicate sample location */
             parent[a] = occupant[slot];
             continue;
@@ -624,12 +662,26 @@ int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t m
         double tau = it.t;
         occupant[it.slot] = -1;
         events++;
-        if (speciates(m, sk, loc, tau)) {
+        int spec = speciates(m, sk, loc, tau);
+        uint64_t target = spec ? ~0ull : disperse(m, sk, loc, tau);
+        if (log) {
+            if (log->n >= log->cap) {
+                status = -5;
+                goto done;
+            }
+            log->time_bits[log->n] = dbl_bits(tau);
+            log->prior_bits[log->n] = dbl_bits(last[a]);
+            log->loc[log->n] = loc;
+            log->target[log->n] = target;
+            log->lineage[log->n] = a;
+            log->n++;
+        }
+        last[a] = tau;
+        if (spec) {
             key_loc[a] = loc;
             key_time[a] = dbl_bits(tau);
             continue;
         }
-        uint64_t target = disperse(m, sk, loc, tau);
         uint64_t ts = slot_of(m, target);
         if (occupant[ts] >= 0) {
             if (pending[ts] == tau) {
@@ -637,6 +689,17 @@ int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t m
                 goto done;
             }
             parent[a] = occupant[ts];
+            if (log) {
+                if (log->n_co >= log->co_cap) {
+                    status = -5;
+                    goto done;
+                }
+                log->co_loc[log->n_co] = target;
+                log->co_time_bits[log->n_co] = dbl_bits(tau);
+                log->co_parent[log->n_co] = occupant[ts];
+                log->co_child[log->n_co] = a;
+                log->n_co++;
+            }
             continue;
         }
         double t = next_event_time(m, sk, target, tau);
@@ -664,6 +727,7 @@ done:
     free(pending);
     free(loc_of);
     free(parent);
+    free(last);
     free(heap);
     return status;
 }

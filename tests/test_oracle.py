@@ -646,3 +646,67 @@ def test_implicit_mode_p_equals_mode_m(sampler):
     pl, pt, ne = m.trace(locs)
     assert np.array_equal(kl, pl) and np.array_equal(kt, pt)
     assert ne.sum() >= U
+
+
+# --------------------------------------------------------------------------
+# Event stream (section "Reporting Coalescence Events Independently"):
+# mode M's executed events in time order, with prior event times, and its
+# coalescences, checked against the plain per-lineage traces
+# --------------------------------------------------------------------------
+NO_TARGET = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def _stream_models(sampler):
+    dm = O.habitat(5, 24, 20)
+    return [
+        O.Model(O.NONSPATIAL, 1, 1, 300, 1e-2, 5, sampler=sampler),
+        O.Model(O.TORUS, 16, 12, 2, 2e-2, 6, sigma=1.5, sampler=sampler),
+        O.Model(O.MAP, 24, 20, 0, 3e-2, 7, sigma=2.0, radius=6, deme_map=dm, sampler=sampler),
+        O.Model(O.IMPLICIT, 1, 1, 300, 0.0, 8, sampler=sampler, migration=0.05, meta_size=400, meta_nu=0.02),
+    ]
+
+
+@pytest.mark.parametrize("sampler", SAMPLERS)
+@pytest.mark.parametrize("idx", [0, 1, 2, 3])
+def test_event_stream_against_plain_traces(idx, sampler):
+    m = _stream_models(sampler)[idx]
+    locs = m.sample()
+    kl, kt, U, ev, co = m.run_merge_events(locs)
+    n = len(locs)
+    t = _times(ev["time_bits"])
+    # every executed event once, in strictly increasing time
+    assert len(t) == U and np.all(np.diff(t) > 0)
+    # every lineage ends in exactly one speciation or one coalescence
+    spec = ev["target"] == NO_TARGET
+    assert int(spec.sum()) + len(co["child"]) == n
+    assert len(set(co["child"].tolist())) == len(co["child"])
+    # each lineage's events are the prefix of its own plain trace, chained by
+    # prior event times and dispersal targets
+    plain = [m.trace_log(int(l)) for l in locs]
+    merged_at = {int(c): int(tb) for c, tb in zip(co["child"], co["time_bits"])}
+    for a in range(n):
+        mine = np.nonzero(ev["lineage"] == a)[0]
+        pl, pt = plain[a]
+        k = len(mine)
+        assert k >= 1
+        assert np.array_equal(ev["loc"][mine], pl[:k]) and np.array_equal(ev["time_bits"][mine], pt[:k])
+        prior = np.concatenate([[0.0], _times(pt[:k - 1])])
+        assert np.array_equal(_times(ev["prior_bits"][mine]), prior)
+        nxt = ev["target"][mine[:-1]]
+        assert np.array_equal(nxt, pl[1:k])
+        if a in merged_at:  # it stopped at its merging dispersal
+            assert ev["time_bits"][mine[-1]] == merged_at[a] and ev["target"][mine[-1]] != NO_TARGET
+        else:
+            assert ev["target"][mine[-1]] == NO_TARGET and k == len(pl)
+    # a coalescence: the child's trace, after dispersing at time t into L,
+    # has its next event where the parent's trace has one at L, and the
+    # parent's event before that lies before t
+    for L, tb, p, c in zip(co["loc"], co["time_bits"], co["parent"], co["child"]):
+        cl, ct = plain[int(c)]
+        j = int(np.nonzero(ct == tb)[0][0])
+        assert cl[j + 1] == L
+        pl, pt = plain[int(p)]
+        hit = np.nonzero((pt == ct[j + 1]) & (pl == L))[0]
+        assert len(hit) == 1
+        h = int(hit[0])
+        assert h == 0 or _times(pt[h - 1:h])[0] < _times([tb])[0]
