@@ -146,6 +146,33 @@ typedef struct {
                                  whole batch for sim_batch_run; 0 for served requests) */
 } ind_run_stats;
 
+/* Event stream (section "Reporting Coalescence Events Independently").
+ * With an event log (sim_set_event_log), sim_run records every event it
+ * executes, copies of not yet culled lineages included, and when the run
+ * ends reduces the record on the device: sorted by (event time, location,
+ * prior event time, lineage), the copies of one event are adjacent; the
+ * first is kept (one entry per distinct event), and every later copy with
+ * a prior time of its own is a lineage that dispersed into the location at
+ * that time: a coalescence with the lineage of the first copy.  A lineage
+ * removed by the horizon dedup leaves a copy of its pending event (with its
+ * own prior time), so that no coalescence is lost to the dedup. */
+#define IND_SPECIATION UINT64_MAX
+typedef struct {
+    uint64_t time_bits;  /* event time: IEEE-754 bits of tau >= 0 */
+    uint64_t prior_bits; /* the executing lineage's previous event time (0: the present) */
+    uint64_t loc;        /* location of the event */
+    uint64_t target;     /* dispersal target, or IND_SPECIATION */
+    uint32_t lineage;    /* a sampled individual (sampling order) whose lineage executes it */
+    uint32_t reserved;
+} ind_event;
+
+typedef struct {
+    uint64_t loc;       /* where the child dispersed to: the parent's location */
+    uint64_t time_bits; /* the child's dispersal time */
+    uint32_t parent;    /* sampled individual whose lineage was at loc */
+    uint32_t child;     /* sampled individual whose lineage arrived */
+} ind_coalescence;
+
 /* Tuning of the engine.  None of it changes results (bit-identical). */
 typedef struct {
     uint32_t block_threads;     /* advance-kernel threads per block: 64..512, multiple of 32 */
@@ -207,6 +234,22 @@ ind_status sim_create(const ind_landscape* landscape, const ind_dispersal* dispe
  * ceil(fraction 2^53).  Individuals are numbered in (cell row-major, i)
  * order.  0 < fraction <= 1.  *n_sampled receives the count (may be NULL). */
 ind_status sim_sample(ind_sim* sim, double fraction, uint64_t sample_seed, uint64_t* n_sampled);
+
+/* Enable the event log of the next run (capacity: raw events the device may
+ * hold, duplicates and one entry per deduplicated lineage included,
+ * 1..2^31) or disable it (0).  Costs 36 bytes per
+ * raw event plus 16 per lineage; a run that executes more events than the
+ * capacity fails with IND_ERR_DEVICE.  Only sim_run logs: sim_batch_run and
+ * srv_submit reject a simulation with a log (IND_ERR_ARG). */
+ind_status sim_set_event_log(ind_sim* sim, uint64_t capacity);
+
+/* After a logged run: the distinct events in (time, location) order and the
+ * coalescences in the same order.  Up to cap / co_cap entries are written
+ * (host or device pointers; NULL: counts only); *n_events and
+ * *n_coalescences (either may be NULL) receive the totals.  IND_ERR_STATE
+ * before the run has finished or without a log. */
+ind_status sim_events(ind_sim* sim, ind_event* out, uint64_t cap, uint64_t* n_events, ind_coalescence* co_out,
+                      uint64_t co_cap, uint64_t* n_coalescences);
 
 /* Run horizon rounds until every lineage has speciated or round_budget
  * rounds were executed in this call (0 = unlimited); IND_ERR_BUDGET means

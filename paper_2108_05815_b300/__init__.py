@@ -78,6 +78,12 @@ class Allocator(ctypes.Structure):
     _fields_ = [("alloc", _ALLOC), ("release", _RELEASE), ("ctx", ctypes.c_void_p)]
 
 
+# ind_event / ind_coalescence
+EVENT_DTYPE = np.dtype([("time_bits", "<u8"), ("prior_bits", "<u8"), ("loc", "<u8"), ("target", "<u8"),
+                        ("lineage", "<u4"), ("reserved", "<u4")])
+COALESCENCE_DTYPE = np.dtype([("loc", "<u8"), ("time_bits", "<u8"), ("parent", "<u4"), ("child", "<u4")])
+SPECIATION = 0xFFFFFFFFFFFFFFFF
+
 EXPORTS = {
     "ind_set_allocator": (ctypes.c_int, [ctypes.c_void_p]),
     "ind_default_tuning": (None, [ctypes.c_void_p]),
@@ -92,6 +98,9 @@ EXPORTS = {
     "sim_mem_estimate": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "sim_destroy": (None, [ctypes.c_void_p]),
     "sim_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "sim_set_event_log": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "sim_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "ind_habitat": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
                                    ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "ind_selftest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
@@ -277,6 +286,21 @@ class Simulation:
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
         _check(lib().sim_species(self._h, ctypes.c_void_p(ptr), ctypes.byref(n)), "sim_species")
         return out, int(n.value)
+
+    def set_event_log(self, capacity):
+        """log the events of the next run (capacity in raw events; 0: off)"""
+        _check(lib().sim_set_event_log(self._h, int(capacity)), "sim_set_event_log")
+
+    def events(self):
+        """after a logged run: (events, coalescences) as numpy structured arrays
+        (EVENT_DTYPE in (time, location) order, COALESCENCE_DTYPE)"""
+        ne, nc = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(lib().sim_events(self._h, None, 0, ctypes.byref(ne), None, 0, ctypes.byref(nc)), "sim_events")
+        ev = np.zeros(ne.value, dtype=EVENT_DTYPE)
+        co = np.zeros(nc.value, dtype=COALESCENCE_DTYPE)
+        _check(lib().sim_events(self._h, ctypes.c_void_p(ev.ctypes.data), ne.value, None,
+                                ctypes.c_void_p(co.ctypes.data), nc.value, None), "sim_events")
+        return ev, co
 
     def species_keys(self):
         """(speciation location, time bits) per sampled individual, uint64 numpy arrays"""

@@ -220,6 +220,7 @@ struct Globals {
     uint32_t prof_n;
     uint32_t round_max;               // most events one lineage ran in the running round
     unsigned long long critical_events;  // sum of round_max over completed rounds
+    unsigned long long log_n;            // events appended to the event log (may pass its capacity)
 };
 
 struct __align__(16) EvSlot {
@@ -231,6 +232,18 @@ struct LinPtrs {
     double* tn;
     uint32_t* gid;
     uint32_t* sim;
+    double* tp;  // the lineage's previous event time (event logging only, else null)
+};
+
+// the event log: every executed event, duplicates of not yet culled copies
+// included (structure of arrays, cap entries)
+struct EventLog {
+    uint64_t* time;    // event time bits
+    uint64_t* prior;   // the lineage's previous event time bits (0 at its first)
+    uint64_t* loc;     // where the event happens
+    uint64_t* target;  // dispersal target, ~0 for a speciation
+    uint32_t* gid;     // lineage
+    unsigned long long cap;
 };
 
 struct BatchDev {
@@ -255,6 +268,7 @@ struct BatchDev {
     int need_ln;  // some simulation uses the exponential-sums sampler
     uint32_t events_per_visit;
     uint32_t coop_lineages;  // a round with at most this many active lineages runs one warp per lineage
+    EventLog log;            // cap 0: no logging
 };
 
 // ---------------------------------------------------------------------------
@@ -760,6 +774,27 @@ __device__ __forceinline__ bool count_event(const BatchDev& B, uint32_t t, uint6
     return false;
 }
 
+// log target of a culled lineage's pending event: the lineage does not
+// execute it (its winner does), but its copy carries its own prior time, so
+// that a coalescence stays visible in the stream
+constexpr uint64_t LOG_CULLED = ~1ull;
+
+// append one executed event to the log; past the capacity the run fails
+// with a device error (error bit 8) and the entry is dropped
+__device__ __forceinline__ void log_event(const BatchDev& B, double tn, double tp, uint64_t loc, uint64_t target,
+                                          uint32_t gid) {
+    const unsigned long long k = atomicAdd(&B.G->log_n, 1ull);
+    if (k < B.log.cap) {
+        B.log.time[k] = (uint64_t)__double_as_longlong(tn);
+        B.log.prior[k] = (uint64_t)__double_as_longlong(tp);
+        B.log.loc[k] = loc;
+        B.log.target[k] = target;
+        B.log.gid[k] = gid;
+    } else {
+        atomicOr(&B.G->error, 8u);
+    }
+}
+
 __device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint64_t skey, uint32_t gid) {
     const uint32_t mask = B.G->mask[t];
     uint32_t h = (uint32_t)mix64(skey) & mask;
@@ -835,11 +870,13 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
         B.lin[0].tn[g] = t;
         B.lin[0].gid[g] = g;
         B.lin[0].sim[g] = lo;
+        if (B.lin[0].tp) B.lin[0].tp[g] = 0.0;
         B.parent[g] = g;
     }
 }
 
-template <bool COUNT, int WIDE>
+// LOG: append every executed event to the event log
+template <bool COUNT, int WIDE, bool LOG>
 __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
@@ -862,7 +899,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     bool has = false;
     uint32_t idx = 0, gid = 0;
     uint64_t loc = 0;
-    double tn = 0.0;
+    double tn = 0.0, tprev = 0.0;
     LaneSim c;
     c.sim = 0xFFFFFFFFu;
     uint64_t ev_raw = 0, ev_unique = 0;
@@ -891,6 +928,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                     gid = L.gid[idx];
                     loc = L.loc[idx];
                     tn = L.tn[idx];
+                    if (LOG) tprev = L.tp[idx];
                     const uint32_t s = L.sim[idx];
                     if (s != c.sim) {
                         if (cnt_sim != 0xFFFFFFFFu && (ev_raw | ev_unique)) {
@@ -920,13 +958,20 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                 // at the horizon: write back and enter the dedup
                 L.loc[idx] = loc;
                 L.tn[idx] = tn;
+                if (LOG) L.tp[idx] = tprev;
                 if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
                 has = false;
             } else {
                 ++ev_raw;
                 lane_max = max(lane_max, ++ev_lin);
                 if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
-                if (do_event(c, B.P, loc, tn)) {
+                const uint64_t at = loc;
+                const bool speciated = do_event(c, B.P, loc, tn);
+                if (LOG) {
+                    log_event(B, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                    tprev = tn;
+                }
+                if (speciated) {
                     B.key_loc[gid] = loc;
                     B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
                     L.gid[idx] = gid | DONE_BIT;
@@ -1187,7 +1232,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 // MODE 0: any mix (the search chosen per lineage).  KIND: the landscape kind
 // shared by every simulation, or -1.  The specialised kernels are smaller,
 // which matters where one warp runs alone and waits on instruction fetch.
-template <bool COUNT, int MODE, int KIND>
+template <bool COUNT, int MODE, int KIND, bool LOG = false>
 __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     const uint32_t n = B.G->n_total;
@@ -1208,6 +1253,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
         const uint32_t gid = L.gid[idx];
         uint64_t loc = L.loc[idx];
         double tn = L.tn[idx];
+        double tprev = LOG ? L.tp[idx] : 0.0;
         const uint32_t s = L.sim[idx];
         LaneSim c;
         load_lanesim(c, B.P, B.S, s);
@@ -1227,6 +1273,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                 if (lane == 0) {
                     L.loc[idx] = loc;
                     L.tn[idx] = tn;
+                    if (LOG) L.tp[idx] = tprev;
                     if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
                 }
                 break;
@@ -1234,7 +1281,13 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
             ++ev_raw;
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
-            if (do_event_warp<KIND>(c, B.P, loc, tn, lane)) {
+            const uint64_t at = loc;
+            const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane);
+            if (LOG) {
+                if (lane == 0) log_event(B, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                tprev = tn;
+            }
+            if (speciated) {
                 if (lane == 0) {
                     B.key_loc[gid] = loc;
                     B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
@@ -1298,13 +1351,14 @@ __global__ void k_compact(BatchDev B) {
         bool survive = false, culled = false;
         uint32_t s = 0xFFFFFFFFu, g = 0;
         uint64_t loc = 0;
-        double tn = 0.0;
+        double tn = 0.0, tprev = 0.0;
         if (i < n) {
             g = in.gid[i];
             if (!(g & DONE_BIT)) {
                 s = in.sim[i];
                 loc = in.loc[i];
                 tn = in.tn[i];
+                if (in.tp) tprev = in.tp[i];
                 survive = true;
                 if (B.dedup) {
                     const uint32_t w = dedup_lookup(B, t, slot_index(B.P + s, loc));
@@ -1312,6 +1366,7 @@ __global__ void k_compact(BatchDev B) {
                         B.parent[g] = w;
                         survive = false;
                         culled = true;
+                        if (in.tp) log_event(B, tn, tprev, loc, LOG_CULLED, g);
                     }
                 }
             }
@@ -1327,6 +1382,7 @@ __global__ void k_compact(BatchDev B) {
             out.tn[pos] = tn;
             out.gid[pos] = g;
             out.sim[pos] = s;
+            if (out.tp) out.tp[pos] = tprev;
         }
         if (sm) {
             const unsigned grp = __match_any_sync(0xFFFFFFFFu, survive ? s : 0xFFFFFFFFu);
@@ -1472,7 +1528,8 @@ __global__ void k_roots(BatchDev B, uint32_t n_lin, uint32_t* root, SortItem* it
 __device__ __forceinline__ bool item_less(const SortItem& x, const SortItem& y) {
     if (x.a != y.a) return x.a < y.a;
     if (x.b != y.b) return x.b < y.b;
-    return x.c < y.c;
+    if (x.c != y.c) return x.c < y.c;
+    return x.d < y.d;  // a total order: equal keys come out the same on every run
 }
 
 __global__ void k_pad_items(SortItem* items, const uint32_t* n_items, uint32_t n_pad) {
@@ -1623,6 +1680,58 @@ __global__ void k_scan_add(uint32_t* out, const uint32_t* sums_excl, uint32_t n)
     const uint32_t add = sums_excl[blockIdx.x];
     for (uint32_t k = threadIdx.x; k < SCAN_TILE; k += blockDim.x)
         if (base + k < n) out[base + k] += add;
+}
+
+// ---------------------------------------------------------------------------
+// event stream: the log sorted by (time, location, prior time, lineage);
+// copies of one event are adjacent, the first (earliest prior time) is the
+// lineage that was at the location longest, and every later distinct prior
+// time is a lineage that dispersed there at that time: a coalescence
+// ---------------------------------------------------------------------------
+__global__ void k_ev_items(EventLog L, uint32_t n, uint32_t n_pad, SortItem* items) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
+        items[i] = i < n ? SortItem{L.time[i], L.loc[i], L.prior[i], ((unsigned long long)L.gid[i] << 32) | i}
+                         : SortItem{~0ull, ~0ull, ~0ull, ~0ull};
+}
+
+__global__ void k_ev_marks(const SortItem* __restrict__ x, uint32_t n, uint32_t* head, uint32_t* coal) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool h = i == 0 || x[i].a != x[i - 1].a || x[i].b != x[i - 1].b;
+        head[i] = h ? 1u : 0u;
+        coal[i] = (!h && x[i].c != x[i - 1].c) ? 1u : 0u;
+    }
+}
+
+__global__ void k_ev_events(const SortItem* __restrict__ x, uint32_t n, const uint32_t* head,
+                            const uint32_t* incl_head, const uint64_t* __restrict__ target, uint32_t* head_pos,
+                            ind_event* out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!head[i]) continue;
+        const uint32_t g = incl_head[i] - 1u;
+        head_pos[g] = i;
+        const uint32_t idx = (uint32_t)x[i].d;
+        out[g] = ind_event{x[i].a, x[i].c, x[i].b, target[idx], (uint32_t)(x[i].d >> 32), 0u};
+    }
+}
+
+// an event's target from a copy that executed it (the first copy may be a
+// culled lineage's; every executed copy has the same target)
+__global__ void k_ev_targets(const SortItem* __restrict__ x, uint32_t n, const uint32_t* incl_head,
+                             const uint64_t* __restrict__ target, ind_event* out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t tg = target[(uint32_t)x[i].d];
+        if (tg != LOG_CULLED) out[incl_head[i] - 1u].target = tg;
+    }
+}
+
+__global__ void k_ev_coalescences(const SortItem* __restrict__ x, uint32_t n, const uint32_t* coal,
+                                  const uint32_t* incl_coal, const uint32_t* incl_head, const uint32_t* head_pos,
+                                  ind_coalescence* out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!coal[i]) continue;
+        const uint32_t parent = (uint32_t)(x[head_pos[incl_head[i] - 1u]].d >> 32);
+        out[incl_coal[i] - 1u] = ind_coalescence{x[i].b, x[i].c, parent, (uint32_t)(x[i].d >> 32)};
+    }
 }
 
 static ind_status scan_u32(Pool& pool, const uint32_t* in, uint32_t* out, uint32_t n, bool inclusive,
@@ -1865,6 +1974,12 @@ struct ind_sim {
     uint64_t n_species = 0;
     Batch* batch = nullptr;
     ind_run_stats stats{};
+    uint64_t log_cap = 0;  // event log capacity of the next run (0: none)
+    Pool events;           // the last logged run's event stream
+    ind_event* d_events = nullptr;
+    ind_coalescence* d_coal = nullptr;
+    uint64_t n_events = 0, n_coal = 0;
+    bool events_ready = false;
 };
 
 static void seed_key(uint64_t seed, uint32_t* k0, uint32_t* k1) {
@@ -2098,6 +2213,21 @@ static ind_status batch_build(Batch& b) {
             d.ev_used[t] = P.get<uint32_t>(ec);
         }
     }
+    // event log: one simulation per batch (sim_run)
+    uint64_t log_cap = 0;
+    for (auto* m : b.sims) log_cap = std::max(log_cap, m->log_cap);
+    if (log_cap) {
+        if (b.n_sims != 1) return IND_ERR_ARG;
+        for (int t = 0; t < 2; ++t)
+            if (!(d.lin[t].tp = P.get<double>(n))) return IND_ERR_OOM;
+        d.log.time = P.get<uint64_t>(log_cap);
+        d.log.prior = P.get<uint64_t>(log_cap);
+        d.log.loc = P.get<uint64_t>(log_cap);
+        d.log.target = P.get<uint64_t>(log_cap);
+        d.log.gid = P.get<uint32_t>(log_cap);
+        if (!d.log.time || !d.log.prior || !d.log.loc || !d.log.target || !d.log.gid) return IND_ERR_OOM;
+        d.log.cap = log_cap;
+    }
     for (int t = 0; t < 2; ++t)
         if (!d.lin[t].loc || !d.lin[t].tn || !d.lin[t].gid || !d.lin[t].sim || !d.ht_key[t] || !d.ht_val[t] ||
             !d.ht_used[t] || (d.count_unique && (!d.ev[t] || !d.ev_used[t])))
@@ -2153,8 +2283,18 @@ static ind_status batch_build(Batch& b) {
         CK(cudaStreamSynchronize(s));
     }
     const uint32_t sms = sm_count();
-    CK(cudaFuncSetAttribute(k_advance<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
-    CK(cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance<true, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    CK(cudaFuncSetAttribute(k_advance<false, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
+    if (b.dev.log.cap) {
+        CK(cudaFuncSetAttribute(k_advance<true, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LN_SMEM_BYTES));
+        CK(cudaFuncSetAttribute(k_advance<false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LN_SMEM_BYTES));
+        CK(cudaFuncSetAttribute(k_advance_coop<true, 0, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LN_SMEM_BYTES));
+        CK(cudaFuncSetAttribute(k_advance_coop<false, 0, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LN_SMEM_BYTES));
+    }
     CK(set_coop_smem<true>());
     CK(set_coop_smem<false>());
     CK(cudaFuncSetAttribute(k_advance_sm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
@@ -2186,15 +2326,27 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     // both advance forms every round: each reads the live lineage count and
     // returns at once unless the round is its own (more than coop_lineages
     // lineages: one lane per lineage; else one warp per lineage), so that the
-    // choice is made per round inside captured chunks
-    if (b.dev.count_unique) {
+    // choice is made per round inside captured chunks.  An event log takes
+    // the logging forms (one-lane loop, generic warp form).
+    const dim3 ag(b.adv_blocks), at(b.adv_threads);
+    if (b.dev.log.cap) {
+        if (b.dev.count_unique) {
+            k_advance<true, 1, true><<<ag, at, smem, s>>>(b.dev);
+            CK(cudaGetLastError());
+            k_advance_coop<true, 0, -1, true><<<ag, at, smem, s>>>(b.dev);
+        } else {
+            k_advance<false, 1, true><<<ag, at, smem, s>>>(b.dev);
+            CK(cudaGetLastError());
+            k_advance_coop<false, 0, -1, true><<<ag, at, smem, s>>>(b.dev);
+        }
+    } else if (b.dev.count_unique) {
         if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-        else k_advance<true, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else k_advance<true, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
         launch_coop<true>(b, smem, s);
     } else {
         if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-        else k_advance<false, 1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        else k_advance<false, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
         launch_coop<false>(b, smem, s);
     }
@@ -2271,6 +2423,31 @@ static void collect_profile(Batch& b, uint32_t rounds) {
 }
 
 // resolve roots, sort/unique species keys, write per-sim outputs
+// ascending bitonic sort of np items (a power of two, at least 2048):
+// global stages for strides of 2048 and more, shared memory for the rest
+static ind_status bitonic_sort(SortItem* items, uint32_t np, cudaStream_t s) {
+    const uint32_t sh_threads = 1024;
+    const uint32_t span = 2 * sh_threads;
+    const size_t sh_bytes = sizeof(SortItem) * span;
+    static bool attr_set = false;
+    if (!attr_set) {
+        CK(cudaFuncSetAttribute(k_bitonic_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_bytes));
+        attr_set = true;
+    }
+    for (uint32_t k = 2; k <= np; k <<= 1) {
+        uint32_t j = k >> 1;
+        for (; j >= span; j >>= 1) {
+            k_bitonic_global<<<(np + 255) / 256, 256, 0, s>>>(items, np, j, k);
+            CKL();
+        }
+        k_bitonic_shared<<<np / span, sh_threads, sh_bytes, s>>>(items, np, k, j);
+        CKL();
+    }
+    return IND_OK;
+}
+
+static ind_status process_event_log(Batch& b);
+
 static ind_status batch_finish(Batch& b) {
     cudaStream_t s = b.stream;
     Pool& T = b.scratch;
@@ -2301,23 +2478,9 @@ static ind_status batch_finish(Batch& b) {
     while (np < h_items) np <<= 1;
     k_pad_items<<<grid_for(np, 256, sms * 16), 256, 0, s>>>(items, n_items, np);
     CKL();
-    // bitonic sort of np items: global stages for j >= 2048, shared for the rest
-    const uint32_t sh_threads = 1024;
-    const uint32_t span = 2 * sh_threads;
-    const size_t sh_bytes = sizeof(SortItem) * span;
-    static bool attr_set = false;
-    if (!attr_set) {
-        CK(cudaFuncSetAttribute(k_bitonic_shared, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_bytes));
-        attr_set = true;
-    }
-    for (uint32_t k = 2; k <= np; k <<= 1) {
-        uint32_t j = k >> 1;
-        for (; j >= span; j >>= 1) {
-            k_bitonic_global<<<(np + 255) / 256, 256, 0, s>>>(items, np, j, k);
-            CKL();
-        }
-        k_bitonic_shared<<<np / span, sh_threads, sh_bytes, s>>>(items, np, k, j);
-        CKL();
+    {
+        const ind_status sst = bitonic_sort(items, np, s);
+        if (sst != IND_OK) return sst;
     }
     k_heads<<<grid_for(h_items, 256, sms * 16), 256, 0, s>>>(items, n_items, head);
     CKL();
@@ -2358,7 +2521,69 @@ static ind_status batch_finish(Batch& b) {
         m->finished = true;
         m->stats.n_species = counts[si];
     }
+    if (b.dev.log.cap) {
+        const ind_status lst = process_event_log(b);
+        if (lst != IND_OK) return lst;
+    }
     b.scratch.release_all();
+    return IND_OK;
+}
+
+// the logged run's record -> the distinct events and the coalescences
+static ind_status process_event_log(Batch& b) {
+    ind_sim* m = b.sims[0];
+    cudaStream_t s = b.stream;
+    Pool& T = b.scratch;
+    const uint32_t sms = sm_count();
+    m->events.release_all();
+    m->events.stream = m->stream;
+    m->d_events = nullptr;
+    m->d_coal = nullptr;
+    m->n_events = m->n_coal = 0;
+    m->events_ready = false;
+    unsigned long long n_log = 0;
+    CK(cudaMemcpyAsync(&n_log, &b.d_g->log_n, sizeof(n_log), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (n_log > b.dev.log.cap) return IND_ERR_DEVICE;
+    const uint32_t n = (uint32_t)n_log;
+    if (n) {
+        uint32_t np = 2048;
+        while (np < n) np <<= 1;
+        SortItem* items = T.get<SortItem>(np);
+        uint32_t* head = T.get<uint32_t>(n);
+        uint32_t* coal = T.get<uint32_t>(n);
+        uint32_t* incl_head = T.get<uint32_t>(n);
+        uint32_t* incl_coal = T.get<uint32_t>(n);
+        if (!items || !head || !coal || !incl_head || !incl_coal) return IND_ERR_OOM;
+        k_ev_items<<<grid_for(np, 256, sms * 16), 256, 0, s>>>(b.dev.log, n, np, items);
+        CKL();
+        ind_status st = bitonic_sort(items, np, s);
+        if (st != IND_OK) return st;
+        k_ev_marks<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, head, coal);
+        CKL();
+        if ((st = scan_u32(T, head, incl_head, n, true, s)) != IND_OK) return st;
+        if ((st = scan_u32(T, coal, incl_coal, n, true, s)) != IND_OK) return st;
+        uint32_t hn = 0, cn = 0;
+        CK(cudaMemcpyAsync(&hn, incl_head + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&cn, incl_coal + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        m->d_events = m->events.get<ind_event>(std::max<uint32_t>(hn, 1u));
+        m->d_coal = m->events.get<ind_coalescence>(std::max<uint32_t>(cn, 1u));
+        uint32_t* head_pos = T.get<uint32_t>(std::max<uint32_t>(hn, 1u));
+        if (!m->d_events || !m->d_coal || !head_pos) return IND_ERR_OOM;
+        k_ev_events<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, head, incl_head, b.dev.log.target, head_pos,
+                                                               m->d_events);
+        CKL();
+        k_ev_targets<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, incl_head, b.dev.log.target, m->d_events);
+        CKL();
+        k_ev_coalescences<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, coal, incl_coal, incl_head, head_pos,
+                                                                     m->d_coal);
+        CKL();
+        CK(cudaStreamSynchronize(s));
+        m->n_events = hn;
+        m->n_coal = cn;
+    }
+    m->events_ready = true;
     return IND_OK;
 }
 
@@ -2558,7 +2783,7 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
     m->nu = nu;
     m->seed = seed;
     m->stream = s;
-    m->tables.stream = m->sample.stream = m->results.stream = s;
+    m->tables.stream = m->sample.stream = m->results.stream = m->events.stream = s;
     ind_default_tuning(&m->tuning);
     m->dt_log2 = dt_log2;
     seed_key(seed, &m->sk0, &m->sk1);
@@ -2674,7 +2899,12 @@ ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_
     }
     m->sample.release_all();
     m->results.release_all();
+    m->events.release_all();
     m->d_species = m->d_key_loc = m->d_key_time = nullptr;
+    m->d_events = nullptr;
+    m->d_coal = nullptr;
+    m->n_events = m->n_coal = 0;
+    m->events_ready = false;
     m->finished = false;
     m->sampled = false;
     m->stats = ind_run_stats{};
@@ -2804,6 +3034,27 @@ ind_status sim_batch_run(ind_sim** sims, uint32_t n, const ind_tuning* tuning, i
     return st;
 }
 
+ind_status sim_set_event_log(ind_sim* m, uint64_t capacity) {
+    if (!m || capacity > (1ull << 31)) return IND_ERR_ARG;
+    if (m->batch) return IND_ERR_STATE;  // a run in progress keeps the log it started with
+    m->log_cap = capacity;
+    return IND_OK;
+}
+
+ind_status sim_events(ind_sim* m, ind_event* out, uint64_t cap, uint64_t* n_events, ind_coalescence* co_out,
+                      uint64_t co_cap, uint64_t* n_coalescences) {
+    if (!m) return IND_ERR_ARG;
+    if (!m->finished || !m->events_ready) return IND_ERR_STATE;
+    const uint64_t ne = std::min(cap, m->n_events), nc = std::min(co_cap, m->n_coal);
+    if (out && ne) CK(cudaMemcpyAsync(out, m->d_events, ne * sizeof(ind_event), cudaMemcpyDefault, m->stream));
+    if (co_out && nc)
+        CK(cudaMemcpyAsync(co_out, m->d_coal, nc * sizeof(ind_coalescence), cudaMemcpyDefault, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (n_events) *n_events = m->n_events;
+    if (n_coalescences) *n_coalescences = m->n_coal;
+    return IND_OK;
+}
+
 ind_status sim_species(ind_sim* m, uint64_t* species_out, uint64_t* n_species_out) {
     if (!m) return IND_ERR_ARG;
     if (!m->finished) return IND_ERR_STATE;
@@ -2863,6 +3114,7 @@ void sim_destroy(ind_sim* m) {
     m->results.release_all();
     m->sample.release_all();
     m->tables.release_all();
+    m->events.release_all();
     delete m;
 }
 
@@ -3368,7 +3620,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     memset(b.h_g, 0, sizeof(Globals));
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
-    if ((e = cudaFuncSetAttribute(k_advance<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
+    if ((e = cudaFuncSetAttribute(k_advance<false, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
         (e = set_coop_smem<false>()) ||
         (e = cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
         return fail(e);
@@ -3396,6 +3648,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
 ind_status srv_submit(ind_server* sv, ind_sim* m, uint64_t* ticket) {
     if (!sv || !m) return IND_ERR_ARG;
     if (!m->sampled || m->finished || m->batch) return IND_ERR_STATE;
+    if (m->log_cap) return IND_ERR_ARG;  // served requests are not logged
     if (m->n_sampled > sv->n_cap || admission_bytes(m) > sv->budget) return IND_ERR_ARG;  // could never fit
     const uint64_t t = sv->next_ticket++;
     sv->queue.emplace_back(m, t);
