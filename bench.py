@@ -59,6 +59,9 @@ def parse():
                     help="event-time sampler of the headline (the other is reported beside it)")
     ap.add_argument("--window", type=float, default=60.0, help="served: arrival window in seconds")
     ap.add_argument("--plain-subset", type=int, default=32, help="batch: simulations timed one by one")
+    ap.add_argument("--events", action="store_true",
+                    help="single workloads: every step also produces the full event stream (distinct events and "
+                         "coalescences) on the device")
     return ap.parse_args()
 
 
@@ -205,6 +208,11 @@ def run_ours(args, rank, world, local, pg):
     U, R = unique_events(ind, 42)
 
     sim = make_sim(ind, 42, tuning=dict(profile=1))
+    # event log capacity: the raw events of the workload (the same on every
+    # run) and one entry per lineage the dedup removes
+    log_cap = int(R) + _single["n"] + 4096 if args.events else 0
+    if log_cap:
+        sim.set_event_log(log_cap)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     n_ind = _single["n"]
     ids = torch.empty(n_ind, dtype=torch.int64, device=dev)
@@ -264,15 +272,27 @@ def run_ours(args, rank, world, local, pg):
         torch.cuda.synchronize()
         h0 = time.perf_counter()
         s2 = make_sim(ind, 42)
+        if log_cap:
+            s2.set_event_log(log_cap)
         s2.sample()
         s2.run()
         s2.species(out=host_ids)
+        if log_cap:
+            ev_host, co_host = s2.events()
         h1 = time.perf_counter()
         s2.close()
         e2e_ms.append((h1 - h0) * 1e3)
     e2e_ms_max = allreduce_max(pg, statistics.median(e2e_ms))
     h2d = _single["h2d"]
     d2h = n_ind * 8 + 64    # species identities + completion flags
+    stream_line = None
+    if log_cap:
+        d2h += ev_host.nbytes + co_host.nbytes  # the event stream
+        stream_line = {"distinct_events": int(len(ev_host)), "coalescences": int(len(co_host)),
+                       "log_capacity": log_cap, "bytes_to_host": int(ev_host.nbytes + co_host.nbytes),
+                       "what": "every step also sorts its raw event log on the device into the distinct events "
+                               "(with prior times and outcomes) and the coalescences"}
+        assert len(ev_host) == U
 
     # batched vs plain on `batch` independent replicas of the workload
     seeds = [42 + k for k in range(args.batch)]
@@ -356,7 +376,8 @@ def run_ours(args, rank, world, local, pg):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
-        "config": {"workload": _single["desc"], "event_sampler": args.sampler,
+        "config": {"workload": _single["desc"] + (" + full event stream" if log_cap else ""),
+                   "event_sampler": args.sampler,
                    "parallelism": "replicas (one independent simulation per GPU)",
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "unique_events_per_step": U, "raw_events_per_step": raw_per_step,
@@ -374,6 +395,7 @@ def run_ours(args, rank, world, local, pg):
                      "busiest_launch": busiest(best or {}, ops_per_event, peak),
                      "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived)"},
         "latency_bound": latency,
+        "event_stream": stream_line,
         "cpu_baseline": cpu,
         "e2e": {"value": U * world / (e2e_ms_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms_max,

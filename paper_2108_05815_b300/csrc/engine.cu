@@ -795,6 +795,47 @@ __device__ __forceinline__ void log_event(const BatchDev& B, double tn, double t
     }
 }
 
+// event records of one warp: lane k holds the k-th pending one; a flush
+// takes one atomic for all of them, so that the log costs no round trip on
+// a lone lineage's chain of events
+struct WarpLogBuf {
+    uint64_t time, prior, loc, target;
+    uint32_t gid;
+    uint32_t n;  // records held (the same in every lane)
+};
+
+__device__ __forceinline__ void warp_log_flush(const BatchDev& B, WarpLogBuf& w, uint32_t lane) {
+    if (w.n == 0) return;
+    unsigned long long k0 = 0;
+    if (lane == 0) k0 = atomicAdd(&B.G->log_n, (unsigned long long)w.n);
+    k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
+    if (lane < w.n) {
+        const unsigned long long k = k0 + lane;
+        if (k < B.log.cap) {
+            B.log.time[k] = w.time;
+            B.log.prior[k] = w.prior;
+            B.log.loc[k] = w.loc;
+            B.log.target[k] = w.target;
+            B.log.gid[k] = w.gid;
+        } else {
+            atomicOr(&B.G->error, 8u);
+        }
+    }
+    w.n = 0;
+}
+
+__device__ __forceinline__ void warp_log_event(const BatchDev& B, WarpLogBuf& w, uint32_t lane, double tn, double tp,
+                                               uint64_t loc, uint64_t target, uint32_t gid) {
+    if (lane == w.n) {
+        w.time = (uint64_t)__double_as_longlong(tn);
+        w.prior = (uint64_t)__double_as_longlong(tp);
+        w.loc = loc;
+        w.target = target;
+        w.gid = gid;
+    }
+    if (++w.n == 32u) warp_log_flush(B, w, lane);
+}
+
 __device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint64_t skey, uint32_t gid) {
     const uint32_t mask = B.G->mask[t];
     uint32_t h = (uint32_t)mix64(skey) & mask;
@@ -1245,6 +1286,8 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     uint64_t ev_raw = 0, ev_unique = 0;
     uint32_t cnt_sim = 0xFFFFFFFFu;
     uint32_t lane_max = 0;  // most events of one lineage this round (the same in every lane)
+    WarpLogBuf wlog;
+    wlog.n = 0;
     for (;;) {
         uint32_t idx = 0;
         if (lane == 0) idx = atomicAdd(&B.G->work_ctr, 1u);
@@ -1284,7 +1327,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
             const uint64_t at = loc;
             const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane);
             if (LOG) {
-                if (lane == 0) log_event(B, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
                 tprev = tn;
             }
             if (speciated) {
@@ -1326,6 +1369,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
         if (COUNT) atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
     }
     if (lane == 0 && lane_max) atomicMax(&B.G->round_max, lane_max);
+    if (LOG) warp_log_flush(B, wlog, lane);
 }
 
 // horizon step (time) of a simulation with n active lineages
