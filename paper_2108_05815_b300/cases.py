@@ -1,8 +1,9 @@
 """Small named runs of the engine for profilers (ncu) and latency checks.
 
-  python -m paper_2108_05815_b300.cases config2 [--sampler exp|poisson]
+  python -m paper_2108_05815_b300.cases config2 [--sampler exp|poisson] [--events]
       the 256 x 256 torus workload once, without CUDA graphs, so that every
-      advance launch is a separate kernel launch a profiler can select
+      advance launch is a separate kernel launch a profiler can select;
+      --events also logs the run and reduces it to the event stream
   python -m paper_2108_05815_b300.cases busy [--sampler ...] [--rounds 6]
       a 1024 x 1024 torus (1,048,576 lineages, sigma 2, nu 1e-3) for a few
       rounds: the throughput-bound phase, all lineages active
@@ -27,16 +28,22 @@ def _sim(ind, kind, nu, seed, sampler, tuning, **kw):
     return ind.Simulation(kind, nu, seed, sampler=sampler, tuning=tuning, **kw)
 
 
-def run_config2(ind, sampler):
+def run_config2(ind, sampler, events=False):
     c = W.config2()
     s = _sim(ind, c["kind"], c["nu"], c["seed"], sampler, dict(use_graph=0, profile=1),
              width=c["width"], height=c["height"], deme=c["deme"], sigma=c["sigma"])
+    if events:
+        s.set_event_log(8 << 20)  # raw events of the workload: about 4.1 M
     s.sample()
     assert s.run()
     _, K = s.species()
     st = s.stats()
+    out = dict(case="config2", species=K, **{k: st[k] for k in ("rounds", "raw_events", "advance_launches")})
+    if events:
+        ev, co = s.events()
+        out.update(distinct_events=len(ev), coalescences=len(co))
     s.close()
-    return dict(case="config2", species=K, **{k: st[k] for k in ("rounds", "raw_events", "advance_launches")})
+    return out
 
 
 def run_busy(ind, sampler, rounds):
@@ -76,6 +83,7 @@ def main(argv=None):
     ap.add_argument("case", choices=["config2", "busy", "tail"])
     ap.add_argument("--sampler", default="exp", choices=sorted(SAMPLERS))
     ap.add_argument("--rounds", type=int, default=6)
+    ap.add_argument("--events", action="store_true")
     a = ap.parse_args(argv)
     import torch  # noqa: F401  (device memory comes from torch's allocator)
     import paper_2108_05815_b300 as ind
@@ -83,7 +91,7 @@ def main(argv=None):
     build.build()
     sampler = SAMPLERS[a.sampler]
     if a.case == "config2":
-        r = run_config2(ind, sampler)
+        r = run_config2(ind, sampler, a.events)
     elif a.case == "busy":
         r = run_busy(ind, sampler, a.rounds)
     else:
