@@ -1,4 +1,5 @@
 """Build step of the native library: nvcc -> paper_2108_05815_b300/lib/libindep.so (sm_103a)."""
+import glob
 import os
 import subprocess
 import sys
@@ -6,7 +7,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("engine.cu", "tables.cpp")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "device.cuh"), os.path.join(ROOT, "include", "indep.h")]
+DEPS = SRC + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [os.path.join(ROOT, "include", "indep.h")]
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libindep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,660 @@
+// engine_advance.cuh -- the round kernels: lineage start, the advance forms, compaction and horizons.
+// A part of the engine.cu translation unit, included there in order after
+// the parts before it; not a standalone header.
+#pragma once
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32_t n_lin) {
+    const LnC ln = ln_tables();
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_lin; g += gridDim.x * blockDim.x) {
+        // simulation of lineage g: last s with gid_base[s] <= g
+        uint32_t lo = 0, hi = B.n_sims;
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (gid_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        LaneSim c;
+        load_lanesim(c, B.P, B.S, lo);
+        const uint64_t loc = B.P[lo].sample_loc[g - gid_base[lo]];
+        double t = next_event_time<1>(c, loc, 0.0, ln);
+        if (search_failed(t)) {
+            atomicOr(&B.S[lo].error, 1u);
+            atomicOr(&B.G->error, 1u);
+            t = INFINITY;
+        }
+        B.lin[0].loc[g] = loc;
+        B.lin[0].tn[g] = t;
+        B.lin[0].gid[g] = g;
+        B.lin[0].sim[g] = lo;
+        if (B.lin[0].tp) B.lin[0].tp[g] = 0.0;
+        B.parent[g] = g;
+    }
+}
+
+// LOG: append every executed event to the event log
+template <bool COUNT, int WIDE, bool LOG>
+__global__ void __launch_bounds__(512) k_advance(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
+    const uint32_t chunk = 32u * B.lpl;
+    // a block whose first possible claim lies beyond the active lineages has
+    // nothing to do (claims go out in order of arrival, at most one per warp)
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    // the logarithm tables are staged only if some simulation sums exponentials
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    uint32_t chunk_next = 0, chunk_end = 0;  // warp-uniform
+    bool exhausted = false;
+
+    bool has = false;
+    uint32_t idx = 0, gid = 0;
+    uint64_t loc = 0;
+    double tn = 0.0, tprev = 0.0;
+    LaneSim c;
+    c.sim = 0xFFFFFFFFu;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t ev_lin = 0, lane_max = 0;  // events of the lane's lineage this round, and their maximum
+
+    for (;;) {
+        unsigned need = __ballot_sync(0xFFFFFFFFu, !has);
+        if (need) {
+            if (chunk_next >= chunk_end && !exhausted) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&B.G->work_ctr, chunk);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base >= n) {
+                    exhausted = true;
+                } else {
+                    chunk_next = base;
+                    chunk_end = min(base + chunk, n);
+                }
+            }
+            if (chunk_next < chunk_end) {
+                const uint32_t avail = chunk_end - chunk_next;
+                const uint32_t rank = __popc(need & lt_mask);
+                if (!has && rank < avail) {
+                    idx = chunk_next + rank;
+                    gid = L.gid[idx];
+                    loc = L.loc[idx];
+                    tn = L.tn[idx];
+                    if (LOG) tprev = L.tp[idx];
+                    const uint32_t s = L.sim[idx];
+                    if (s != c.sim) {
+                        if (cnt_sim != 0xFFFFFFFFu && (ev_raw | ev_unique)) {
+                            atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                            if (COUNT)
+                                atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events,
+                                          (unsigned long long)ev_unique);
+                            ev_raw = ev_unique = 0;
+                        }
+                        load_lanesim(c, B.P, B.S, s);
+                        cnt_sim = s;
+                    }
+                    has = true;
+                    ev_lin = 0;
+                }
+                chunk_next += min(avail, (uint32_t)__popc(need));
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, has)) {
+            if (exhausted) break;
+            continue;
+        }
+        // up to events_per_visit events of the lane's lineage between warp votes
+        for (uint32_t visit = 0; has && visit < B.events_per_visit; ++visit) {
+            // both non-negative: compare the bit patterns (an integer compare)
+            if ((uint64_t)__double_as_longlong(tn) > (uint64_t)__double_as_longlong(c.horizon)) {
+                // at the horizon: write back and enter the dedup
+                L.loc[idx] = loc;
+                L.tn[idx] = tn;
+                if (LOG) L.tp[idx] = tprev;
+                if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                has = false;
+            } else {
+                ++ev_raw;
+                lane_max = max(lane_max, ++ev_lin);
+                if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+                const uint64_t at = loc;
+                const bool speciated = do_event(c, B.P, loc, tn);
+                if (LOG) {
+                    log_event(B, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                    tprev = tn;
+                }
+                if (speciated) {
+                    B.key_loc[gid] = loc;
+                    B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                    L.gid[idx] = gid | DONE_BIT;
+                    has = false;
+                } else {
+                    const double nt = next_event_time<WIDE>(c, loc, tn, ln);
+                    if (search_failed(nt)) {
+                        atomicOr(&B.S[c.sim].error, 1u);
+                        atomicOr(&B.G->error, 1u);
+                        B.key_loc[gid] = ~0ull;
+                        B.key_time[gid] = ~0ull;
+                        L.gid[idx] = gid | DONE_BIT;
+                        has = false;
+                    } else {
+                        tn = nt;
+                    }
+                }
+            }
+        }
+    }
+    // flush the event counters, aggregated over lanes of the same simulation
+    const bool valid = cnt_sim != 0xFFFFFFFFu;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+        warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
+        if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
+    }
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, lane_max);
+    if (lane == 0 && wmax) atomicMax(&B.G->round_max, wmax);
+}
+
+// Throughput phase, convergent form: every iteration each lane computes
+// exactly one Philox block whose counter depends on the lane's state (event
+// block 0 or 1, or the next block of its re-prime interval search), so the
+// bulk of the instructions runs with all lanes active; only the short
+// state-specific processing diverges.  Lanes refill from the warp's chunk
+// whenever they fall idle.  Same draws, same order, same results as the
+// one-lane-per-lineage loop above.
+constexpr uint32_t SM_IDLE = 0, SM_EVENT0 = 1, SM_EVENT1 = 2, SM_SEARCH = 3;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
+    const uint32_t chunk = 32u * B.lpl;
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    uint32_t chunk_next = 0, chunk_end = 0;  // warp-uniform
+    bool exhausted = false;
+
+    uint32_t st = SM_IDLE, idx = 0, gid = 0;
+    uint64_t loc = 0;
+    double tn = 0.0;
+    LaneSim c;
+    memset(&c, 0, sizeof(c));
+    c.sim = 0xFFFFFFFFu;
+    c.lam = 1.0;
+    c.lam1 = true;
+    uint64_t hz = 0;                          // horizon bits of the lane's simulation
+    uint64_t k = 0, tau_b = 0, end_b = 0, best = ~0ull, e0hi = 0;
+    uint32_t j = 0, N = 0, iv = 0;
+    double p = 0.0, base = 0.0;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t ev_lin = 0, lane_max = 0;  // events of the lane's lineage this round, and their maximum
+
+    auto fail = [&]() {
+        atomicOr(&B.S[c.sim].error, 1u);
+        atomicOr(&B.G->error, 1u);
+        B.key_loc[gid] = ~0ull;
+        B.key_time[gid] = ~0ull;
+        L.gid[idx] = gid | DONE_BIT;
+        st = SM_IDLE;
+    };
+    auto start_interval = [&]() {
+        base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
+        p = base;
+        best = ~0ull;
+        N = 0;
+        j = 0;
+        if (k >= (1ull << 52) || iv >= INTERVAL_LIMIT) fail();
+    };
+    auto begin_search = [&]() {
+        tau_b = (uint64_t)__double_as_longlong(tn);
+        k = floor_div_pow2(tau_b, c.dt_log2);
+        iv = 0;
+        st = SM_SEARCH;
+        start_interval();
+    };
+    auto found = [&](double v) {
+        tn = v;
+        if ((uint64_t)__double_as_longlong(tn) > hz) {  // beyond the horizon: park the lineage
+            L.loc[idx] = loc;
+            L.tn[idx] = tn;
+            if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+            st = SM_IDLE;
+        } else {
+            st = SM_EVENT0;
+        }
+    };
+
+    for (;;) {
+        // refill idle lanes from the warp's chunk
+        const unsigned need = __ballot_sync(0xFFFFFFFFu, st == SM_IDLE);
+        if (need) {
+            if (chunk_next >= chunk_end && !exhausted) {
+                uint32_t b0 = 0;
+                if (lane == 0) b0 = atomicAdd(&B.G->work_ctr, chunk);
+                b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+                if (b0 >= n) {
+                    exhausted = true;
+                } else {
+                    chunk_next = b0;
+                    chunk_end = min(b0 + chunk, n);
+                }
+            }
+            if (chunk_next < chunk_end) {
+                const uint32_t avail = chunk_end - chunk_next;
+                const uint32_t rank = __popc(need & lt_mask);
+                if (st == SM_IDLE && rank < avail) {
+                    idx = chunk_next + rank;
+                    gid = L.gid[idx];
+                    loc = L.loc[idx];
+                    tn = L.tn[idx];
+                    const uint32_t s = L.sim[idx];
+                    if (s != c.sim) {
+                        if (cnt_sim != 0xFFFFFFFFu && (ev_raw | ev_unique)) {
+                            atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                            if (COUNT)
+                                atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events,
+                                          (unsigned long long)ev_unique);
+                            ev_raw = ev_unique = 0;
+                        }
+                        load_lanesim(c, B.P, B.S, s);
+                        cnt_sim = s;
+                        hz = (uint64_t)__double_as_longlong(c.horizon);
+                    }
+                    ev_lin = 0;
+                    if ((uint64_t)__double_as_longlong(tn) > hz) {
+                        if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);  // already at the horizon
+                    } else {
+                        st = SM_EVENT0;
+                    }
+                }
+                chunk_next += min(avail, (uint32_t)__popc(need));
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, st != SM_IDLE)) {
+            if (exhausted) break;
+            continue;
+        }
+        // one Philox block per lane, its counter chosen by the lane's state
+        const bool ev = st == SM_EVENT0 || st == SM_EVENT1;
+        const uint64_t tkey = ev ? (uint64_t)__double_as_longlong(tn) : k;
+        const uint32_t jj = ev ? (st == SM_EVENT1 ? 1u : 0u) : j;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, tkey, jj, ev ? TAG_EVENT : TAG_INTERVAL);
+        // the two exponentials of the block, when some lane of the warp sums them
+        double x0 = 0.0, x1 = 0.0;
+        if (__any_sync(0xFFFFFFFFu, st == SM_SEARCH && c.sampler == 0)) {
+            x0 = exp_draw<true>(b.lo, ln, c);
+            x1 = exp_draw<true>(b.hi, ln, c);
+            if (!c.lam1) {
+                x0 = div_rn_call(x0, c.lam);
+                x1 = div_rn_call(x1, c.lam);
+            }
+        }
+        if (st == SM_EVENT0) {
+            ++ev_raw;
+            lane_max = max(lane_max, ++ev_lin);
+            if (COUNT) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+            if ((b.lo >> 11) < spec_thr(c, B.P, c.kind, loc)) {
+                B.key_loc[gid] = loc;
+                B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                L.gid[idx] = gid | DONE_BIT;
+                st = SM_IDLE;
+            } else if (c.kind == KIND_NONSPATIAL || (c.kind == KIND_IMPLICIT && in_meta(loc))) {
+                loc = disperse(c, B.P, loc, b.hi, 0ull, 0ull);
+                begin_search();
+            } else {
+                e0hi = b.hi;
+                st = SM_EVENT1;
+            }
+        } else if (st == SM_EVENT1) {
+            loc = disperse(c, B.P, loc, e0hi, b.lo, b.hi);
+            begin_search();
+        } else if (st == SM_SEARCH) {
+            if (c.sampler == 0) {
+                // sums of exponentials: draws 2j and 2j + 1 of interval k
+                int r = 0;
+                p = __dadd_rn(p, x0);
+                uint64_t pb = (uint64_t)__double_as_longlong(p);
+                r = pb >= end_b ? 2 : (pb > tau_b ? 1 : 0);
+                if (r == 0) {
+                    p = __dadd_rn(p, x1);
+                    pb = (uint64_t)__double_as_longlong(p);
+                    r = pb >= end_b ? 2 : (pb > tau_b ? 1 : 0);
+                }
+                if (r == 1) {
+                    found(p);
+                } else if (r == 2) {
+                    ++k;
+                    ++iv;
+                    start_interval();
+                } else if (++j >= INTERVAL_BLOCK_LIMIT) {
+                    fail();
+                }
+            } else {
+                // Poisson points: block j holds draws 2j, 2j + 1; draw 0 is the count
+                auto consider = [&](uint64_t r) {
+                    const double x = q53_scaled(r >> 11, c.dt_log2 - 53);
+                    const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+                    if (pb > tau_b && pb < best) best = pb;
+                };
+                if (j == 0) {
+                    N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b.lo);
+                    if (N >= 1) consider(b.hi);
+                } else {
+                    if (2u * j - 1u < N) consider(b.lo);
+                    if (2u * j < N) consider(b.hi);
+                }
+                if (2u * j + 1u >= N) {
+                    if (best != ~0ull) {
+                        found(__longlong_as_double((long long)best));
+                    } else {
+                        ++k;
+                        ++iv;
+                        start_interval();
+                    }
+                } else {
+                    ++j;
+                }
+            }
+        }
+    }
+    // flush the event counters, aggregated over lanes of the same simulation
+    const bool valid = cnt_sim != 0xFFFFFFFFu;
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+        warp_add_by_sim(vm, cnt_sim, ev_raw, &B.S[0].raw_events, sizeof(SimState));
+        if (COUNT) warp_add_by_sim(vm, cnt_sim, ev_unique, &B.S[0].unique_events, sizeof(SimState));
+    }
+    const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, lane_max);
+    if (lane == 0 && wmax) atomicMax(&B.G->round_max, wmax);
+}
+
+
+// evaluates in parallel the draws a one-lane search would reach one after
+// another.  Lane 0 writes the results.
+// MODE 1: every simulation sums exponentials with lambda = 1 on the short
+// search; MODE 2: every simulation draws Poisson points on the short search;
+// MODE 0: any mix (the search chosen per lineage).  KIND: the landscape kind
+// shared by every simulation, or -1.  The specialised kernels are smaller,
+// which matters where one warp runs alone and waits on instruction fetch.
+template <bool COUNT, int MODE, int KIND, bool LOG = false>
+__global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char adv_smem[];
+    const uint32_t n = B.G->n_total;
+    if (n > B.coop_lineages) return;  // a round for the one-lane form
+    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
+    const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs L = B.lin[t];
+    const uint32_t lane = threadIdx.x & 31u;
+    uint64_t ev_raw = 0, ev_unique = 0;
+    uint32_t cnt_sim = 0xFFFFFFFFu;
+    uint32_t lane_max = 0;  // most events of one lineage this round (the same in every lane)
+    WarpLogBuf wlog;
+    wlog.n = 0;
+    for (;;) {
+        uint32_t idx = 0;
+        if (lane == 0) idx = atomicAdd(&B.G->work_ctr, 1u);
+        idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+        if (idx >= n) break;
+        const uint32_t gid = L.gid[idx];
+        uint64_t loc = L.loc[idx];
+        double tn = L.tn[idx];
+        double tprev = LOG ? L.tp[idx] : 0.0;
+        const uint32_t s = L.sim[idx];
+        LaneSim c;
+        load_lanesim(c, B.P, B.S, s);
+        if (s != cnt_sim) {
+            if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
+                atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+                if (COUNT)
+                    atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
+            }
+            ev_raw = ev_unique = 0;
+            cnt_sim = s;
+        }
+        const uint64_t hz = (uint64_t)__double_as_longlong(c.horizon);
+        uint32_t ev_lin = 0;
+        for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
+            if ((uint64_t)__double_as_longlong(tn) > hz) {
+                if (lane == 0) {
+                    L.loc[idx] = loc;
+                    L.tn[idx] = tn;
+                    if (LOG) L.tp[idx] = tprev;
+                    if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                }
+                break;
+            }
+            ++ev_raw;
+            lane_max = max(lane_max, ++ev_lin);
+            if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+            const uint64_t at = loc;
+            const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane);
+            if (LOG) {
+                warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                tprev = tn;
+            }
+            if (speciated) {
+                if (lane == 0) {
+                    B.key_loc[gid] = loc;
+                    B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                    L.gid[idx] = gid | DONE_BIT;
+                }
+                break;
+            }
+            double nt;
+            if (MODE == 1) {
+                nt = coop_next_exp_short<true>(c, loc, tn, ln, lane);
+            } else if (MODE == 2) {
+                nt = coop_next_poisson_short(c, loc, tn, lane);
+            } else {
+                nt = c.sampler == 1 ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
+                                                    : coop_next_poisson(c, loc, tn, lane))
+                     : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
+                                              : coop_next_exp_short<false>(c, loc, tn, ln, lane))
+                                    : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
+                                              : coop_next_exp<false>(c, loc, tn, ln, lane));
+            }
+            if (search_failed(nt)) {
+                if (lane == 0) {
+                    atomicOr(&B.S[c.sim].error, 1u);
+                    atomicOr(&B.G->error, 1u);
+                    B.key_loc[gid] = ~0ull;
+                    B.key_time[gid] = ~0ull;
+                    L.gid[idx] = gid | DONE_BIT;
+                }
+                break;
+            }
+            tn = nt;
+        }
+    }
+    if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
+        atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
+        if (COUNT) atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);
+    }
+    if (lane == 0 && lane_max) atomicMax(&B.G->round_max, lane_max);
+    if (LOG) warp_log_flush(B, wlog, lane);
+}
+
+// horizon step (time) of a simulation with n active lineages
+__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n) {
+    const double dn = (double)n;
+    const double floor_ev = dn < p->busy_lineages ? p->tail_events : p->min_events;
+    const double per = fmax(floor_ev, fmin(p->occupancy_step * p->n_slots / dn, p->events_per_round / dn));
+    return fmin(per, p->max_step_events) / p->lambda;
+}
+
+__global__ void k_compact(BatchDev B) {
+    const uint32_t t = B.G->round & 1u;
+    const LinPtrs in = B.lin[t];
+    const LinPtrs out = B.lin[t ^ 1u];
+    const uint32_t n = B.G->n_total;
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+
+    for (uint32_t base = warp_global * 32u; base < n; base += n_warps * 32u) {
+        const uint32_t i = base + lane;
+        bool survive = false, culled = false;
+        uint32_t s = 0xFFFFFFFFu, g = 0;
+        uint64_t loc = 0;
+        double tn = 0.0, tprev = 0.0;
+        if (i < n) {
+            g = in.gid[i];
+            if (!(g & DONE_BIT)) {
+                s = in.sim[i];
+                loc = in.loc[i];
+                tn = in.tn[i];
+                if (in.tp) tprev = in.tp[i];
+                survive = true;
+                if (B.dedup) {
+                    const uint32_t w = dedup_lookup(B, t, slot_index(B.P + s, loc));
+                    if (w != g && w != 0xFFFFFFFFu) {
+                        B.parent[g] = w;
+                        survive = false;
+                        culled = true;
+                        if (in.tp) log_event(B, tn, tprev, loc, LOG_CULLED, g);
+                    }
+                }
+            }
+        }
+        const unsigned sm = __ballot_sync(0xFFFFFFFFu, survive);
+        const unsigned cm = __ballot_sync(0xFFFFFFFFu, culled);
+        uint32_t pos0 = 0;
+        if (lane == 0 && sm) pos0 = atomicAdd(&B.G->n_total_next, (uint32_t)__popc(sm));
+        pos0 = __shfl_sync(0xFFFFFFFFu, pos0, 0);
+        if (survive) {
+            const uint32_t pos = pos0 + __popc(sm & lt_mask);
+            out.loc[pos] = loc;
+            out.tn[pos] = tn;
+            out.gid[pos] = g;
+            out.sim[pos] = s;
+            if (out.tp) out.tp[pos] = tprev;
+        }
+        if (sm) {
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, survive ? s : 0xFFFFFFFFu);
+            if (survive && lane == (uint32_t)(__ffs(grp) - 1))
+                atomicAdd(&B.S[s].n_next, (uint32_t)__popc(grp));
+        }
+        if (cm) {
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, culled ? s : 0xFFFFFFFFu);
+            if (culled && lane == (uint32_t)(__ffs(grp) - 1))
+                atomicAdd(&B.S[s].culled_round, (uint32_t)__popc(grp));
+        }
+    }
+    // clear the dedup / event tables of the previous round (no longer read)
+    const uint32_t tp = t ^ 1u;
+    const uint32_t nu = B.G->used[tp];
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nu; k += gridDim.x * blockDim.x) {
+        const uint32_t h = B.ht_used[tp][k];
+        B.ht_key[tp][h] = EMPTY_KEY;
+        B.ht_val[tp][h] = 0xFFFFFFFFu;
+    }
+    if (B.count_unique) {
+        const uint32_t ne = B.G->ev_used[tp];
+        for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += gridDim.x * blockDim.x) {
+            const uint32_t h = B.ev_used[tp][k];
+            B.ev[tp][h].a = EMPTY_KEY;
+            B.ev[tp][h].b = EMPTY_KEY;
+        }
+    }
+
+    // the last block to finish advances the round
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&B.G->blocks_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    __shared__ uint32_t live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
+        SimState* st = B.S + s;
+        const uint32_t na = atomicAdd(&st->n_next, 0u);
+        const uint32_t nc = atomicAdd(&st->culled_round, 0u);
+        st->culled += nc;
+        st->culled_round = 0;
+        st->n_next = 0;
+        if (st->done) continue;
+        st->n_active = na;
+        st->rounds += 1;
+        if (na == 0) {
+            st->done = 1;
+            continue;
+        }
+        atomicAdd(&live, 1u);
+        st->horizon = st->horizon + horizon_step(B.P + s, na);
+    }
+    __syncthreads();
+    if (B.G->prof_events) {
+        __shared__ unsigned long long ev_sum;
+        if (threadIdx.x == 0) ev_sum = 0;
+        __syncthreads();
+        unsigned long long part = 0;
+        for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) part += B.S[s].raw_events;
+        atomicAdd(&ev_sum, part);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t slot = B.G->prof_slot;
+            if (slot < B.G->prof_n) B.G->prof_events[slot] = ev_sum;
+            B.G->prof_slot = slot + 1;
+        }
+    }
+    if (threadIdx.x == 0) {
+        Globals* G = B.G;
+        const uint32_t nt = atomicAdd(&G->n_total_next, 0u);
+        G->n_total = nt;
+        G->n_total_next = 0;
+        G->work_ctr = 0;
+        G->blocks_done = 0;
+        G->used[tp] = 0;
+        G->ev_used[tp] = 0;
+        G->n_live_sims = live;
+        G->critical_events += G->round_max;
+        G->round_max = 0;
+        uint32_t cap = 2u;
+        while (cap < 2u * nt && cap < B.ht_cap) cap <<= 1;
+        G->mask[tp] = cap - 1u;  // the next round uses table tp
+        G->round += 1;
+        __threadfence();
+    }
+}
+
+// initial horizons and counters of a fresh batch
+__global__ void k_start(BatchDev B, uint32_t n_lin) {
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
+        const SimParams* p = B.P + s;
+        SimState* st = B.S + s;
+        const uint32_t na = p->n_lineages;
+        st->n_active = na;
+        st->done = na == 0 ? 1u : 0u;
+        st->horizon = horizon_step(p, max(na, 1u));
+    }
+    if (threadIdx.x == 0) {
+        Globals* G = B.G;
+        G->n_total = n_lin;
+        uint32_t cap = 2u;
+        while (cap < 2u * n_lin && cap < B.ht_cap) cap <<= 1;
+        G->mask[0] = cap - 1u;
+        G->mask[1] = cap - 1u;
+    }
+}

@@ -1,0 +1,618 @@
+// engine_events.cuh -- per-lineage event arithmetic: event-time searches, dispersal, the event step, dedup and log helpers.
+// A part of the engine.cu translation unit, included there in order after
+// the parts before it; not a standalone header.
+#pragma once
+
+// ---------------------------------------------------------------------------
+// per-lineage event arithmetic
+// ---------------------------------------------------------------------------
+struct LaneSim {
+    uint32_t sim;
+    int kind;
+    uint32_t W, H, D;
+    uint64_t nu_thr;
+    uint32_t sk0, sk1;
+    int dt_log2;
+    double lam;
+    bool lam1;
+    double horizon;
+    int sampler;
+    bool coop_short;
+    uint32_t pois_n;
+    const uint64_t* pois_cdf;
+    const uint32_t* pois_guide;
+    int32_t gauss_half;
+    uint32_t gauss_n;
+    const uint64_t* gauss;
+    const uint32_t* gauss_guide;
+};
+
+__device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
+                                             const SimState* S, uint32_t sim) {
+    const SimParams* p = P + sim;
+    c.sim = sim;
+    c.kind = __ldg(&p->kind);
+    c.W = __ldg(&p->W);
+    c.H = __ldg(&p->H);
+    c.D = __ldg(&p->D);
+    c.nu_thr = __ldg(&p->nu_thr);
+    c.sk0 = __ldg(&p->sk0);
+    c.sk1 = __ldg(&p->sk1);
+    c.dt_log2 = __ldg(&p->dt_log2);
+    c.lam = __ldg(&p->lambda);
+    c.lam1 = (c.lam == 1.0);
+    c.sampler = __ldg(&p->sampler);
+    c.pois_n = __ldg(&p->pois_n);
+    c.pois_cdf = p->pois_cdf;
+    c.pois_guide = p->pois_guide;
+    c.coop_short = __ldg(&p->coop_short) != 0u;
+    c.gauss_half = __ldg(&p->gauss_half);
+    c.gauss_n = __ldg(&p->gauss_n);
+    c.gauss = p->gauss;
+    c.gauss_guide = p->gauss_guide;
+    c.horizon = *(volatile const double*)&S[sim].horizon;
+}
+
+// the logarithm tables (global, read through L1, or a block's shared copy)
+struct LnC {
+    const uint64_t* L;
+    const uint32_t* R;
+    uint64_t ln2;
+    int64_t c3;
+};
+
+__device__ __forceinline__ LnC ln_tables() {
+    return LnC{g_ln.L, g_ln.R, g_ln.ln2_q64, g_ln.c3};
+}
+
+constexpr size_t LN_SMEM_BYTES = sizeof(uint64_t) * LN_N + sizeof(uint32_t) * LN_N;
+
+// copy the logarithm tables into shared memory (all threads of the block)
+__device__ __forceinline__ LnC ln_tables_shared(unsigned char* smem) {
+    uint4* dst = (uint4*)smem;
+    const uint4* src = (const uint4*)&g_ln;  // L then R, contiguous, 16-byte aligned
+    for (uint32_t i = threadIdx.x; i < LN_SMEM_BYTES / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    return LnC{(const uint64_t*)smem, (const uint32_t*)(smem + sizeof(uint64_t) * LN_N), g_ln.ln2_q64, g_ln.c3};
+}
+
+// binary64 of q 2^-58: the hardware conversion rounds q to nearest even, and
+// the scaling by 2^-58 is exact (normal range), applied to the exponent field
+__device__ __forceinline__ double q58_to_double_hw(uint64_t q) {
+    if (q == 0ull) return 0.0;
+    const uint64_t b = (uint64_t)__double_as_longlong(__ull2double_rn(q));
+    return __longlong_as_double((long long)(b - (58ull << 52)));
+}
+
+// Exp(lambda) draw.  LAM1 (lambda = 1) is a template argument rather than a
+// select: given both operands the compiler evaluates the binary64 division
+// even where it is not used, on the latency chain and on B300's narrow FP64
+// pipe.  Callers branch on c.lam1 once per search.
+// the division out of line, for code whose lanes mix lambdas: a call is
+// not evaluated speculatively
+__device__ __noinline__ double div_rn_call(double x, double y) { return __ddiv_rn(x, y); }
+
+template <bool LAM1>
+__device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const LaneSim& c) {
+    const double x = q58_to_double(exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+    if (LAM1) return x;
+    return __ddiv_rn(x, c.lam);
+}
+
+// first point of loc's event process strictly after tau; negative on overflow.
+// Times are non-negative binary64, so they order like their bit patterns: the
+// compares, floor(tau / delta_t) and k delta_t are done on the bits.  WIDE
+// blocks (2 WIDE draws) are generated and converted together; the draws of a
+// step are independent, so their logarithms overlap, and only the binary64
+// sums run one after another, in the spec's order.
+template <int WIDE, bool LAM1>
+__device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
+        if (k >= (1ull << 52)) return -1.0;
+        double p = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const uint64_t end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
+        bool next_interval = false;
+        for (uint32_t j = 0; j < INTERVAL_BLOCK_LIMIT; j += WIDE) {
+            double x[2 * WIDE];
+#pragma unroll
+            for (int w = 0; w < WIDE; ++w) {
+                const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
+                x[2 * w] = exp_draw<LAM1>(b.lo, ln, c);
+                x[2 * w + 1] = exp_draw<LAM1>(b.hi, ln, c);
+            }
+#pragma unroll
+            for (int d = 0; d < 2 * WIDE; ++d) {
+                p = __dadd_rn(p, x[d]);
+                const uint64_t pb = (uint64_t)__double_as_longlong(p);
+                if (pb >= end_b) {
+                    next_interval = true;
+                    break;
+                }
+                if (pb > tau_b) return p;
+            }
+            if (next_interval) break;
+        }
+        if (!next_interval) return -1.0;
+        ++k;
+    }
+    return -1.0;
+}
+
+// number of table entries <= r: the guide entry of r's bucket, and a scan
+// of the table only where a threshold falls inside the bucket
+__device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t, const uint32_t* __restrict__ guide,
+                                                 uint32_t n, uint64_t r) {
+    const uint32_t e = __ldg(guide + (r >> (64 - GUIDE_BITS)));
+    uint32_t idx = e & ~GUIDE_SCAN;
+    if (e & GUIDE_SCAN)
+        while (idx < n && __ldg(t + idx) <= r) ++idx;
+    return idx;
+}
+
+// Poisson method: interval k holds N ~ Poi(lambda dt) points (N = the count
+// of CDF thresholds <= draw 0), point i at k dt + U dt, U = (draw (1 + i)
+// >> 11) 2^-53, the sum rounded to nearest; the next event is the smallest
+// point > tau of the first interval that has one.  The points of an interval
+// are independent of each other, so there is no sequential chain.
+__device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double tau) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
+        if (k >= (1ull << 52)) return -1.0;
+        const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t best = ~0ull;
+        auto consider = [&](uint64_t r) {
+            const double x = q53_scaled(r >> 11, c.dt_log2 - 53);  // U dt, exact
+            const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+            if (pb > tau_b && pb < best) best = pb;
+        };
+        if (N >= 1) consider(b0.hi);
+        for (uint32_t j = 1; 2 * j <= N; ++j) {
+            const u64x2 bj = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+            consider(bj.lo);
+            if (2 * j + 1 <= N) consider(bj.hi);
+        }
+        if (best != ~0ull) return __longlong_as_double((long long)best);
+        ++k;
+    }
+    return -1.0;
+}
+
+// the searches return a time >= 0, or -1 when they give up: a sign-bit test
+// rather than a binary64 compare, which is slow on B300 and on the chain
+__device__ __forceinline__ bool search_failed(double t) { return __double_as_longlong(t) < 0; }
+
+template <int WIDE>
+__device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+    if (c.sampler == 1) return next_event_time_poisson(c, loc, tau);
+    return c.lam1 ? next_event_time_exp<WIDE, true>(c, loc, tau, ln) : next_event_time_exp<WIDE, false>(c, loc, tau, ln);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative next-event searches (one lineage per warp; every lane
+// returns the same time).  They compute exactly what the one-lane searches
+// compute; the lanes only evaluate draws that the one-lane search may need,
+// ahead of time and side by side.
+// ---------------------------------------------------------------------------
+// Poisson sampler: lane l searches interval k + l (k = floor(tau / dt)); the
+// answer is the smallest point > tau of the lowest interval that has one.
+__device__ double coop_next_poisson(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 32; ++round) {
+        const uint64_t k = k0 + 32ull * round + lane;
+        uint64_t best = ~0ull;
+        if (k < (1ull << 52)) {
+            const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+            const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+            const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+            auto consider = [&](uint64_t r) {
+                const double x = q53_scaled(r >> 11, c.dt_log2 - 53);  // U dt, exact
+                const uint64_t pb = (uint64_t)__double_as_longlong(__dadd_rn(base, x));
+                if (pb > tau_b && pb < best) best = pb;
+            };
+            if (N >= 1) consider(b0.hi);
+            for (uint32_t j = 1; 2 * j <= N; ++j) {
+                const u64x2 bj = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+                consider(bj.lo);
+                if (2 * j + 1 <= N) consider(bj.hi);
+            }
+        }
+        const unsigned found = __ballot_sync(0xFFFFFFFFu, best != ~0ull);
+        if (found) return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, best, __ffs(found) - 1));
+        if (k0 + 32ull * round + 32ull >= (1ull << 52)) return -1.0;
+    }
+    return -1.0;
+}
+
+// Sums of exponentials: in each step lanes 0-15 hold draws 16 qa .. 16 qa + 15
+// of interval k and lanes 16-31 draws 0 .. 15 of interval k + 1, all
+// converted side by side; the binary64 running sums then follow the spec's
+// order one draw at a time (shuffled from the lane that holds it).
+template <bool LAM1>
+__device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    uint64_t k = floor_div_pow2(tau_b, c.dt_log2);
+    uint32_t qa = 0;  // 16-draw groups of interval k already summed
+    double p = 0.0;   // running sum of interval k (valid when qa > 0)
+    for (uint32_t it = 0; it < INTERVAL_LIMIT; ++it) {
+        if (k + 2ull >= (1ull << 52) || qa >= 2u * INTERVAL_BLOCK_LIMIT / 16u) return -1.0;
+        if (qa == 0) p = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+        const uint64_t end_b = k_times_pow2_bits(k + 1ull, c.dt_log2);
+        const uint64_t kk = lane < 16u ? k : k + 1ull;
+        const uint32_t d = lane < 16u ? 16u * qa + lane : lane - 16u;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, kk, d >> 1, TAG_INTERVAL);
+        const double x = exp_draw<LAM1>((d & 1u) ? b.hi : b.lo, ln, c);
+        bool done_k = false;
+        for (uint32_t i = 0; i < 16u; ++i) {
+            p = __dadd_rn(p, __shfl_sync(0xFFFFFFFFu, x, i));
+            const uint64_t pb = (uint64_t)__double_as_longlong(p);
+            if (pb >= end_b) {
+                done_k = true;
+                break;
+            }
+            if (pb > tau_b) return p;
+        }
+        if (!done_k) {  // interval k goes on: its next 16 draws in the next step
+            ++qa;
+            continue;
+        }
+        // interval k + 1 from its first 16 draws (lanes 16-31)
+        double p1 = __longlong_as_double((long long)k_times_pow2_bits(k + 1ull, c.dt_log2));
+        const uint64_t end1_b = k_times_pow2_bits(k + 2ull, c.dt_log2);
+        bool done_k1 = false;
+        for (uint32_t i = 0; i < 16u; ++i) {
+            p1 = __dadd_rn(p1, __shfl_sync(0xFFFFFFFFu, x, 16 + i));
+            const uint64_t pb = (uint64_t)__double_as_longlong(p1);
+            if (pb >= end1_b) {
+                done_k1 = true;
+                break;
+            }
+            if (pb > tau_b) return p1;
+        }
+        if (done_k1) {
+            k += 2ull;
+            qa = 0;
+        } else {  // interval k + 1 needs more than 16 draws: go on from draw 16
+            k += 1ull;
+            qa = 1;
+            p = p1;
+        }
+    }
+    return -1.0;
+}
+
+// Short searches (lambda dt <= 2, and >= 1/2 for Poisson points): lanes
+// 8 m .. 8 m + 7 take interval k + m (m = 0..3, k = floor(tau / dt)), lane
+// 8 m + i the interval's point i.  Intervals of more than 8 points are rare
+// here (Poi(2) > 8: 2.4e-4 of intervals); the search then starts again in
+// the general form above.  Four intervals without an answer: go on at k + 4.
+__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        if (k0 + 4ull >= (1ull << 52)) return coop_next_poisson(c, loc, tau, lane);
+        const uint64_t k = k0 + m;
+        // draw 0 gives the count N; point i is draw 1 + i
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const u64x2 bi = stream_block(c.sk0, c.sk1, loc, k, (1u + i) >> 1, TAG_INTERVAL);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t pb = ~0ull;
+        if (i < N) {
+            const uint64_t r = (i & 1u) ? bi.lo : bi.hi;
+            const double base = __longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2));
+            const uint64_t q = (uint64_t)__double_as_longlong(__dadd_rn(base, q53_scaled(r >> 11, c.dt_log2 - 53)));
+            if (q > tau_b) pb = q;
+        }
+        if (__any_sync(0xFFFFFFFFu, N > 8u)) return coop_next_poisson(c, loc, tau, lane);
+        // the smallest point > tau of the four intervals is the smallest of
+        // the first interval that has one: points of interval k lie in
+        // [k dt, (k + 1) dt], rounding included
+        const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32));
+        if (hi != 0xFFFFFFFFu) {
+            const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32) == hi ? (uint32_t)pb : 0xFFFFFFFFu);
+            return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
+        }
+    }
+    return -1.0;
+}
+
+// sums of exponentials: every lane runs interval k's binary64 running sum in
+// the spec's order on the shuffled draws; intervals k + 1 .. k + 3 only need
+// their first point
+template <bool LAM1>
+__device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        if (k0 + 4ull >= (1ull << 52)) return coop_next_exp<LAM1>(c, loc, tau, ln, lane);
+        const uint64_t k = k0 + m;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, i >> 1, TAG_INTERVAL);
+        const double x = exp_draw<LAM1>((i & 1u) ? b.hi : b.lo, ln, c);
+        double xs[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xs[j] = __shfl_sync(0xFFFFFFFFu, x, j);
+        // first point of interval k (lanes 8 m), kept if inside the interval
+        const double first = __dadd_rn(__longlong_as_double((long long)k_times_pow2_bits(k, c.dt_log2)), x);
+        const bool has = i == 0u && m > 0u &&
+                         (uint64_t)__double_as_longlong(first) < k_times_pow2_bits(k + 1ull, c.dt_log2);
+        double p = __longlong_as_double((long long)k_times_pow2_bits(k0, c.dt_log2));
+        const uint64_t end0 = k_times_pow2_bits(k0 + 1ull, c.dt_log2);
+        int state = 0;  // 1: point after tau, 2: interval k0 ended first
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            p = __dadd_rn(p, xs[j]);
+            const uint64_t pb = (uint64_t)__double_as_longlong(p);
+            if (pb >= end0) {
+                state = 2;
+                break;
+            }
+            if (pb > tau_b) {
+                state = 1;
+                break;
+            }
+        }
+        if (state == 1) return p;
+        if (state == 0) return coop_next_exp<LAM1>(c, loc, tau, ln, lane);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, has);
+        if (bal) return __shfl_sync(0xFFFFFFFFu, first, __ffs(bal) - 1);
+    }
+    return -1.0;
+}
+
+// dispersal target from the event stream's draws 1, 2, 3 (draw 0 decided
+// speciation): non-spatial uses d1; torus d1 (x), d2 (y), d3 (deme index),
+// each axis a discretised normal by inversion, -half + #{k : cdf[k] <= d};
+// map d1 (alias column and threshold), d2 (deme index); spatially implicit
+// d1 (migration, or the metacommunity parent), d2 (parent after migration
+// or locally)
+// (KIND: the landscape kind when the caller knows it at compile time, -1
+// for the simulation's own)
+template <int KIND = -1>
+__device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* __restrict__ P, uint64_t loc,
+                                            uint64_t d1, uint64_t d2, uint64_t d3) {
+    const int kind = KIND >= 0 ? KIND : c.kind;
+    if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
+    const SimParams* p = P + c.sim;
+    if (kind == KIND_IMPLICIT) {
+        // in the metacommunity: a uniform parent there (d1); locally:
+        // migration iff d1 says so, then the parent's index (d2) in the
+        // metacommunity or the local community
+        const uint64_t meta_n = __ldg(&p->meta_size);
+        if (in_meta(loc)) return meta_loc(umulhi64(d1, meta_n));
+        if ((d1 >> 11) < __ldg(&p->m_thr)) return meta_loc(umulhi64(d2, meta_n));
+        return pack_loc(0, 0, umulhi64(d2, c.D));
+    }
+    const uint32_t x = loc_x(loc), y = loc_y(loc);
+    if (kind == KIND_TORUS) {
+        // both guide entries first, so that the two loads overlap; a table
+        // scan only for draws in a bucket that holds a threshold
+        const uint32_t ex = __ldg(c.gauss_guide + (d1 >> (64 - GUIDE_BITS)));
+        const uint32_t ey = __ldg(c.gauss_guide + (d2 >> (64 - GUIDE_BITS)));
+        uint32_t cx = ex & ~GUIDE_SCAN, cy = ey & ~GUIDE_SCAN;
+        if ((ex | ey) & GUIDE_SCAN) {
+            if (ex & GUIDE_SCAN)
+                while (cx < c.gauss_n && __ldg(c.gauss + cx) <= d1) ++cx;
+            if (ey & GUIDE_SCAN)
+                while (cy < c.gauss_n && __ldg(c.gauss + cy) <= d2) ++cy;
+        }
+        const uint32_t tx = wrap_add(x, (int32_t)cx - c.gauss_half, c.W);
+        const uint32_t ty = wrap_add(y, (int32_t)cy - c.gauss_half, c.H);
+        const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
+        return pack_loc(tx, ty, ti);
+    }
+    // habitat map: alias row of the origin cell
+    const uint32_t n_off = __ldg(&p->n_off);
+    const uint32_t row = __ldg(p->row_of + (size_t)y * c.W + x);
+    const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
+    const uint64_t e = __ldg(p->alias + (size_t)row * n_off + col);
+    const uint32_t u = (uint32_t)d1;
+    const uint32_t o = ((e >> 63) != 0 || u < (uint32_t)e) ? col : (uint32_t)((e >> 32) & 0xFFFFu);
+    const int8_t* off = p->off;
+    const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+    const uint32_t tx = wrap_add(x, dx, c.W);
+    const uint32_t ty = wrap_add(y, dy, c.H);
+    const uint32_t d = __ldg(p->deme_map + (size_t)ty * c.W + tx);
+    return pack_loc(tx, ty, umulhi64(d2, d));
+}
+
+// speciation threshold at loc: the metacommunity's in the spatially
+// implicit model, else the simulation's
+__device__ __forceinline__ uint64_t spec_thr(const LaneSim& c, const SimParams* __restrict__ P, int kind,
+                                             uint64_t loc) {
+    return (kind == KIND_IMPLICIT && in_meta(loc)) ? __ldg(&P[c.sim].meta_nu_thr) : c.nu_thr;
+}
+
+// one event at (loc, tau); returns true if the lineage speciated, else
+// moves loc to the dispersal target
+__device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
+                                         double tau) {
+    const uint64_t tk = (uint64_t)__double_as_longlong(tau);
+    const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
+    if (c.kind == KIND_NONSPATIAL || (c.kind == KIND_IMPLICIT && in_meta(loc))) {
+        if ((b0.lo >> 11) < spec_thr(c, P, c.kind, loc)) return true;
+        loc = disperse(c, P, loc, b0.hi, 0ull, 0ull);
+        return false;
+    }
+    const u64x2 b1 = stream_block(c.sk0, c.sk1, loc, tk, 1, TAG_EVENT);
+    if ((b0.lo >> 11) < c.nu_thr) return true;
+    loc = disperse(c, P, loc, b0.hi, b1.lo, b1.hi);
+    return false;
+}
+
+// do_event for one lineage per warp: lanes of even and odd index compute
+// the event stream's blocks 0 and 1 side by side, then every lane takes the
+// four draws by shuffle (one block's latency instead of two interleaved)
+template <int KIND>
+__device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
+                                              double tau, uint32_t lane) {
+    const int kind = KIND >= 0 ? KIND : c.kind;
+    const uint64_t tk = (uint64_t)__double_as_longlong(tau);
+    if (kind == KIND_NONSPATIAL) {
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
+        if ((b0.lo >> 11) < c.nu_thr) return true;
+        loc = disperse<KIND_NONSPATIAL>(c, P, loc, b0.hi, 0ull, 0ull);
+        return false;
+    }
+    const u64x2 b = stream_block(c.sk0, c.sk1, loc, tk, lane & 1u, TAG_EVENT);
+    const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0), d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
+    const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1), d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
+    if ((d0 >> 11) < spec_thr(c, P, kind, loc)) return true;
+    loc = disperse<KIND>(c, P, loc, d1, d2, d3);
+    return false;
+}
+
+// global slot index of a location: cells row-major x slot_deme + deme
+// index, after the simulation's slot_base; the spatially implicit model
+// numbers its J local individuals first, then the metacommunity
+__device__ __forceinline__ uint64_t slot_index(const SimParams* __restrict__ p, uint64_t loc) {
+    const uint64_t base = __ldg(&p->slot_base);
+    if (__ldg(&p->kind) == KIND_IMPLICIT)
+        return base + (in_meta(loc) ? (uint64_t)__ldg(&p->D) + meta_index(loc) : (uint64_t)loc_i(loc));
+    const uint64_t cell = (uint64_t)loc_y(loc) * __ldg(&p->W) + loc_x(loc);
+    return base + cell * __ldg(&p->slot_deme) + loc_i(loc);
+}
+
+__device__ __forceinline__ uint64_t slot_key(const SimParams* __restrict__ P, const LaneSim& c, uint64_t loc) {
+    return slot_index(P + c.sim, loc);
+}
+
+// exact distinct-event counting: insert (slot, time bits); true if new
+__device__ __forceinline__ bool count_event(const BatchDev& B, uint32_t t, uint64_t skey, double tau) {
+    EvSlot mine;
+    mine.a = skey;
+    mine.b = (unsigned long long)__double_as_longlong(tau);
+    EvSlot empty;
+    empty.a = EMPTY_KEY;
+    empty.b = EMPTY_KEY;
+    uint32_t h = (uint32_t)mix64(skey ^ (mine.b * 0x9E3779B97F4A7C15ull)) & B.ev_mask;
+    for (uint32_t probe = 0; probe <= B.ev_mask; ++probe) {
+        EvSlot old = atomicCAS(&B.ev[t][h], empty, mine);
+        if (old.a == EMPTY_KEY && old.b == EMPTY_KEY) {
+            uint32_t k = atomicAdd(&B.G->ev_used[t], 1u);
+            B.ev_used[t][k] = h;
+            return true;
+        }
+        if (old.a == mine.a && old.b == mine.b) return false;
+        h = (h + 1u) & B.ev_mask;
+    }
+    atomicOr(&B.G->error, 2u);
+    return false;
+}
+
+// log target of a culled lineage's pending event: the lineage does not
+// execute it (its winner does), but its copy carries its own prior time, so
+// that a coalescence stays visible in the stream
+constexpr uint64_t LOG_CULLED = ~1ull;
+
+// append one executed event to the log; past the capacity the run fails
+// with a device error (error bit 8) and the entry is dropped
+__device__ __forceinline__ void log_event(const BatchDev& B, double tn, double tp, uint64_t loc, uint64_t target,
+                                          uint32_t gid) {
+    const unsigned long long k = atomicAdd(&B.G->log_n, 1ull);
+    if (k < B.log.cap) {
+        B.log.time[k] = (uint64_t)__double_as_longlong(tn);
+        B.log.prior[k] = (uint64_t)__double_as_longlong(tp);
+        B.log.loc[k] = loc;
+        B.log.target[k] = target;
+        B.log.gid[k] = gid;
+    } else {
+        atomicOr(&B.G->error, 8u);
+    }
+}
+
+// event records of one warp: lane k holds the k-th pending one; a flush
+// takes one atomic for all of them, so that the log costs no round trip on
+// a lone lineage's chain of events
+struct WarpLogBuf {
+    uint64_t time, prior, loc, target;
+    uint32_t gid;
+    uint32_t n;  // records held (the same in every lane)
+};
+
+__device__ __forceinline__ void warp_log_flush(const BatchDev& B, WarpLogBuf& w, uint32_t lane) {
+    if (w.n == 0) return;
+    unsigned long long k0 = 0;
+    if (lane == 0) k0 = atomicAdd(&B.G->log_n, (unsigned long long)w.n);
+    k0 = __shfl_sync(0xFFFFFFFFu, k0, 0);
+    if (lane < w.n) {
+        const unsigned long long k = k0 + lane;
+        if (k < B.log.cap) {
+            B.log.time[k] = w.time;
+            B.log.prior[k] = w.prior;
+            B.log.loc[k] = w.loc;
+            B.log.target[k] = w.target;
+            B.log.gid[k] = w.gid;
+        } else {
+            atomicOr(&B.G->error, 8u);
+        }
+    }
+    w.n = 0;
+}
+
+__device__ __forceinline__ void warp_log_event(const BatchDev& B, WarpLogBuf& w, uint32_t lane, double tn, double tp,
+                                               uint64_t loc, uint64_t target, uint32_t gid) {
+    if (lane == w.n) {
+        w.time = (uint64_t)__double_as_longlong(tn);
+        w.prior = (uint64_t)__double_as_longlong(tp);
+        w.loc = loc;
+        w.target = target;
+        w.gid = gid;
+    }
+    if (++w.n == 32u) warp_log_flush(B, w, lane);
+}
+
+__device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint64_t skey, uint32_t gid) {
+    const uint32_t mask = B.G->mask[t];
+    uint32_t h = (uint32_t)mix64(skey) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long old = atomicCAS(&B.ht_key[t][h], EMPTY_KEY, (unsigned long long)skey);
+        if (old == EMPTY_KEY) {
+            uint32_t k = atomicAdd(&B.G->used[t], 1u);
+            B.ht_used[t][k] = h;
+            atomicMin(&B.ht_val[t][h], gid);
+            return;
+        }
+        if (old == skey) {
+            atomicMin(&B.ht_val[t][h], gid);
+            return;
+        }
+        h = (h + 1u) & mask;
+    }
+    atomicOr(&B.G->error, 4u);
+}
+
+__device__ __forceinline__ uint32_t dedup_lookup(const BatchDev& B, uint32_t t, uint64_t skey) {
+    const uint32_t mask = B.G->mask[t];
+    uint32_t h = (uint32_t)mix64(skey) & mask;
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = B.ht_key[t][h];
+        if (k == skey) return B.ht_val[t][h];
+        if (k == EMPTY_KEY) break;
+        h = (h + 1u) & mask;
+    }
+    return 0xFFFFFFFFu;
+}
+
+// warp-aggregated add of v to ctr[sim] over the lanes of mask
+__device__ __forceinline__ void warp_add_by_sim(unsigned mask, uint32_t sim, uint64_t v, uint64_t* base,
+                                                size_t stride_bytes) {
+    if (!mask) return;
+    const unsigned grp = __match_any_sync(mask, sim);
+    const int leader = __ffs(grp) - 1;
+    uint64_t sum = 0;
+    // reduce within the group: every lane contributes, the leader adds
+    for (int l = 0; l < 32; ++l) {
+        if (!((mask >> l) & 1u)) continue;
+        uint64_t x = __shfl_sync(mask, v, l);
+        if ((grp >> l) & 1u) sum += x;
+    }
+    if ((int)(threadIdx.x & 31) == leader && sum)
+        atomicAdd((unsigned long long*)((char*)base + stride_bytes * sim), (unsigned long long)sum);
+}

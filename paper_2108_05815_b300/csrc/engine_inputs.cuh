@@ -1,0 +1,126 @@
+// engine_inputs.cuh -- inputs: habitat map, alias rows, sampling, the arithmetic self-test.
+// A part of the engine.cu translation unit, included there in order after
+// the parts before it; not a standalone header.
+#pragma once
+
+// ---------------------------------------------------------------------------
+// inputs: habitat map, alias rows, sampling
+// ---------------------------------------------------------------------------
+__global__ void k_habitat(uint8_t* out, uint32_t W, uint32_t H, uint32_t sk0, uint32_t sk1, uint64_t thr,
+                          uint32_t max_deme) {
+    const uint64_t n = (uint64_t)W * H;
+    for (uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; c < n; c += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(c % W), y = (uint32_t)(c / W);
+        const u64x2 b = stream_block(sk0, sk1, pack_loc(x, y, 0), 0, 0, TAG_MAP);
+        out[c] = (b.lo >> 11) < thr ? (uint8_t)(1u + umulhi64(b.hi, max_deme)) : (uint8_t)0;
+    }
+}
+
+// one warp per habitable cell: weights, then integer Vose on lane 0
+__global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint32_t H,
+                              const uint32_t* __restrict__ cells, uint32_t n_rows, const int8_t* __restrict__ off,
+                              uint32_t n_off, const uint64_t* __restrict__ kw, uint64_t* __restrict__ alias) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const size_t per_warp = ((size_t)n_off * 12 + 15) & ~(size_t)15;  // 16-byte aligned regions
+    uint64_t* s = (uint64_t*)(smem + per_warp * w);
+    uint16_t* small_ = (uint16_t*)(s + n_off);
+    uint16_t* large_ = small_ + n_off;
+    for (uint32_t row = blockIdx.x * warps + w; row < n_rows; row += gridDim.x * warps) {
+        const uint32_t cell = cells[row];
+        const uint32_t cx = cell % W, cy = cell / W;
+        unsigned long long part = 0;
+        for (uint32_t o = lane; o < n_off; o += 32) {
+            const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+            const uint32_t tx = wrap_add(cx, dx, W), ty = wrap_add(cy, dy, H);
+            const uint64_t wgt = kw[dx * dx + dy * dy] * (uint64_t)deme[(size_t)ty * W + tx];
+            s[o] = (uint64_t)n_off * wgt;
+            part += wgt;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        __syncwarp();
+        if (lane == 0) {
+            const uint64_t Wt = part;
+            uint64_t* e = alias + (size_t)row * n_off;
+            uint32_t ns = 0, nl = 0;
+            for (uint32_t o = 0; o < n_off; ++o) {
+                if (s[o] < Wt) small_[ns++] = (uint16_t)o;
+                else large_[nl++] = (uint16_t)o;
+            }
+            while (ns > 0 && nl > 0) {
+                const uint32_t a = small_[--ns];
+                const uint32_t b = large_[--nl];
+                // q = floor(s_a 2^32 / W) by restoring division (s_a < W < 2^56)
+                uint64_t rem = s[a], q = 0;
+                for (int bit = 0; bit < 32; ++bit) {
+                    rem <<= 1;
+                    q <<= 1;
+                    if (rem >= Wt) {
+                        rem -= Wt;
+                        q |= 1ull;
+                    }
+                }
+                e[a] = q | ((uint64_t)b << 32);
+                s[b] = s[b] + s[a] - Wt;
+                if (s[b] < Wt) small_[ns++] = (uint16_t)b;
+                else large_[nl++] = (uint16_t)b;
+            }
+            while (nl > 0) {
+                const uint32_t b = large_[--nl];
+                e[b] = 0xFFFFFFFFull | ((uint64_t)b << 32) | (1ull << 63);
+            }
+            while (ns > 0) {
+                const uint32_t a = small_[--ns];
+                e[a] = 0xFFFFFFFFull | ((uint64_t)a << 32) | (1ull << 63);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_sample_flags(uint32_t* flags, uint64_t n_slots, int kind, uint32_t W, uint32_t D,
+                               uint32_t slot_deme, const uint8_t* deme, int all, uint32_t sk0, uint32_t sk1,
+                               uint64_t thr) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t cell = s / slot_deme;
+        const uint32_t i = (uint32_t)(s % slot_deme);
+        const uint32_t d = kind == KIND_MAP ? deme[cell] : D;
+        bool keep = i < d;
+        if (keep && !all) {
+            const uint64_t loc = pack_loc(cell % W, cell / W, i);
+            keep = (stream_block(sk0, sk1, loc, 0, 0, TAG_SAMPLE).lo >> 11) < thr;
+        }
+        flags[s] = keep ? 1u : 0u;
+    }
+}
+
+__global__ void k_sample_write(const uint32_t* flags, const uint32_t* pos, uint64_t n_slots, uint32_t W,
+                               uint32_t slot_deme, uint64_t* out) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        if (!flags[s]) continue;
+        const uint64_t cell = s / slot_deme;
+        out[pos[s]] = pack_loc(cell % W, cell / W, s % slot_deme);
+    }
+}
+
+// device arithmetic probes for the conformance tests
+__global__ void k_selftest(const uint64_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ exp_q58,
+                           uint32_t* __restrict__ philox_out) {
+    const LnC ln = ln_tables();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = in[i];
+        if (exp_q58) exp_q58[i] = exp1_q58(v >> 11, ln.L, ln.R, ln.ln2, ln.c3);
+        if (philox_out) {
+            const uint64_t w = in[(i + 1) % n], z = in[(i + 2) % n];
+            const u32x4 o = philox10((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)w, (uint32_t)(w >> 32),
+                                     (uint32_t)z, (uint32_t)(z >> 32));
+            philox_out[4 * i + 0] = o.x;
+            philox_out[4 * i + 1] = o.y;
+            philox_out[4 * i + 2] = o.z;
+            philox_out[4 * i + 3] = o.w;
+        }
+    }
+}
