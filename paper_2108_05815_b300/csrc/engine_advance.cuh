@@ -448,6 +448,8 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
                 warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
                 tprev = tn;
             }
+            if (!speciated && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP)))
+                prefetch_alias_row(B.P, c, loc, lane);
             if (speciated) {
                 if (lane == 0) {
                     B.key_loc[gid] = loc;

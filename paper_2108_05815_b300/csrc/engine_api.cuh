@@ -181,14 +181,11 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
         }
         uint32_t maxd = 0;
         m->n_slots = 0;
-        std::vector<uint32_t> cells, row_of(ncell, 0xFFFFFFFFu);
+        std::vector<uint32_t> cells;  // habitable cells: one alias row each
         for (size_t c = 0; c < ncell; ++c) {
             maxd = std::max<uint32_t>(maxd, dm[c]);
             m->n_slots += dm[c];
-            if (dm[c]) {
-                row_of[c] = (uint32_t)cells.size();
-                cells.push_back((uint32_t)c);
-            }
+            if (dm[c]) cells.push_back((uint32_t)c);
         }
         if (cells.empty()) return fail(IND_ERR_ARG);
         m->slot_deme = maxd;
@@ -201,17 +198,16 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
                     off.push_back((int8_t)dy);
                 }
         m->n_off = (uint32_t)(off.size() / 2);
+        if (m->n_off > ALIAS_MAX_OFFSETS) return fail(IND_ERR_ARG);
         m->n_rows = (uint32_t)cells.size();
         std::vector<uint64_t> kw = host_kernel_weights(D->sigma, R);
         m->d_deme = m->tables.get<uint8_t>(ncell);
-        m->d_row_of = m->tables.get<uint32_t>(ncell);
         m->d_off = m->tables.get<int8_t>(off.size());
         uint64_t* d_kw = m->tables.get<uint64_t>(kw.size());
         uint32_t* d_cells = m->tables.get<uint32_t>(cells.size());
-        m->d_alias = m->tables.get<uint64_t>((size_t)m->n_rows * m->n_off);
-        if (!m->d_deme || !m->d_row_of || !m->d_off || !d_kw || !d_cells || !m->d_alias) return fail(IND_ERR_OOM);
+        m->d_alias = m->tables.get<uint64_t>(ncell * m->n_off);  // rows by cell (HBM is plentiful)
+        if (!m->d_deme || !m->d_off || !d_kw || !d_cells || !m->d_alias) return fail(IND_ERR_OOM);
         bool okc = cudaMemcpyAsync(m->d_deme, dm.data(), ncell, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-                   cudaMemcpyAsync(m->d_row_of, row_of.data(), ncell * 4, cudaMemcpyHostToDevice, s) == cudaSuccess &&
                    cudaMemcpyAsync(m->d_off, off.data(), off.size(), cudaMemcpyHostToDevice, s) == cudaSuccess &&
                    cudaMemcpyAsync(d_kw, kw.data(), kw.size() * 8, cudaMemcpyHostToDevice, s) == cudaSuccess &&
                    cudaMemcpyAsync(d_cells, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -219,7 +215,7 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
             g_last_cuda_error.store((int)cudaGetLastError());
             return fail(IND_ERR_CUDA);
         }
-        const size_t per_warp = ((size_t)m->n_off * 12 + 15) & ~(size_t)15;
+        const size_t per_warp = ((size_t)m->n_off * 13 + 15) & ~(size_t)15;
         int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
         const size_t shb = per_warp * warps;
         if (cudaFuncSetAttribute(k_alias_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb) != cudaSuccess) {
@@ -439,7 +435,7 @@ size_t sim_mem_estimate(const ind_landscape* L, const ind_dispersal* D, double f
         for (int dy = -R; dy <= R; ++dy)
             for (int dx = -R; dx <= R; ++dx)
                 if (dx * dx + dy * dy <= R * R) ++n_off;
-        tables = ncell * (1 + 4 + 4 + n_off * 8) + 2 * n_off + 8 * (size_t)(R * R + 1);
+        tables = ncell * (1 + 4 + n_off * 8) + 2 * n_off + 8 * (size_t)(R * R + 1);
     } else {
         individuals = (double)ncell * L->deme;
         if (L->kind == IND_TORUS) tables = 16 * (size_t)host_gauss_half(D->sigma) + 4 * GUIDE_N;

@@ -31,7 +31,6 @@ struct ind_sim {
     uint32_t gauss_n = 0;
     int gauss_half = 0;
     uint8_t* d_deme = nullptr;
-    uint32_t* d_row_of = nullptr;
     uint64_t* d_alias = nullptr;
     int8_t* d_off = nullptr;
     uint32_t n_off = 0, n_rows = 0;
@@ -162,8 +161,6 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.pois_n = m->pois_n;
     p.pois_cdf = m->d_pois;
     p.pois_guide = m->d_pois_guide;
-    p.deme_map = m->d_deme;
-    p.row_of = m->d_row_of;
     p.alias = m->d_alias;
     p.off = m->d_off;
     p.n_off = m->n_off;

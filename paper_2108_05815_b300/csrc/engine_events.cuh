@@ -407,19 +407,34 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
         const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
         return pack_loc(tx, ty, ti);
     }
-    // habitat map: alias row of the origin cell
+    // habitat map: one load of the origin cell's alias entry, which also
+    // carries the target deme (k_alias_build), then the offset table (L1)
     const uint32_t n_off = __ldg(&p->n_off);
-    const uint32_t row = __ldg(p->row_of + (size_t)y * c.W + x);
     const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
-    const uint64_t e = __ldg(p->alias + (size_t)row * n_off + col);
+    const uint64_t e = __ldg(p->alias + ((size_t)y * c.W + x) * n_off + col);
     const uint32_t u = (uint32_t)d1;
-    const uint32_t o = ((e >> 63) != 0 || u < (uint32_t)e) ? col : (uint32_t)((e >> 32) & 0xFFFFu);
+    const bool take_col = (e >> 63) != 0 || u < (uint32_t)e;
+    const uint32_t o = take_col ? col : (uint32_t)((e >> 32) & (ALIAS_MAX_OFFSETS - 1u));
+    const uint32_t d = (uint32_t)(e >> (take_col ? 45 : 53)) & 0xFFu;
     const int8_t* off = p->off;
     const int32_t dx = off[2 * o], dy = off[2 * o + 1];
     const uint32_t tx = wrap_add(x, dx, c.W);
     const uint32_t ty = wrap_add(y, dy, c.H);
-    const uint32_t d = __ldg(p->deme_map + (size_t)ty * c.W + tx);
     return pack_loc(tx, ty, umulhi64(d2, d));
+}
+
+// A map lineage's next dispersal reads one entry of its cell's alias row.
+// Once the lineage has moved, the warp prefetches that row (n_off x 8 bytes,
+// two lines per lane for the 797 offsets of radius 16) into its SM's L1
+// while it searches for the next event, so that the dispersal's load does not
+// wait on HBM (L1 measured slightly faster than L2 here).  Every address lies
+// in the row.
+__device__ __forceinline__ void prefetch_alias_row(const SimParams* __restrict__ P, const LaneSim& c, uint64_t loc,
+                                                   uint32_t lane) {
+    const SimParams* p = P + c.sim;
+    const uint32_t bytes = __ldg(&p->n_off) * 8u;
+    const char* row = (const char*)(p->alias + ((size_t)loc_y(loc) * c.W + loc_x(loc)) * __ldg(&p->n_off));
+    for (uint32_t o = lane * 128u; o < bytes; o += 32u * 128u) asm volatile("prefetch.global.L1 [%0];" ::"l"(row + o));
 }
 
 // speciation threshold at loc: the metacommunity's in the spatially

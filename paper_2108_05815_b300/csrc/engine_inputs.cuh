@@ -16,16 +16,28 @@ __global__ void k_habitat(uint8_t* out, uint32_t W, uint32_t H, uint32_t sk0, ui
     }
 }
 
-// one warp per habitable cell: weights, then integer Vose on lane 0
+// one warp per habitable cell: weights, then integer Vose on lane 0.  Rows
+// are indexed by cell (those of cells without habitat are never read), and
+// an entry holds everything a dispersal needs besides the offset table:
+// threshold q (bits 0-31), alias column (32-44), the deme of the column's
+// own target (45-52) and of the alias column's target (53-60), and bit 63
+// for a column that is always taken
+__device__ __forceinline__ uint64_t alias_entry(uint64_t q, uint32_t col, uint32_t alias_col, uint8_t deme_col,
+                                                uint8_t deme_alias, bool full) {
+    return q | ((uint64_t)alias_col << 32) | ((uint64_t)deme_col << 45) | ((uint64_t)deme_alias << 53) |
+           (full ? (1ull << 63) : 0ull);
+}
+
 __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint32_t H,
                               const uint32_t* __restrict__ cells, uint32_t n_rows, const int8_t* __restrict__ off,
                               uint32_t n_off, const uint64_t* __restrict__ kw, uint64_t* __restrict__ alias) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const size_t per_warp = ((size_t)n_off * 12 + 15) & ~(size_t)15;  // 16-byte aligned regions
+    const size_t per_warp = ((size_t)n_off * 13 + 15) & ~(size_t)15;  // 16-byte aligned regions
     uint64_t* s = (uint64_t*)(smem + per_warp * w);
     uint16_t* small_ = (uint16_t*)(s + n_off);
     uint16_t* large_ = small_ + n_off;
+    uint8_t* tdeme = (uint8_t*)(large_ + n_off);  // deme of each offset's target
     for (uint32_t row = blockIdx.x * warps + w; row < n_rows; row += gridDim.x * warps) {
         const uint32_t cell = cells[row];
         const uint32_t cx = cell % W, cy = cell / W;
@@ -33,8 +45,10 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
         for (uint32_t o = lane; o < n_off; o += 32) {
             const int32_t dx = off[2 * o], dy = off[2 * o + 1];
             const uint32_t tx = wrap_add(cx, dx, W), ty = wrap_add(cy, dy, H);
-            const uint64_t wgt = kw[dx * dx + dy * dy] * (uint64_t)deme[(size_t)ty * W + tx];
+            const uint8_t td = deme[(size_t)ty * W + tx];
+            const uint64_t wgt = kw[dx * dx + dy * dy] * (uint64_t)td;
             s[o] = (uint64_t)n_off * wgt;
+            tdeme[o] = td;
             part += wgt;
         }
 #pragma unroll
@@ -42,7 +56,7 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
         __syncwarp();
         if (lane == 0) {
             const uint64_t Wt = part;
-            uint64_t* e = alias + (size_t)row * n_off;
+            uint64_t* e = alias + (size_t)cell * n_off;
             uint32_t ns = 0, nl = 0;
             for (uint32_t o = 0; o < n_off; ++o) {
                 if (s[o] < Wt) small_[ns++] = (uint16_t)o;
@@ -61,18 +75,18 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
                         q |= 1ull;
                     }
                 }
-                e[a] = q | ((uint64_t)b << 32);
+                e[a] = alias_entry(q, a, b, tdeme[a], tdeme[b], false);
                 s[b] = s[b] + s[a] - Wt;
                 if (s[b] < Wt) small_[ns++] = (uint16_t)b;
                 else large_[nl++] = (uint16_t)b;
             }
             while (nl > 0) {
                 const uint32_t b = large_[--nl];
-                e[b] = 0xFFFFFFFFull | ((uint64_t)b << 32) | (1ull << 63);
+                e[b] = alias_entry(0xFFFFFFFFull, b, b, tdeme[b], tdeme[b], true);
             }
             while (ns > 0) {
                 const uint32_t a = small_[--ns];
-                e[a] = 0xFFFFFFFFull | ((uint64_t)a << 32) | (1ull << 63);
+                e[a] = alias_entry(0xFFFFFFFFull, a, a, tdeme[a], tdeme[a], true);
             }
         }
         __syncwarp();

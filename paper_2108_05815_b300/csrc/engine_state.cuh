@@ -110,6 +110,10 @@ constexpr int GUIDE_BITS = 12;
 constexpr uint32_t GUIDE_N = 1u << GUIDE_BITS;
 constexpr uint32_t GUIDE_SCAN = 0x80000000u;
 
+// alias rows of a habitat map: entries name their alias column in 13 bits
+constexpr int ALIAS_COL_BITS = 13;
+constexpr uint32_t ALIAS_MAX_OFFSETS = 1u << ALIAS_COL_BITS;
+
 struct SimParams {
     int32_t kind;
     uint32_t W, H, D;          // D: individuals per cell (non-spatial: J)
@@ -126,9 +130,7 @@ struct SimParams {
     uint32_t pois_n;
     const uint64_t* pois_cdf;     // round(2^64 P(Poi(lambda dt) <= n))
     const uint32_t* pois_guide;   // GUIDE_N entries
-    const uint8_t* deme_map;   // W*H
-    const uint32_t* row_of;    // W*H alias row of a cell
-    const uint64_t* alias;     // rows x n_off entries: q | alias << 32 | full << 63
+    const uint64_t* alias;     // W*H rows (by cell) x n_off entries (format: k_alias_build)
     const int8_t* off;         // n_off (dx, dy)
     uint32_t n_off;
     uint32_t n_lineages;
