@@ -42,8 +42,8 @@ INT32_LANES_PER_SM = 128  # Blackwell: 128 INT32-capable lanes per SM per clock
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum \
 #       --clock-control none -k regex:k_advance -c 200 --csv \
 #       python -m paper_2108_05815_b300.cases config2
-# (21.5 MB over 48 rounds).  Not measured for the Poisson sampler.
-TRAFFIC_PER_ROUND = {"exp": 448e3}
+# (18.5 MB over the 26 rounds).  Not measured for the Poisson sampler.
+TRAFFIC_PER_ROUND = {"exp": 712e3}
 
 
 def parse():
