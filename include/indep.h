@@ -199,9 +199,10 @@ typedef struct {
     double occupancy_step;         /* alpha: duplicate work per round stays near alpha / 2 */
     double tail_events;            /* lower bound of lambda x horizon step below busy_lineages */
     double busy_lineages;          /* active lineages that fill the GPU */
-    double max_step_events;        /* upper bound of lambda x horizon step: no round waits long on
-                                      one simulation's few lineages (all resident simulations share
-                                      each round) */
+    double max_step_events;        /* upper bound of lambda x horizon step while several
+                                      simulations share the rounds (no round waits long on one
+                                      simulation's few lineages); a simulation alone in its batch
+                                      is bounded 16 times higher */
 } ind_tuning;
 
 typedef struct {

@@ -493,11 +493,18 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
 }
 
 // horizon step (time) of a simulation with n active lineages
-__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n) {
+// horizon step (time) of a simulation with n active lineages while `live`
+// simulations share the rounds: max_step_events bounds it so that no round
+// waits long on one simulation; a simulation alone is bounded 16 times
+// higher (fewer rounds, nothing else waits)
+constexpr double ALONE_STEP_FACTOR = 16.0;
+
+__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n, uint32_t live) {
     const double dn = (double)n;
     const double floor_ev = dn < p->busy_lineages ? p->tail_events : p->min_events;
     const double per = fmax(floor_ev, fmin(p->occupancy_step * p->n_slots / dn, p->events_per_round / dn));
-    return fmin(per, p->max_step_events) / p->lambda;
+    const double cap = live > 1u ? p->max_step_events : p->max_step_events * ALONE_STEP_FACTOR;
+    return fmin(per, cap) / p->lambda;
 }
 
 __global__ void k_compact(BatchDev B) {
@@ -604,7 +611,11 @@ __global__ void k_compact(BatchDev B) {
             continue;
         }
         atomicAdd(&live, 1u);
-        st->horizon = st->horizon + horizon_step(B.P + s, na);
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
+        SimState* st = B.S + s;
+        if (!st->done) st->horizon = st->horizon + horizon_step(B.P + s, st->n_active, live);
     }
     __syncthreads();
     if (B.G->prof_events) {
@@ -643,13 +654,19 @@ __global__ void k_compact(BatchDev B) {
 
 // initial horizons and counters of a fresh batch
 __global__ void k_start(BatchDev B, uint32_t n_lin) {
+    __shared__ uint32_t live;
+    if (threadIdx.x == 0) live = 0;
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x)
+        if (B.P[s].n_lineages) atomicAdd(&live, 1u);
+    __syncthreads();
     for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
         const SimParams* p = B.P + s;
         SimState* st = B.S + s;
         const uint32_t na = p->n_lineages;
         st->n_active = na;
         st->done = na == 0 ? 1u : 0u;
-        st->horizon = horizon_step(p, max(na, 1u));
+        st->horizon = horizon_step(p, max(na, 1u), live);
     }
     if (threadIdx.x == 0) {
         Globals* G = B.G;

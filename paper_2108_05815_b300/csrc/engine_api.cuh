@@ -51,7 +51,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->occupancy_step = 0.25;
     t->tail_events = 128.0;
     t->busy_lineages = 32768.0;
-    t->max_step_events = 16384.0;
+    t->max_step_events = 1024.0;
 }
 
 static bool tuning_ok(const ind_tuning* t) {
