@@ -114,11 +114,14 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
         for (uint32_t visit = 0; has && visit < B.events_per_visit; ++visit) {
             // both non-negative: compare the bit patterns (an integer compare)
             if ((uint64_t)__double_as_longlong(tn) > (uint64_t)__double_as_longlong(c.horizon)) {
-                // at the horizon: write back and enter the dedup
-                L.loc[idx] = loc;
-                L.tn[idx] = tn;
-                if (LOG) L.tp[idx] = tprev;
-                if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                // at the horizon: a lineage that moved this round writes its
+                // state back and enters the dedup (see k_compact)
+                if (ev_lin) {
+                    L.loc[idx] = loc;
+                    L.tn[idx] = tn;
+                    if (LOG) L.tp[idx] = tprev;
+                    if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                }
                 has = false;
             } else {
                 ++ev_raw;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
                     }
                     ev_lin = 0;
                     if ((uint64_t)__double_as_longlong(tn) > hz) {
-                        if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);  // already at the horizon
+                        // already at the horizon: nothing to write, no dedup entry (see k_compact)
                     } else {
                         st = SM_EVENT0;
                     }
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
         uint32_t ev_lin = 0;
         for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
             if ((uint64_t)__double_as_longlong(tn) > hz) {
-                if (lane == 0) {
+                if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
                     L.loc[idx] = loc;
                     L.tn[idx] = tn;
                     if (LOG) L.tp[idx] = tprev;
@@ -507,6 +510,14 @@ __device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n, u
     return fmin(per, cap) / p->lambda;
 }
 
+// Dedup at the horizon.  Lineages that moved this round entered the round's
+// table (the least lineage id of a slot wins); every active lineage looks
+// its slot up.  Two lineages in one slot at a horizon are exact duplicates
+// (both next events are the slot's first point after the horizon), so one
+// that finds another winner is culled.  A lineage that did not move made no
+// entry: it is culled if a mover entered its slot, and otherwise keeps its
+// place; it has no other duplicate, because duplicates are culled in the
+// round they meet.
 __global__ void k_compact(BatchDev B) {
     const uint32_t t = B.G->round & 1u;
     const LinPtrs in = B.lin[t];
