@@ -34,14 +34,37 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
     }
 }
 
+// The round's work list: the lineages whose next event lies before their
+// simulation's horizon (warp-aggregated appends).  The others have nothing
+// to do in the round: no event, no state to write, no dedup entry.
+__global__ void k_filter(BatchDev B) {
+    const uint32_t n = B.G->n_total;
+    const LinPtrs L = B.lin[B.G->round & 1u];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t stride = gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        const uint32_t i = base + lane;
+        bool due = false;
+        if (i < n) {
+            const double h = B.S[L.sim[i]].horizon;
+            due = (uint64_t)__double_as_longlong(L.tn[i]) <= (uint64_t)__double_as_longlong(h);
+        }
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, due);
+        uint32_t p0 = 0;
+        if (lane == 0 && m) p0 = atomicAdd(&B.G->n_work, (uint32_t)__popc(m));
+        p0 = __shfl_sync(0xFFFFFFFFu, p0, 0);
+        if (due) B.work[p0 + __popc(m & ((1u << lane) - 1u))] = i;
+    }
+}
+
 // LOG: append every executed event to the event log
 template <bool COUNT, int WIDE, bool LOG>
 __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
-    const uint32_t n = B.G->n_total;
-    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
+    if (B.G->n_total <= B.coop_lineages) return;  // a round for k_advance_coop
+    const uint32_t n = B.G->n_work;              // lineages with an event before the horizon (k_filter)
     const uint32_t chunk = 32u * B.lpl;
-    // a block whose first possible claim lies beyond the active lineages has
+    // a block whose first possible claim lies beyond the work list has
     // nothing to do (claims go out in order of arrival, at most one per warp)
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
     // the logarithm tables are staged only if some simulation sums exponentials
@@ -83,7 +106,7 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                 const uint32_t avail = chunk_end - chunk_next;
                 const uint32_t rank = __popc(need & lt_mask);
                 if (!has && rank < avail) {
-                    idx = chunk_next + rank;
+                    idx = B.work[chunk_next + rank];
                     gid = L.gid[idx];
                     loc = L.loc[idx];
                     tn = L.tn[idx];
@@ -177,8 +200,8 @@ constexpr uint32_t SM_IDLE = 0, SM_EVENT0 = 1, SM_EVENT1 = 2, SM_SEARCH = 3;
 template <bool COUNT>
 __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
-    const uint32_t n = B.G->n_total;
-    if (n <= B.coop_lineages) return;  // a round for k_advance_coop
+    if (B.G->n_total <= B.coop_lineages) return;  // a round for k_advance_coop
+    const uint32_t n = B.G->n_work;              // lineages with an event before the horizon (k_filter)
     const uint32_t chunk = 32u * B.lpl;
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
@@ -261,7 +284,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
                 const uint32_t avail = chunk_end - chunk_next;
                 const uint32_t rank = __popc(need & lt_mask);
                 if (st == SM_IDLE && rank < avail) {
-                    idx = chunk_next + rank;
+                    idx = B.work[chunk_next + rank];
                     gid = L.gid[idx];
                     loc = L.loc[idx];
                     tn = L.tn[idx];
@@ -397,8 +420,8 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 template <bool COUNT, int MODE, int KIND, bool LOG = false>
 __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
-    const uint32_t n = B.G->n_total;
-    if (n > B.coop_lineages) return;  // a round for the one-lane form
+    if (B.G->n_total > B.coop_lineages) return;  // a round for the one-lane form
+    const uint32_t n = B.G->n_work;             // lineages with an event before the horizon (k_filter)
     if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
     const uint32_t t = B.G->round & 1u;
@@ -410,10 +433,11 @@ __global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
     WarpLogBuf wlog;
     wlog.n = 0;
     for (;;) {
-        uint32_t idx = 0;
-        if (lane == 0) idx = atomicAdd(&B.G->work_ctr, 1u);
-        idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
-        if (idx >= n) break;
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(&B.G->work_ctr, 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= n) break;
+        const uint32_t idx = B.work[k];
         const uint32_t gid = L.gid[idx];
         uint64_t loc = L.loc[idx];
         double tn = L.tn[idx];
@@ -649,6 +673,7 @@ __global__ void k_compact(BatchDev B) {
         G->n_total = nt;
         G->n_total_next = 0;
         G->work_ctr = 0;
+        G->n_work = 0;
         G->blocks_done = 0;
         G->used[tp] = 0;
         G->ev_used[tp] = 0;

@@ -447,7 +447,8 @@ size_t sim_mem_estimate(const ind_landscape* L, const ind_dispersal* D, double f
     const double slots = (L->kind == IND_MAP ? (double)ncell * 255.0 : individuals);
     // per lineage: 2 x 24 (buffers) + 20 (parent, keys) + 24 (outputs) + 8 (sample)
     // + 2 x 4 x 12 (dedup tables of twice the size) + 8 (used lists) + 32 x 2 (species sort)
-    const double per = 48 + 20 + 24 + 8 + 96 + 8 + 64 + 16;
+    // + 4 (work list)
+    const double per = 48 + 20 + 24 + 8 + 96 + 8 + 64 + 16 + 4;
     const double bytes = tables + std::max(sampled * per, slots * 8.0) + (1 << 20);
     return (size_t)bytes;
 }

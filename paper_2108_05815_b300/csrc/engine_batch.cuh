@@ -254,6 +254,7 @@ static ind_status batch_build(Batch& b) {
         d.lin[t].sim = P.get<uint32_t>(n);
     }
     d.parent = P.get<uint32_t>(n);
+    d.work = P.get<uint32_t>(n);
     d.key_loc = P.get<uint64_t>(n);
     d.key_time = P.get<uint64_t>(n);
     uint32_t cap = 2;
@@ -300,7 +301,7 @@ static ind_status batch_build(Batch& b) {
         if (!d.lin[t].loc || !d.lin[t].tn || !d.lin[t].gid || !d.lin[t].sim || !d.ht_key[t] || !d.ht_val[t] ||
             !d.ht_used[t] || (d.count_unique && (!d.ev[t] || !d.ev_used[t])))
             return IND_ERR_OOM;
-    if (!b.d_params || !b.d_state || !b.d_g || !b.d_gid_base || !d.parent || !d.key_loc || !d.key_time)
+    if (!b.d_params || !b.d_state || !b.d_g || !b.d_gid_base || !d.parent || !d.work || !d.key_loc || !d.key_time)
         return IND_ERR_OOM;
     d.P = b.d_params;
     d.S = b.d_state;
@@ -381,13 +382,15 @@ static ind_status batch_build(Batch& b) {
     return IND_OK;
 }
 
-constexpr uint64_t LAUNCHES_PER_ROUND = 3;  // one-lane advance, warp-per-lineage advance, compaction
+constexpr uint64_t LAUNCHES_PER_ROUND = 4;  // work-list filter, one-lane and warp-per-lineage advance, compaction
 
 static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     cudaStream_t s = capturing ? b.cap_stream : b.stream;
     const bool prof = b.tun.profile && r < b.ev_start.size();
     const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (prof) CK(cudaEventRecordWithFlags(b.ev_start[r], s, flag));
+    k_filter<<<b.cmp_blocks, 256, 0, s>>>(b.dev);
+    CK(cudaGetLastError());
     // shared memory only when some simulation sums exponentials (leaves L1 larger otherwise)
     const size_t smem = b.dev.need_ln ? LN_SMEM_BYTES : 0;
     const bool conv = b.tun.advance_variant == 0;  // convergent state machine or one-lane loop

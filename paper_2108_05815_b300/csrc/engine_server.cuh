@@ -320,6 +320,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
         ok = d.lin[t].loc && d.lin[t].tn && d.lin[t].gid && d.lin[t].sim;
     }
     d.parent = P.get<uint32_t>(n);
+    d.work = P.get<uint32_t>(n);
     d.key_loc = P.get<uint64_t>(n);
     d.key_time = P.get<uint64_t>(n);
     uint32_t cap = 2;
@@ -331,7 +332,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
         d.ht_used[t] = P.get<uint32_t>(n);
         ok = d.ht_key[t] && d.ht_val[t] && d.ht_used[t];
     }
-    ok = ok && d.parent && d.key_loc && d.key_time;
+    ok = ok && d.parent && d.work && d.key_loc && d.key_time;
     if (!ok) {
         delete sv;
         return IND_ERR_OOM;

@@ -168,6 +168,7 @@ struct Globals {
     uint32_t n_total;       // lineages in the current input buffer
     uint32_t n_total_next;  // survivors written by the running compaction
     uint32_t work_ctr;      // claim counter of the advance kernel
+    uint32_t n_work;        // entries of the round's work list (k_filter)
     uint32_t blocks_done;   // finished blocks of the running compaction
     uint32_t round;         // rounds completed (parity selects buffers)
     uint32_t mask[2];       // probe mask of the dedup tables
@@ -208,6 +209,7 @@ struct EventLog {
 
 struct BatchDev {
     LinPtrs lin[2];
+    uint32_t* work;  // the round's work list: buffer indices of lineages with an event before the horizon
     uint32_t* parent;
     uint64_t* key_loc;
     uint64_t* key_time;
