@@ -181,44 +181,47 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.n_slots = (double)m->n_slots;
 }
 
-template <bool COUNT, int MODE, int KIND>
+template <bool COUNT, int MODE, int KIND, bool LOG>
 static cudaError_t set_smem_one() {
-    return cudaFuncSetAttribute(k_advance_coop<COUNT, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_advance_coop<COUNT, MODE, KIND, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)LN_SMEM_BYTES);
 }
 
 // the instantiations launch_coop uses: with counting (measurement runs) only
 // the generic kind
-template <bool COUNT>
+template <bool COUNT, bool LOG>
 static cudaError_t set_coop_smem() {
     cudaError_t e;
-    if ((e = set_smem_one<COUNT, 0, -1>()) || (e = set_smem_one<COUNT, 1, -1>()) ||
-        (e = set_smem_one<COUNT, 2, -1>()))
+    if ((e = set_smem_one<COUNT, 0, -1, LOG>()) || (e = set_smem_one<COUNT, 1, -1, LOG>()) ||
+        (e = set_smem_one<COUNT, 2, -1, LOG>()))
         return e;
     if (!COUNT) {
-        if ((e = set_smem_one<COUNT, 1, 0>()) || (e = set_smem_one<COUNT, 1, 1>()) ||
-            (e = set_smem_one<COUNT, 1, 2>()) || (e = set_smem_one<COUNT, 2, 0>()) ||
-            (e = set_smem_one<COUNT, 2, 1>()) || (e = set_smem_one<COUNT, 2, 2>()))
+        if ((e = set_smem_one<COUNT, 1, 0, LOG>()) || (e = set_smem_one<COUNT, 1, 1, LOG>()) ||
+            (e = set_smem_one<COUNT, 1, 2, LOG>()) || (e = set_smem_one<COUNT, 2, 0, LOG>()) ||
+            (e = set_smem_one<COUNT, 2, 1, LOG>()) || (e = set_smem_one<COUNT, 2, 2, LOG>()))
             return e;
     }
     return cudaSuccess;
 }
 
-template <bool COUNT, int MODE>
+template <bool COUNT, int MODE, bool LOG>
 static void launch_coop_kind(const Batch& b, size_t smem, cudaStream_t s) {
     const dim3 g(b.adv_blocks), t(b.adv_threads);
     if (COUNT || b.coop_kind < 0 || b.coop_kind > KIND_MAP)  // counting runs and mixed or implicit batches
-        k_advance_coop<COUNT, MODE, -1><<<g, t, smem, s>>>(b.dev);
-    else if (b.coop_kind == KIND_NONSPATIAL) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 0)><<<g, t, smem, s>>>(b.dev);
-    else if (b.coop_kind == KIND_TORUS) k_advance_coop<COUNT, MODE, (COUNT ? -1 : 1)><<<g, t, smem, s>>>(b.dev);
-    else k_advance_coop<COUNT, MODE, (COUNT ? -1 : 2)><<<g, t, smem, s>>>(b.dev);
+        k_advance_coop<COUNT, MODE, -1, LOG><<<g, t, smem, s>>>(b.dev);
+    else if (b.coop_kind == KIND_NONSPATIAL)
+        k_advance_coop<COUNT, MODE, (COUNT ? -1 : 0), LOG><<<g, t, smem, s>>>(b.dev);
+    else if (b.coop_kind == KIND_TORUS)
+        k_advance_coop<COUNT, MODE, (COUNT ? -1 : 1), LOG><<<g, t, smem, s>>>(b.dev);
+    else
+        k_advance_coop<COUNT, MODE, (COUNT ? -1 : 2), LOG><<<g, t, smem, s>>>(b.dev);
 }
 
-template <bool COUNT>
+template <bool COUNT, bool LOG>
 static void launch_coop(const Batch& b, size_t smem, cudaStream_t s) {
-    if (b.coop_mode == 1) launch_coop_kind<COUNT, 1>(b, smem, s);
-    else if (b.coop_mode == 2) launch_coop_kind<COUNT, 2>(b, smem, s);
-    else k_advance_coop<COUNT, 0, -1><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+    if (b.coop_mode == 1) launch_coop_kind<COUNT, 1, LOG>(b, smem, s);
+    else if (b.coop_mode == 2) launch_coop_kind<COUNT, 2, LOG>(b, smem, s);
+    else k_advance_coop<COUNT, 0, -1, LOG><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
 }
 
 static ind_status batch_build(Batch& b) {
@@ -359,13 +362,11 @@ static ind_status batch_build(Batch& b) {
                                 (int)LN_SMEM_BYTES));
         CK(cudaFuncSetAttribute(k_advance<false, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)LN_SMEM_BYTES));
-        CK(cudaFuncSetAttribute(k_advance_coop<true, 0, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)LN_SMEM_BYTES));
-        CK(cudaFuncSetAttribute(k_advance_coop<false, 0, -1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)LN_SMEM_BYTES));
+        CK((set_coop_smem<true, true>()));
+        CK((set_coop_smem<false, true>()));
     }
-    CK(set_coop_smem<true>());
-    CK(set_coop_smem<false>());
+    CK((set_coop_smem<true, false>()));
+    CK((set_coop_smem<false, false>()));
     CK(cudaFuncSetAttribute(k_advance_sm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     CK(cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
@@ -398,28 +399,29 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     // returns at once unless the round is its own (more than coop_lineages
     // lineages: one lane per lineage; else one warp per lineage), so that the
     // choice is made per round inside captured chunks.  An event log takes
-    // the logging forms (one-lane loop, generic warp form).
+    // the logging forms (one-lane loop; the warp form as specialised as
+    // without a log).
     const dim3 ag(b.adv_blocks), at(b.adv_threads);
     if (b.dev.log.cap) {
         if (b.dev.count_unique) {
             k_advance<true, 1, true><<<ag, at, smem, s>>>(b.dev);
             CK(cudaGetLastError());
-            k_advance_coop<true, 0, -1, true><<<ag, at, smem, s>>>(b.dev);
+            launch_coop<true, true>(b, smem, s);
         } else {
             k_advance<false, 1, true><<<ag, at, smem, s>>>(b.dev);
             CK(cudaGetLastError());
-            k_advance_coop<false, 0, -1, true><<<ag, at, smem, s>>>(b.dev);
+            launch_coop<false, true>(b, smem, s);
         }
     } else if (b.dev.count_unique) {
         if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<true, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
-        launch_coop<true>(b, smem, s);
+        launch_coop<true, false>(b, smem, s);
     } else {
         if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<false, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
-        launch_coop<false>(b, smem, s);
+        launch_coop<false, false>(b, smem, s);
     }
     CK(cudaGetLastError());
     if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));
@@ -618,18 +620,56 @@ static ind_status process_event_log(Batch& b) {
     if (n_log > b.dev.log.cap) return IND_ERR_DEVICE;
     const uint32_t n = (uint32_t)n_log;
     if (n) {
-        uint32_t np = 2048;
-        while (np < n) np <<= 1;
-        SortItem* items = T.get<SortItem>(np);
+        // the log's order by stable radix passes, least significant field
+        // first (lineage, prior time, location, time); bytes that are equal
+        // in every entry are skipped
+        const uint32_t nb = (n + RS_TILE - 1) / RS_TILE;
+        uint64_t* key0 = T.get<uint64_t>(n);
+        uint64_t* key1 = T.get<uint64_t>(n);
+        uint32_t* val0 = T.get<uint32_t>(n);
+        uint32_t* val1 = T.get<uint32_t>(n);
+        uint32_t* counts = T.get<uint32_t>((size_t)RS_RADIX * nb);
+        uint32_t* offs = T.get<uint32_t>((size_t)RS_RADIX * nb);
+        unsigned long long* d_bits = T.get<unsigned long long>(8);
+        SortItem* items = T.get<SortItem>(n);
         uint32_t* head = T.get<uint32_t>(n);
         uint32_t* coal = T.get<uint32_t>(n);
         uint32_t* incl_head = T.get<uint32_t>(n);
         uint32_t* incl_coal = T.get<uint32_t>(n);
-        if (!items || !head || !coal || !incl_head || !incl_coal) return IND_ERR_OOM;
-        k_ev_items<<<grid_for(np, 256, sms * 16), 256, 0, s>>>(b.dev.log, n, np, items);
+        if (!key0 || !key1 || !val0 || !val1 || !counts || !offs || !d_bits || !items || !head || !coal ||
+            !incl_head || !incl_coal)
+            return IND_ERR_OOM;
+        unsigned long long h_bits[8];
+        for (int f = 0; f < 4; ++f) {
+            h_bits[2 * f] = ~0ull;
+            h_bits[2 * f + 1] = 0ull;
+        }
+        CK(cudaMemcpyAsync(d_bits, h_bits, sizeof(h_bits), cudaMemcpyHostToDevice, s));
+        k_ev_bits<<<grid_for(n, 256, sms * 8), 256, 0, s>>>(b.dev.log, n, d_bits);
         CKL();
-        ind_status st = bitonic_sort(items, np, s);
-        if (st != IND_OK) return st;
+        CK(cudaMemcpyAsync(h_bits, d_bits, sizeof(h_bits), cudaMemcpyDeviceToHost, s));
+        k_iota<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(val0, n);
+        CKL();
+        CK(cudaStreamSynchronize(s));
+        ind_status st = IND_OK;
+        for (int f = 0; f < 4; ++f) {
+            const uint64_t varies = h_bits[2 * f] ^ h_bits[2 * f + 1];
+            if (!varies) continue;
+            k_ev_field<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, f, val0, n, key0);
+            CKL();
+            for (int shift = 0; shift < 64; shift += 8) {
+                if (!((varies >> shift) & 0xFFull)) continue;
+                k_rs_count<<<nb, RS_WARPS * 32, 0, s>>>(key0, n, shift, counts);
+                CKL();
+                if ((st = scan_u32(T, counts, offs, RS_RADIX * nb, false, s)) != IND_OK) return st;
+                k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(key0, val0, n, shift, offs, key1, val1);
+                CKL();
+                std::swap(key0, key1);
+                std::swap(val0, val1);
+            }
+        }
+        k_ev_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, val0, n, items);
+        CKL();
         k_ev_marks<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, head, coal);
         CKL();
         if ((st = scan_u32(T, head, incl_head, n, true, s)) != IND_OK) return st;

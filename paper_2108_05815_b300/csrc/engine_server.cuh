@@ -371,7 +371,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
     if ((e = cudaFuncSetAttribute(k_advance<false, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)) ||
-        (e = set_coop_smem<false>()) ||
+        (e = (set_coop_smem<false, false>())) ||
         (e = cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES)))
         return fail(e);
     b.adv_threads = b.tun.block_threads;

@@ -194,10 +194,120 @@ __global__ void k_scan_add(uint32_t* out, const uint32_t* sums_excl, uint32_t n)
 // lineage that was at the location longest, and every later distinct prior
 // time is a lineage that dispersed there at that time: a coalescence
 // ---------------------------------------------------------------------------
-__global__ void k_ev_items(EventLog L, uint32_t n, uint32_t n_pad, SortItem* items) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
-        items[i] = i < n ? SortItem{L.time[i], L.loc[i], L.prior[i], ((unsigned long long)L.gid[i] << 32) | i}
-                         : SortItem{~0ull, ~0ull, ~0ull, ~0ull};
+// Stable least-significant-digit radix sort of (u64 key, u32 value) pairs:
+// 8-bit digits, tiles of 4,096 items per block of 8 warps.  Per pass:
+// per-block digit counts, one exclusive scan (digit-major, so that block b's
+// items of digit d follow those of blocks before b), and a scatter in which
+// every warp handles a contiguous sub-tile in order, ranking equal digits of
+// each 32-item chunk with __match_any_sync: ties keep their input order.
+constexpr int RS_RADIX = 256;
+constexpr int RS_WARPS = 8;
+constexpr int RS_ITEMS = 16;                           // per lane
+constexpr uint32_t RS_SUB = 32u * RS_ITEMS;            // items per warp
+constexpr uint32_t RS_TILE = RS_WARPS * RS_SUB;        // items per block
+
+__global__ void __launch_bounds__(RS_WARPS * 32) k_rs_count(const uint64_t* __restrict__ keys, uint32_t n, int shift,
+                                                             uint32_t* __restrict__ counts) {
+    __shared__ uint32_t h[RS_RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t start = blockIdx.x * RS_TILE, end = min(start + RS_TILE, n);
+    for (uint32_t i = start + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (RS_RADIX - 1)], 1u);
+    __syncthreads();
+    counts[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_WARPS * 32) k_rs_scatter(const uint64_t* __restrict__ keys_in,
+                                                               const uint32_t* __restrict__ vals_in, uint32_t n,
+                                                               int shift, const uint32_t* __restrict__ offsets,
+                                                               uint64_t* __restrict__ keys_out,
+                                                               uint32_t* __restrict__ vals_out) {
+    __shared__ uint32_t wbase[RS_WARPS][RS_RADIX];  // per-warp digit counts, then starting positions
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    for (uint32_t k = threadIdx.x; k < RS_WARPS * RS_RADIX; k += blockDim.x) (&wbase[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t sub = blockIdx.x * RS_TILE + w * RS_SUB;
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const uint32_t i = sub + (uint32_t)j * 32u + lane;
+        if (i < n) atomicAdd(&wbase[w][(uint32_t)(keys_in[i] >> shift) & (RS_RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    {   // thread d: the block's offset of digit d, handed out to the warps in order
+        const uint32_t d = threadIdx.x;
+        uint32_t run = offsets[d * gridDim.x + blockIdx.x];
+        for (int v = 0; v < RS_WARPS; ++v) {
+            const uint32_t c = wbase[v][d];
+            wbase[v][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int j = 0; j < RS_ITEMS; ++j) {
+        const uint32_t i = sub + (uint32_t)j * 32u + lane;
+        const bool valid = i < n;
+        const uint64_t key = valid ? keys_in[i] : 0ull;
+        const uint32_t d = valid ? ((uint32_t)(key >> shift) & (RS_RADIX - 1)) : (RS_RADIX + lane);  // unique when invalid
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (valid) {
+            const uint32_t pos = wbase[w][d] + __popc(peers & lt);
+            keys_out[pos] = key;
+            vals_out[pos] = vals_in[i];
+        }
+        __syncwarp();
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) wbase[w][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+}
+
+// sort key of one field of the log entries, in the current order
+// (field 0: lineage, 1: prior time, 2: location, 3: time)
+__device__ __forceinline__ uint64_t ev_field(const EventLog& L, int f, uint32_t k) {
+    return f == 0 ? (uint64_t)L.gid[k] : f == 1 ? L.prior[k] : f == 2 ? L.loc[k] : L.time[k];
+}
+
+__global__ void k_ev_field(EventLog L, int f, const uint32_t* __restrict__ order, uint32_t n, uint64_t* keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        keys[i] = ev_field(L, f, order ? order[i] : i);
+}
+
+__global__ void k_iota(uint32_t* v, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
+// AND and OR of every field over the log: a byte that is the same in every
+// entry needs no radix pass
+__global__ void k_ev_bits(EventLog L, uint32_t n, unsigned long long* and_or /* 4 fields x (and, or) */) {
+    uint64_t a[4], o[4];
+    for (int f = 0; f < 4; ++f) {
+        a[f] = ~0ull;
+        o[f] = 0ull;
+    }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int f = 0; f < 4; ++f) {
+            const uint64_t v = ev_field(L, f, i);
+            a[f] &= v;
+            o[f] |= v;
+        }
+    for (int f = 0; f < 4; ++f) {
+        for (int d = 16; d > 0; d >>= 1) {
+            a[f] &= __shfl_xor_sync(0xFFFFFFFFu, a[f], d);
+            o[f] |= __shfl_xor_sync(0xFFFFFFFFu, o[f], d);
+        }
+        if ((threadIdx.x & 31u) == 0) {
+            atomicAnd(&and_or[2 * f], (unsigned long long)a[f]);
+            atomicOr(&and_or[2 * f + 1], (unsigned long long)o[f]);
+        }
+    }
+}
+
+// the log in (time, location, prior time, lineage) order as sort items
+__global__ void k_ev_gather(EventLog L, const uint32_t* __restrict__ order, uint32_t n, SortItem* items) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t k = order[i];
+        items[i] = SortItem{L.time[k], L.loc[k], L.prior[k], ((unsigned long long)L.gid[k] << 32) | k};
+    }
 }
 
 __global__ void k_ev_marks(const SortItem* __restrict__ x, uint32_t n, uint32_t* head, uint32_t* coal) {
