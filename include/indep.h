@@ -360,6 +360,22 @@ ind_status ind_habitat(uint64_t map_seed, uint32_t width, uint32_t height, doubl
 ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, uint32_t* philox_out,
                         void* cuda_stream);
 
+/* Conformance probe of the event-time searches (no counterpart in the
+ * paper; used by the tests).  For each i, out[i] receives the first point
+ * strictly after tau[i] of the event process at location loc[i] of
+ * simulation m (its seed, sampler, lambda and delta_t; sections "Memoryless
+ * sums of exponentials" and "Homogeneous Poisson Point Process" under
+ * "Exponential inter-event Times"), computed by search form `form`: 0 and 1 the
+ * one-lane searches (one or two draw blocks per step), 2 the warp-
+ * cooperative general search, 3 the short warp search in binary64, 4 the
+ * short warp search as the tail kernel runs it (integer sums for lambda =
+ * 1).  Every form returns the same value; a negative value reports a search
+ * beyond the interval limits (IND_ERR_DEVICE in a run).  tau[i] >= 0
+ * finite; loc[i] any packed location.  Pointers host or device, owned by
+ * the caller; 1 <= n <= 2^26; runs on m's stream and returns after it. */
+ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const double* tau, uint64_t n,
+                               double* out);
+
 /* Species ranking that allocates nothing (the paper has no counterpart: it
  * exists for callers that must not allocate device memory while they run,
  * e.g. a process that plans all of its device memory at start-up, or code

@@ -105,6 +105,8 @@ EXPORTS = {
                                    ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "ind_selftest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    "sim_selftest_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_uint64, ctypes.c_void_p]),
     "ind_species_rank_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "srv_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
@@ -301,6 +303,18 @@ class Simulation:
         _check(lib().sim_events(self._h, ctypes.c_void_p(ev.ctypes.data), ne.value, None,
                                 ctypes.c_void_p(co.ctypes.data), nc.value, None), "sim_events")
         return ev, co
+
+    def selftest_search(self, form, locs, taus):
+        """device probe (sim_selftest_search): the first event time after each
+        taus[i] at locs[i] by search form 0..4, float64 numpy array"""
+        lv = np.ascontiguousarray(locs, dtype=np.uint64)
+        tv = np.ascontiguousarray(taus, dtype=np.float64)
+        assert lv.shape == tv.shape
+        out = np.zeros(lv.size, dtype=np.float64)
+        _check(lib().sim_selftest_search(self._h, int(form), ctypes.c_void_p(lv.ctypes.data),
+                                         ctypes.c_void_p(tv.ctypes.data), lv.size, ctypes.c_void_p(out.ctypes.data)),
+               "sim_selftest_search")
+        return out
 
     def species_keys(self):
         """(speciation location, time bits) per sampled individual, uint64 numpy arrays"""

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 // shared by every simulation, or -1.  The specialised kernels are smaller,
 // which matters where one warp runs alone and waits on instruction fetch.
 template <bool COUNT, int MODE, int KIND, bool LOG = false>
-__global__ void __launch_bounds__(512) k_advance_coop(BatchDev B) {
+__global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     if (B.G->n_total > B.coop_lineages) return;  // a round for the one-lane form
     const uint32_t n = B.G->n_work;             // lineages with an event before the horizon (k_filter)

@@ -326,7 +326,7 @@ __device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double
 // the spec's order on the shuffled draws; intervals k + 1 .. k + 3 only need
 // their first point
 template <bool LAM1>
-__device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+__device__ double coop_next_exp_short_fp(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     const uint32_t m = lane >> 3, i = lane & 7u;
     uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
@@ -364,6 +364,103 @@ __device__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau
         if (bal) return __shfl_sync(0xFFFFFFFFu, first, __ffs(bal) - 1);
     }
     return -1.0;
+}
+
+// q 2^-58 rounded to binary64 (53 significant bits, nearest, ties to even),
+// as the multiple of 2^-58 it equals (q < 2^63.5, so no overflow)
+__device__ __forceinline__ uint64_t rn53_q58(uint64_t q) {
+    const int lz = __clzll((long long)q);
+    if (lz >= 11) return q;  // below 2^53: exact
+    const int sh = 11 - lz;
+    const uint64_t mant = q >> sh, rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    return (mant + ((rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull)) << sh;
+}
+
+// The short search for lambda = 1 in integer arithmetic, with the same
+// result as the binary64 form.  For k >= 1 every point below the end of
+// interval k lies in one binade [2^e, 2^(e+1)), e = floor(log2 k) + d
+// (delta_t = 2^d), whose binary64 values are the multiples of u = 2^(e-52).
+// Counted in u, interval k starts at P0 = k 2^(52 - floor(log2 k)) and ends
+// at E = (k + 1) 2^(52 - floor(log2 k)) (at most 2^53), and the binary64 sum
+// of a point P u and a draw x = RN53(q) 2^-58 is P + (x / u rounded to the
+// nearest integer, a tie going to the even sum).  That is exact while the
+// sum stays below 2^(e+1), and at or above E exactly when binary64's is,
+// which ends the interval either way.  Each lane rounds its own draw; the
+// direction of a tie depends on the parity of the sum before it, which
+// follows from the ties and the parities of the lanes below (two ballots).
+// Prefix sums over lanes 8 m .. 8 m + 7 (shuffles) then give every point of
+// interval k at once, where the binary64 form adds them one after another
+// at 64 cycles per add on B300.  Outside its range (k = 0, extreme delta_t,
+// k near 2^52) it hands over to the binary64 form.
+__device__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    const int d = c.dt_log2;
+    uint64_t k0 = floor_div_pow2(tau_b, d);
+    const uint64_t T = (tau_b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // tau in units of interval k0
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        // the draws first: the range check and the interval bounds below do
+        // not depend on them and overlap their latency
+        const uint64_t k = k0 + m;
+        const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, i >> 1, TAG_INTERVAL);
+        const uint64_t R = rn53_q58(exp1_q58(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+        const int lg0 = 63 - __clzll((long long)k0);
+        const int lg3 = 63 - __clzll((long long)(k0 + 3ull));
+        const int lg = 63 - __clzll((long long)k);
+        const int sft = min(max(lg + d + 6, 0), 63);  // x / u = RN53(q) 2^-sft
+        const int sh = max(52 - lg, 0), sh0 = max(52 - lg0, 0);  // in range below: 1 .. 52
+        const uint64_t P0 = k << sh;
+        const uint64_t E = (k + 1ull) << sh;
+        const uint64_t E0 = (k0 + 1ull) << sh0;
+        if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52))
+            return coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
+        uint64_t a = R >> sft;
+        bool tie = false;
+        if (sft > 0) {
+            const uint64_t rem = R & ((1ull << sft) - 1ull), half = 1ull << (sft - 1);
+            a += rem > half ? 1ull : 0ull;
+            tie = rem == half;
+        }
+        const unsigned ties = __ballot_sync(0xFFFFFFFFu, tie);
+        if (ties) {
+            // parity of the sum below lane i: the parities of the draws after
+            // the last tie below i (a tie leaves an even sum; P0 is even)
+            const unsigned odd = __ballot_sync(0xFFFFFFFFu, (a & 1ull) != 0ull);
+            const unsigned tm = (ties >> (8u * m)) & 0xFFu, om = (odd >> (8u * m)) & 0xFFu;
+            const unsigned below = (1u << i) - 1u, tb = tm & below;
+            const unsigned upto = tb ? (2u << (31 - __clz(tb))) - 1u : 0u;
+            const unsigned parity = (unsigned)__popc(om & below & ~upto) & 1u;
+            if (tie) a += (parity ^ (unsigned)a) & 1u;
+        }
+        // a draw of more than 2^54 u ends the interval whatever follows
+        uint64_t S = a < (1ull << 54) ? a : (1ull << 54);
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+            const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, S, off, 8);
+            if (i >= (uint32_t)off) S += o;
+        }
+        const uint64_t P = P0 + S;
+        const uint64_t tu = round == 0 ? T : 0ull;  // later rounds: every point is after tau
+        const unsigned hit = __ballot_sync(0xFFFFFFFFu, m == 0u && (P >= E || P > tu));
+        if (!hit) return coop_next_exp<true>(c, loc, tau, ln, lane);  // eight points up to tau
+        const uint64_t Pj = __shfl_sync(0xFFFFFFFFu, P, __ffs(hit) - 1);
+        if (Pj < E0) return __longlong_as_double((long long)(((uint64_t)(lg0 + d + 1023) << 52) | (Pj & 0xFFFFFFFFFFFFFull)));
+        // interval k0 ended first: the first point of the lowest later
+        // interval that has one inside it
+        const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
+        if (later) {
+            const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
+            return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, bits, __ffs(later) - 1));
+        }
+    }
+    return -1.0;
+}
+
+template <bool LAM1>
+__device__ __forceinline__ double coop_next_exp_short(const LaneSim& c, uint64_t loc, double tau, const LnC& ln,
+                                                      uint32_t lane) {
+    if (LAM1) return coop_next_exp_int(c, loc, tau, ln, lane);
+    return coop_next_exp_short_fp<false>(c, loc, tau, ln, lane);
 }
 
 // dispersal target from the event stream's draws 1, 2, 3 (draw 0 decided

@@ -138,3 +138,39 @@ __global__ void k_selftest(const uint64_t* __restrict__ in, uint64_t n, uint64_t
         }
     }
 }
+
+// event-time search probe (sim_selftest_search): the first event time after
+// tau[q] at loc[q] by one search form; forms 0 and 1 one lane per query
+// (one or two draw blocks per step), 2 to 4 one warp per query (general,
+// short in binary64, short as the tail kernel runs it)
+template <int FORM>
+__global__ void k_selftest_search(const SimParams* __restrict__ P, const SimState* S, const uint64_t* __restrict__ loc,
+                                  const double* __restrict__ tau, uint64_t n, double* __restrict__ out) {
+    LaneSim c;
+    load_lanesim(c, P, S, 0);
+    const LnC ln = ln_tables();
+    if (FORM <= 1) {
+        for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n;
+             q += (uint64_t)gridDim.x * blockDim.x)
+            out[q] = next_event_time<FORM + 1>(c, loc[q], tau[q], ln);
+        return;
+    }
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; q < n; q += warps) {
+        const uint64_t l = loc[q];
+        const double t0 = tau[q];
+        double t;
+        if (c.sampler == 1) {
+            t = FORM == 2 ? coop_next_poisson(c, l, t0, lane) : coop_next_poisson_short(c, l, t0, lane);
+        } else if (FORM == 2) {
+            t = c.lam1 ? coop_next_exp<true>(c, l, t0, ln, lane) : coop_next_exp<false>(c, l, t0, ln, lane);
+        } else if (FORM == 3) {
+            t = c.lam1 ? coop_next_exp_short_fp<true>(c, l, t0, ln, lane)
+                       : coop_next_exp_short_fp<false>(c, l, t0, ln, lane);
+        } else {
+            t = c.lam1 ? coop_next_exp_short<true>(c, l, t0, ln, lane) : coop_next_exp_short<false>(c, l, t0, ln, lane);
+        }
+        if (lane == 0) out[q] = t;
+    }
+}
