@@ -291,7 +291,7 @@ __device__ double coop_next_exp(const LaneSim& c, uint64_t loc, double tau, cons
 // 8 m + i the interval's point i.  Intervals of more than 8 points are rare
 // here (Poi(2) > 8: 2.4e-4 of intervals); the search then starts again in
 // the general form above.  Four intervals without an answer: go on at k + 4.
-__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+__device__ double coop_next_poisson_short_fp(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     const uint32_t m = lane >> 3, i = lane & 7u;
     uint64_t k0 = floor_div_pow2(tau_b, c.dt_log2);
@@ -313,6 +313,54 @@ __device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double
         // the smallest point > tau of the four intervals is the smallest of
         // the first interval that has one: points of interval k lie in
         // [k dt, (k + 1) dt], rounding included
+        const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32));
+        if (hi != 0xFFFFFFFFu) {
+            const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32) == hi ? (uint32_t)pb : 0xFFFFFFFFu);
+            return __longlong_as_double((long long)(((uint64_t)hi << 32) | lo));
+        }
+    }
+    return -1.0;
+}
+
+// The same search with the points in integer arithmetic.  For k >= 1,
+// point i of interval k is the binary64 sum of k dt (exact) and U dt (exact,
+// U = (draw >> 11) 2^-53); in the binade of k dt, e = floor(log2 k) + d,
+// whose values are the multiples of u = 2^(e-52), that sum is
+// P0 + (U dt / u rounded to the nearest integer, ties to even) with
+// P0 = k 2^(52 - floor(log2 k)) even and U dt / u = (draw >> 11) 2^-(floor(log2 k) + 1).
+// A sum that rounds up to (k + 1) dt is that value (2^(e+1) when it starts
+// the next binade).  No binary64 arithmetic is on the chain.  k = 0 and
+// k near 2^52 go to the binary64 form.
+__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const uint32_t m = lane >> 3, i = lane & 7u;
+    const int d = c.dt_log2;
+    uint64_t k0 = floor_div_pow2(tau_b, d);
+    if (k0 == 0ull) return coop_next_poisson_short_fp(c, loc, tau, lane);
+    for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
+        if (k0 + 4ull >= (1ull << 52)) return coop_next_poisson(c, loc, tau, lane);
+        const uint64_t k = k0 + m;
+        // draw 0 gives the count N; point i is draw 1 + i
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const u64x2 bi = stream_block(c.sk0, c.sk1, loc, k, (1u + i) >> 1, TAG_INTERVAL);
+        const int lg = 63 - __clzll((long long)k);  // 0 .. 51
+        const uint64_t P0 = k << (52 - lg);
+        const int e = lg + d;
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t pb = ~0ull;
+        if (i < N) {
+            const uint64_t v = ((i & 1u) ? bi.lo : bi.hi) >> 11;
+            const int s = lg + 1;  // 1 .. 52
+            const uint64_t fl = v >> s, rem = v & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+            const uint64_t P = P0 + fl + ((rem > half || (rem == half && (fl & 1ull))) ? 1ull : 0ull);
+            const uint64_t q = P < (1ull << 53) ? ((uint64_t)(e + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull)
+                                                : (uint64_t)(e + 1024) << 52;
+            if (q > tau_b) pb = q;
+        }
+        if (__any_sync(0xFFFFFFFFu, N > 8u)) return coop_next_poisson(c, loc, tau, lane);
+        // the smallest point > tau of the four intervals is the smallest of
+        // the first interval that has one: points of interval k lie in
+        // [k dt, (k + 1) dt]
         const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32));
         if (hi != 0xFFFFFFFFu) {
             const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(pb >> 32) == hi ? (uint32_t)pb : 0xFFFFFFFFu);

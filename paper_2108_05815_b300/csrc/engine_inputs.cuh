@@ -162,7 +162,9 @@ __global__ void k_selftest_search(const SimParams* __restrict__ P, const SimStat
         const double t0 = tau[q];
         double t;
         if (c.sampler == 1) {
-            t = FORM == 2 ? coop_next_poisson(c, l, t0, lane) : coop_next_poisson_short(c, l, t0, lane);
+            t = FORM == 2   ? coop_next_poisson(c, l, t0, lane)
+                : FORM == 3 ? coop_next_poisson_short_fp(c, l, t0, lane)
+                            : coop_next_poisson_short(c, l, t0, lane);
         } else if (FORM == 2) {
             t = c.lam1 ? coop_next_exp<true>(c, l, t0, ln, lane) : coop_next_exp<false>(c, l, t0, ln, lane);
         } else if (FORM == 3) {
