@@ -7,10 +7,13 @@
   python -m paper_2108_05815_b300.cases busy [--sampler ...] [--rounds 6]
       a 1024 x 1024 torus (1,048,576 lineages, sigma 2, nu 1e-3) for a few
       rounds: the throughput-bound phase, all lineages active
-  python -m paper_2108_05815_b300.cases tail [--sampler ...]
+  python -m paper_2108_05815_b300.cases tail [--sampler ...] [--only nonspatial|torus]
+         [--reps 3] [--block-threads T --blocks-per-sm B]
       one lineage, nu 1e-4 (about 10^4 events), on a non-spatial deme of one
       and on a 1 x 1 torus with sigma 2: the latency-bound phase; prints the
-      device time per event
+      device time per event (fastest of --reps runs).  A small launch shape
+      (--block-threads 64 --blocks-per-sm 1) leaves few idle warps beside the
+      working one, so that a profiler's per-warp figures are its own
 
 Every run prints one JSON line with what it did.  The device memory held is
 well under 1 GB in all cases.
@@ -55,22 +58,24 @@ def run_busy(ind, sampler, rounds):
     return dict(case="busy", finished=bool(done), rounds=st["rounds"], raw_events=st["raw_events"])
 
 
-def run_tail(ind, sampler):
+def run_tail(ind, sampler, only=None, reps=3, launch=None):
     out = {}
     for name, kw in (("nonspatial_deme1", dict(kind=W.NONSPATIAL, deme=1)),
                      ("torus_1x1_sigma2", dict(kind=W.TORUS, width=1, height=1, deme=1, sigma=2.0))):
+        if only and not name.startswith(only):
+            continue
         best = None
-        for _ in range(3):
+        for _ in range(reps):
             kind = kw["kind"]
             args = {k: v for k, v in kw.items() if k != "kind"}
-            s = _sim(ind, kind, 1e-4, 1, sampler, dict(profile=1), **args)
+            s = _sim(ind, kind, 1e-4, 1, sampler, dict(profile=1, **(launch or {})), **args)
             s.sample()
             t0 = time.perf_counter()
             assert s.run()
             t1 = time.perf_counter()
             st = s.stats()
             s.close()
-            per = dict(events=st["raw_events"], us_per_event_wall=(t1 - t0) * 1e6 / st["raw_events"],
+            per = dict(events=st["raw_events"], rounds=st["rounds"], us_per_event_wall=(t1 - t0) * 1e6 / st["raw_events"],
                        us_per_event_device=st["advance_ms"] * 1e3 / st["raw_events"])
             if best is None or per["us_per_event_device"] < best["us_per_event_device"]:
                 best = per
@@ -84,6 +89,10 @@ def main(argv=None):
     ap.add_argument("--sampler", default="exp", choices=sorted(SAMPLERS))
     ap.add_argument("--rounds", type=int, default=6)
     ap.add_argument("--events", action="store_true")
+    ap.add_argument("--only", choices=["nonspatial", "torus"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--block-threads", type=int)
+    ap.add_argument("--blocks-per-sm", type=int)
     a = ap.parse_args(argv)
     import torch  # noqa: F401  (device memory comes from torch's allocator)
     import paper_2108_05815_b300 as ind
@@ -95,7 +104,12 @@ def main(argv=None):
     elif a.case == "busy":
         r = run_busy(ind, sampler, a.rounds)
     else:
-        r = run_tail(ind, sampler)
+        launch = {}
+        if a.block_threads:
+            launch["block_threads"] = a.block_threads
+        if a.blocks_per_sm:
+            launch["blocks_per_sm"] = a.blocks_per_sm
+        r = run_tail(ind, sampler, a.only, a.reps, launch)
     r["sampler"] = a.sampler
     print(json.dumps(r))
 
