@@ -432,7 +432,11 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     uint32_t lane_max = 0;  // most events of one lineage this round (the same in every lane)
     WarpLogBuf wlog;
     wlog.n = 0;
+    // this warp's alias-row buffer (map lineages; after the tables)
+    uint64_t* const sbuf = (uint64_t*)(adv_smem + B.stage_off + (size_t)(threadIdx.x >> 5) * B.stage_bytes);
     for (;;) {
+        // the previous lineage's last row copy lands before the buffer is reused
+        if (B.stage_bytes) asm volatile("cp.async.wait_all;" ::: "memory");
         uint32_t k = 0;
         if (lane == 0) k = atomicAdd(&B.G->work_ctr, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
@@ -456,6 +460,9 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         }
         const uint64_t hz = (uint64_t)__double_as_longlong(c.horizon);
         uint32_t ev_lin = 0;
+        // a map lineage's alias row, staged in the warp's buffer
+        const bool stage = B.stage_bytes && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP));
+        const uint64_t* srow = stage ? stage_alias_row(sbuf, B.P, c, loc, lane) : nullptr;
         for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
             if ((uint64_t)__double_as_longlong(tn) > hz) {
                 if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
@@ -470,12 +477,14 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             const uint64_t at = loc;
-            const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane);
+            if (stage) alias_row_wait();
+            const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane, srow);
             if (LOG) {
                 warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
                 tprev = tn;
             }
-            if (!speciated && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP)))
+            if (!speciated && stage) srow = stage_alias_row(sbuf, B.P, c, loc, lane);
+            else if (!speciated && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP)))
                 prefetch_alias_row(B.P, c, loc, lane);
             if (speciated) {
                 if (lane == 0) {

@@ -205,7 +205,10 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
         m->d_off = m->tables.get<int8_t>(off.size());
         uint64_t* d_kw = m->tables.get<uint64_t>(kw.size());
         uint32_t* d_cells = m->tables.get<uint32_t>(cells.size());
-        m->d_alias = m->tables.get<uint64_t>(ncell * m->n_off);  // rows by cell (HBM is plentiful)
+        // rows by cell (HBM is plentiful); two entries of padding: the warp
+        // kernel copies a row in 16-byte pieces from the 16-byte boundary at
+        // or below its start, up to 15 bytes past its end
+        m->d_alias = m->tables.get<uint64_t>(ncell * m->n_off + 2);
         if (!m->d_deme || !m->d_off || !d_kw || !d_cells || !m->d_alias) return fail(IND_ERR_OOM);
         bool okc = cudaMemcpyAsync(m->d_deme, dm.data(), ncell, cudaMemcpyHostToDevice, s) == cudaSuccess &&
                    cudaMemcpyAsync(m->d_off, off.data(), off.size(), cudaMemcpyHostToDevice, s) == cudaSuccess &&
@@ -435,7 +438,7 @@ size_t sim_mem_estimate(const ind_landscape* L, const ind_dispersal* D, double f
         for (int dy = -R; dy <= R; ++dy)
             for (int dx = -R; dx <= R; ++dx)
                 if (dx * dx + dy * dy <= R * R) ++n_off;
-        tables = ncell * (1 + 4 + n_off * 8) + 2 * n_off + 8 * (size_t)(R * R + 1);
+        tables = ncell * (1 + 4 + n_off * 8) + 16 + 2 * n_off + 8 * (size_t)(R * R + 1);
     } else {
         individuals = (double)ncell * L->deme;
         if (L->kind == IND_TORUS) tables = 16 * (size_t)host_gauss_half(D->sigma) + 4 * GUIDE_N;

@@ -95,6 +95,7 @@ struct Batch {
     uint32_t graph_rounds = 0;
     int coop_mode = 0;                               // its specialisation (k_advance_coop MODE)
     int coop_kind = -1;                              // the landscape kind all simulations share, or -1
+    size_t coop_smem = 0;                            // its dynamic shared memory (tables, alias-row buffers)
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -181,10 +182,26 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.n_slots = (double)m->n_slots;
 }
 
+// dynamic shared memory a block may use, less what the kernel declares statically
+static size_t coop_smem_limit() {
+    static size_t lim = 0;
+    if (!lim) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, k_advance_coop<false, 0, -1, false>) == cudaSuccess && optin > 0)
+            lim = (size_t)optin - fa.sharedSizeBytes;
+        else
+            lim = LN_SMEM_BYTES;
+    }
+    return lim;
+}
+
 template <bool COUNT, int MODE, int KIND, bool LOG>
 static cudaError_t set_smem_one() {
     return cudaFuncSetAttribute(k_advance_coop<COUNT, MODE, KIND, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)LN_SMEM_BYTES);
+                                (int)std::max(coop_smem_limit(), LN_SMEM_BYTES));
 }
 
 // the instantiations launch_coop uses: with counting (measurement runs) only
@@ -325,6 +342,25 @@ static ind_status batch_build(Batch& b) {
     b.coop_kind = b.n_sims > 0 ? hp[0].kind : -1;
     for (uint32_t si = 1; si < b.n_sims; ++si)
         if (hp[si].kind != b.coop_kind) b.coop_kind = -1;
+    // map simulations: the warp kernel stages each lineage's alias row in
+    // shared memory (one buffer per warp) while it searches for the next
+    // event, when buffers for the largest dispersal kernel fit beside the
+    // logarithm tables
+    uint32_t n_off_max = 0;
+    for (auto* m : b.sims)
+        if (m->land.kind == IND_MAP) n_off_max = std::max(n_off_max, m->n_off);
+    const size_t ln_bytes = d.need_ln ? LN_SMEM_BYTES : 0;
+    b.coop_smem = ln_bytes;
+    d.stage_off = d.stage_bytes = 0;
+    if (n_off_max) {
+        const size_t per = ((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15;  // a row from a 16-byte boundary
+        const size_t total = ln_bytes + (size_t)(b.tun.block_threads / 32) * per;
+        if (total <= coop_smem_limit()) {
+            d.stage_off = (uint32_t)ln_bytes;
+            d.stage_bytes = (uint32_t)per;
+            b.coop_smem = total;
+        }
+    }
     cudaStream_t s = b.stream;
     CK(cudaMemcpyAsync(b.d_params, hp.data(), sizeof(SimParams) * b.n_sims, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b.d_gid_base, gid_base.data(), sizeof(uint32_t) * b.n_sims, cudaMemcpyHostToDevice, s));
@@ -406,22 +442,22 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
         if (b.dev.count_unique) {
             k_advance<true, 1, true><<<ag, at, smem, s>>>(b.dev);
             CK(cudaGetLastError());
-            launch_coop<true, true>(b, smem, s);
+            launch_coop<true, true>(b, b.coop_smem, s);
         } else {
             k_advance<false, 1, true><<<ag, at, smem, s>>>(b.dev);
             CK(cudaGetLastError());
-            launch_coop<false, true>(b, smem, s);
+            launch_coop<false, true>(b, b.coop_smem, s);
         }
     } else if (b.dev.count_unique) {
         if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<true, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
-        launch_coop<true, false>(b, smem, s);
+        launch_coop<true, false>(b, b.coop_smem, s);
     } else {
         if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         else k_advance<false, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
         CK(cudaGetLastError());
-        launch_coop<false, false>(b, smem, s);
+        launch_coop<false, false>(b, b.coop_smem, s);
     }
     CK(cudaGetLastError());
     if (prof) CK(cudaEventRecordWithFlags(b.ev_end[r], s, flag));

@@ -518,10 +518,12 @@ __device__ __forceinline__ double coop_next_exp_short(const LaneSim& c, uint64_t
 // d1 (migration, or the metacommunity parent), d2 (parent after migration
 // or locally)
 // (KIND: the landscape kind when the caller knows it at compile time, -1
-// for the simulation's own)
+// for the simulation's own; srow: the origin cell's alias row staged in
+// shared memory, or null to read it from global memory)
 template <int KIND = -1>
 __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* __restrict__ P, uint64_t loc,
-                                            uint64_t d1, uint64_t d2, uint64_t d3) {
+                                            uint64_t d1, uint64_t d2, uint64_t d3,
+                                            const uint64_t* srow = nullptr) {
     const int kind = KIND >= 0 ? KIND : c.kind;
     if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
     const SimParams* p = P + c.sim;
@@ -556,7 +558,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     // carries the target deme (k_alias_build), then the offset table (L1)
     const uint32_t n_off = __ldg(&p->n_off);
     const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
-    const uint64_t e = __ldg(p->alias + ((size_t)y * c.W + x) * n_off + col);
+    const uint64_t e = srow ? srow[col] : __ldg(p->alias + ((size_t)y * c.W + x) * n_off + col);
     const uint32_t u = (uint32_t)d1;
     const bool take_col = (e >> 63) != 0 || u < (uint32_t)e;
     const uint32_t o = take_col ? col : (uint32_t)((e >> 32) & (ALIAS_MAX_OFFSETS - 1u));
@@ -580,6 +582,33 @@ __device__ __forceinline__ void prefetch_alias_row(const SimParams* __restrict__
     const uint32_t bytes = __ldg(&p->n_off) * 8u;
     const char* row = (const char*)(p->alias + ((size_t)loc_y(loc) * c.W + loc_x(loc)) * __ldg(&p->n_off));
     for (uint32_t o = lane * 128u; o < bytes; o += 32u * 128u) asm volatile("prefetch.global.L1 [%0];" ::"l"(row + o));
+}
+
+// The warp kernel's alternative: copy the row into the warp's shared-memory
+// buffer (cp.async, 16-byte pieces from the 16-byte boundary at or below the
+// row's start; the allocation has two entries of padding for the last row)
+// while the search runs.  Returns the buffer address of the row's entry 0.
+// Every lane issues its pieces and one commit; alias_row_wait() makes the
+// whole row visible to every lane of the warp.
+__device__ __forceinline__ const uint64_t* stage_alias_row(uint64_t* buf, const SimParams* __restrict__ P,
+                                                           const LaneSim& c, uint64_t loc, uint32_t lane) {
+    const SimParams* p = P + c.sim;
+    const uint32_t n_off = __ldg(&p->n_off);
+    const uint64_t* row = p->alias + ((size_t)loc_y(loc) * c.W + loc_x(loc)) * n_off;
+    const uintptr_t a = (uintptr_t)row;
+    const char* src = (const char*)(a & ~(uintptr_t)15);
+    const uint32_t lead = (uint32_t)(a & 15u);  // 0 or 8
+    const uint32_t pieces = (lead + n_off * 8u + 15u) >> 4;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
+    for (uint32_t k = lane; k < pieces; k += 32u)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * k), "l"(src + 16u * k) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    return buf + (lead >> 3);
+}
+
+__device__ __forceinline__ void alias_row_wait() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
 }
 
 // speciation threshold at loc: the metacommunity's in the spatially
@@ -611,7 +640,7 @@ __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __re
 // four draws by shuffle (one block's latency instead of two interleaved)
 template <int KIND>
 __device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
-                                              double tau, uint32_t lane) {
+                                              double tau, uint32_t lane, const uint64_t* srow = nullptr) {
     const int kind = KIND >= 0 ? KIND : c.kind;
     const uint64_t tk = (uint64_t)__double_as_longlong(tau);
     if (kind == KIND_NONSPATIAL) {
@@ -624,7 +653,7 @@ __device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams*
     const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0), d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
     const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1), d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
     if ((d0 >> 11) < spec_thr(c, P, kind, loc)) return true;
-    loc = disperse<KIND>(c, P, loc, d1, d2, d3);
+    loc = disperse<KIND>(c, P, loc, d1, d2, d3, srow);
     return false;
 }
 

@@ -230,5 +230,7 @@ struct BatchDev {
     int need_ln;  // some simulation uses the exponential-sums sampler
     uint32_t events_per_visit;
     uint32_t coop_lineages;  // a round with at most this many active lineages runs one warp per lineage
+    uint32_t stage_off;      // warp kernel: shared-memory offset of the per-warp alias-row buffers
+    uint32_t stage_bytes;    // bytes of one such buffer (0: map rows are read from global memory)
     EventLog log;            // cap 0: no logging
 };
