@@ -422,8 +422,15 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     if (B.G->n_total > B.coop_lineages) return;  // a round for the one-lane form
     const uint32_t n = B.G->n_work;             // lineages with an event before the horizon (k_filter)
-    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) >= n) return;
+    // Warps take part in the order warp 0 of every block, then warp 1 of
+    // every block, and so on (the grid is one wave of resident blocks), so
+    // that a round with few lineages spreads them over the SMs instead of
+    // packing one block's warps onto one SM's four schedulers.  A block
+    // whose warp 0 has no part leaves at once.
+    const uint32_t wg = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    if (blockIdx.x >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    if (wg >= n) return;  // after the block's table copy
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
     const uint32_t lane = threadIdx.x & 31u;

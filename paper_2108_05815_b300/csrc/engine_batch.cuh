@@ -96,6 +96,7 @@ struct Batch {
     int coop_mode = 0;                               // its specialisation (k_advance_coop MODE)
     int coop_kind = -1;                              // the landscape kind all simulations share, or -1
     size_t coop_smem = 0;                            // its dynamic shared memory (tables, alias-row buffers)
+    uint32_t coop_blocks = 0;                        // its grid: one wave of resident blocks
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -221,9 +222,34 @@ static cudaError_t set_coop_smem() {
     return cudaSuccess;
 }
 
+// blocks of the warp kernel an SM holds at once (the fewest over its
+// instantiations), for a block of `threads` with `smem` dynamic bytes
+static uint32_t coop_blocks_per_sm(uint32_t threads, size_t smem) {
+    const void* fns[] = {
+        (const void*)k_advance_coop<false, 0, -1, false>, (const void*)k_advance_coop<false, 1, -1, false>,
+        (const void*)k_advance_coop<false, 2, -1, false>, (const void*)k_advance_coop<false, 1, 0, false>,
+        (const void*)k_advance_coop<false, 1, 1, false>, (const void*)k_advance_coop<false, 1, 2, false>,
+        (const void*)k_advance_coop<false, 2, 0, false>, (const void*)k_advance_coop<false, 2, 1, false>,
+        (const void*)k_advance_coop<false, 2, 2, false>, (const void*)k_advance_coop<true, 0, -1, false>,
+        (const void*)k_advance_coop<true, 1, -1, false>, (const void*)k_advance_coop<true, 2, -1, false>,
+        (const void*)k_advance_coop<false, 0, -1, true>, (const void*)k_advance_coop<false, 1, -1, true>,
+        (const void*)k_advance_coop<false, 2, -1, true>, (const void*)k_advance_coop<false, 1, 0, true>,
+        (const void*)k_advance_coop<false, 1, 1, true>, (const void*)k_advance_coop<false, 1, 2, true>,
+        (const void*)k_advance_coop<false, 2, 0, true>, (const void*)k_advance_coop<false, 2, 1, true>,
+        (const void*)k_advance_coop<false, 2, 2, true>, (const void*)k_advance_coop<true, 0, -1, true>,
+        (const void*)k_advance_coop<true, 1, -1, true>, (const void*)k_advance_coop<true, 2, -1, true>};
+    int best = 0;
+    for (const void* f : fns) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)threads, smem) != cudaSuccess) nb = 1;
+        best = best == 0 ? nb : std::min(best, nb);
+    }
+    return (uint32_t)std::max(best, 1);
+}
+
 template <bool COUNT, int MODE, bool LOG>
 static void launch_coop_kind(const Batch& b, size_t smem, cudaStream_t s) {
-    const dim3 g(b.adv_blocks), t(b.adv_threads);
+    const dim3 g(b.coop_blocks), t(b.adv_threads);
     if (COUNT || b.coop_kind < 0 || b.coop_kind > KIND_MAP)  // counting runs and mixed or implicit batches
         k_advance_coop<COUNT, MODE, -1, LOG><<<g, t, smem, s>>>(b.dev);
     else if (b.coop_kind == KIND_NONSPATIAL)
@@ -238,7 +264,7 @@ template <bool COUNT, bool LOG>
 static void launch_coop(const Batch& b, size_t smem, cudaStream_t s) {
     if (b.coop_mode == 1) launch_coop_kind<COUNT, 1, LOG>(b, smem, s);
     else if (b.coop_mode == 2) launch_coop_kind<COUNT, 2, LOG>(b, smem, s);
-    else k_advance_coop<COUNT, 0, -1, LOG><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+    else k_advance_coop<COUNT, 0, -1, LOG><<<b.coop_blocks, b.adv_threads, smem, s>>>(b.dev);
 }
 
 static ind_status batch_build(Batch& b) {
@@ -407,6 +433,7 @@ static ind_status batch_build(Batch& b) {
     CK(cudaFuncSetAttribute(k_advance_sm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LN_SMEM_BYTES));
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
+    b.coop_blocks = std::min(b.adv_blocks, sms * coop_blocks_per_sm(b.adv_threads, b.coop_smem));
     b.cmp_blocks = sms * 4;
     // starting states
     k_start<<<1, 256, 0, s>>>(d, b.n_lin);
