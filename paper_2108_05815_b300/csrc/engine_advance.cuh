@@ -64,11 +64,16 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     if (B.G->n_total <= B.coop_lineages) return;  // a round for k_advance_coop
     const uint32_t n = B.G->n_work;              // lineages with an event before the horizon (k_filter)
     const uint32_t chunk = 32u * B.lpl;
-    // a block whose first possible claim lies beyond the work list has
-    // nothing to do (claims go out in order of arrival, at most one per warp)
-    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    // Warps take part in the order warp 0 of every block, then warp 1, ...
+    // (the grid is one wave of resident blocks): a round with few lineages
+    // spreads its warps over the SMs.  Claims go out in order of arrival, at
+    // most one chunk per warp at a time, so a warp whose first possible claim
+    // lies beyond the work list has nothing to do.
+    const uint32_t wg = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    if ((uint64_t)blockIdx.x * chunk >= n) return;
     // the logarithm tables are staged only if some simulation sums exponentials
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    if ((uint64_t)wg * chunk >= n) return;  // after the block's table copy
 
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
@@ -203,8 +208,10 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
     if (B.G->n_total <= B.coop_lineages) return;  // a round for k_advance_coop
     const uint32_t n = B.G->n_work;              // lineages with an event before the horizon (k_filter)
     const uint32_t chunk = 32u * B.lpl;
-    if ((uint64_t)blockIdx.x * (blockDim.x >> 5) * chunk >= n) return;
+    const uint32_t wg = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;  // order of taking part, as k_advance
+    if ((uint64_t)blockIdx.x * chunk >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
+    if ((uint64_t)wg * chunk >= n) return;
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
     const uint32_t lane = threadIdx.x & 31u;

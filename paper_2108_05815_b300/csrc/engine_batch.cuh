@@ -97,6 +97,7 @@ struct Batch {
     int coop_kind = -1;                              // the landscape kind all simulations share, or -1
     size_t coop_smem = 0;                            // its dynamic shared memory (tables, alias-row buffers)
     uint32_t coop_blocks = 0;                        // its grid: one wave of resident blocks
+    uint32_t lane_blocks = 0;                        // the one-lane kernels' grid: one wave of resident blocks
     cudaStream_t cap_stream = nullptr;  // private stream for graph capture (the legacy stream cannot capture)
     std::vector<cudaEvent_t> ev_start, ev_end;  // profile: one pair per round of a chunk
     double advance_ms = 0.0;
@@ -238,6 +239,20 @@ static uint32_t coop_blocks_per_sm(uint32_t threads, size_t smem) {
         (const void*)k_advance_coop<false, 2, 0, true>, (const void*)k_advance_coop<false, 2, 1, true>,
         (const void*)k_advance_coop<false, 2, 2, true>, (const void*)k_advance_coop<true, 0, -1, true>,
         (const void*)k_advance_coop<true, 1, -1, true>, (const void*)k_advance_coop<true, 2, -1, true>};
+    int best = 0;
+    for (const void* f : fns) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)threads, smem) != cudaSuccess) nb = 1;
+        best = best == 0 ? nb : std::min(best, nb);
+    }
+    return (uint32_t)std::max(best, 1);
+}
+
+// blocks of the one-lane kernels an SM holds at once (the fewest over them)
+static uint32_t lane_blocks_per_sm(uint32_t threads, size_t smem) {
+    const void* fns[] = {(const void*)k_advance<false, 1, false>, (const void*)k_advance<true, 1, false>,
+                         (const void*)k_advance<false, 1, true>, (const void*)k_advance<true, 1, true>,
+                         (const void*)k_advance_sm<false>, (const void*)k_advance_sm<true>};
     int best = 0;
     for (const void* f : fns) {
         int nb = 0;
@@ -434,6 +449,7 @@ static ind_status batch_build(Batch& b) {
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
     b.coop_blocks = std::min(b.adv_blocks, sms * coop_blocks_per_sm(b.adv_threads, b.coop_smem));
+    b.lane_blocks = std::min(b.adv_blocks, sms * lane_blocks_per_sm(b.adv_threads, LN_SMEM_BYTES));
     b.cmp_blocks = sms * 4;
     // starting states
     k_start<<<1, 256, 0, s>>>(d, b.n_lin);
@@ -464,7 +480,7 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
     // choice is made per round inside captured chunks.  An event log takes
     // the logging forms (one-lane loop; the warp form as specialised as
     // without a log).
-    const dim3 ag(b.adv_blocks), at(b.adv_threads);
+    const dim3 ag(b.lane_blocks), at(b.adv_threads);
     if (b.dev.log.cap) {
         if (b.dev.count_unique) {
             k_advance<true, 1, true><<<ag, at, smem, s>>>(b.dev);
@@ -476,13 +492,13 @@ static ind_status launch_round(Batch& b, uint32_t r, bool capturing) {
             launch_coop<false, true>(b, b.coop_smem, s);
         }
     } else if (b.dev.count_unique) {
-        if (conv) k_advance_sm<true><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-        else k_advance<true, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (conv) k_advance_sm<true><<<ag, at, smem, s>>>(b.dev);
+        else k_advance<true, 1, false><<<ag, at, smem, s>>>(b.dev);
         CK(cudaGetLastError());
         launch_coop<true, false>(b, b.coop_smem, s);
     } else {
-        if (conv) k_advance_sm<false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
-        else k_advance<false, 1, false><<<b.adv_blocks, b.adv_threads, smem, s>>>(b.dev);
+        if (conv) k_advance_sm<false><<<ag, at, smem, s>>>(b.dev);
+        else k_advance<false, 1, false><<<ag, at, smem, s>>>(b.dev);
         CK(cudaGetLastError());
         launch_coop<false, false>(b, b.coop_smem, s);
     }

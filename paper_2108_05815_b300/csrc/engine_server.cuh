@@ -379,6 +379,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.adv_threads = b.tun.block_threads;
     b.adv_blocks = sms * b.tun.blocks_per_sm;
     b.coop_blocks = std::min(b.adv_blocks, sms * coop_blocks_per_sm(b.adv_threads, b.coop_smem));
+    b.lane_blocks = std::min(b.adv_blocks, sms * lane_blocks_per_sm(b.adv_threads, LN_SMEM_BYTES));
     b.cmp_blocks = sms * 4;
     if (b.tun.profile) {
         b.ev_start.resize(b.tun.rounds_per_check);
