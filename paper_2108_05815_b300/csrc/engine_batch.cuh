@@ -8,6 +8,31 @@
 // ---------------------------------------------------------------------------
 struct Batch;
 
+// Pinned host copies of the device globals, reused across batches: a
+// cudaMallocHost costs about half a millisecond, as much as a short
+// simulation's whole setup.  Kept until the process ends.
+static std::mutex g_pinned_mu;
+static std::vector<Globals*> g_pinned_free;
+
+static Globals* pinned_globals_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_pinned_mu);
+        if (!g_pinned_free.empty()) {
+            Globals* p = g_pinned_free.back();
+            g_pinned_free.pop_back();
+            return p;
+        }
+    }
+    Globals* p = nullptr;
+    return cudaMallocHost(&p, sizeof(Globals)) == cudaSuccess ? p : nullptr;
+}
+
+static void pinned_globals_put(Globals* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned_free.push_back(p);
+}
+
 struct ind_sim {
     ind_landscape land{};
     ind_dispersal disp{};
@@ -115,7 +140,7 @@ struct Batch {
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (auto e : ev_start) cudaEventDestroy(e);
         for (auto e : ev_end) cudaEventDestroy(e);
-        if (h_g) cudaFreeHost(h_g);
+        pinned_globals_put(h_g);
         scratch.release_all();
         pool.release_all();
     }
@@ -412,7 +437,8 @@ static ind_status batch_build(Batch& b) {
         CK(cudaMemsetAsync(d.ht_val[t], 0xFF, sizeof(uint32_t) * cap, s));
         if (d.count_unique) CK(cudaMemsetAsync(d.ev[t], 0xFF, sizeof(EvSlot) * ((size_t)d.ev_mask + 1), s));
     }
-    CK(cudaMallocHost(&b.h_g, sizeof(Globals)));
+    b.h_g = pinned_globals_get();
+    if (!b.h_g) return IND_ERR_OOM;
     b.h_state.resize(b.n_sims);
     if (b.tun.profile) {
         b.ev_start.resize(b.tun.rounds_per_check);

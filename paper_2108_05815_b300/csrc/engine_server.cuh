@@ -368,7 +368,9 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
         if ((e = cudaMemsetAsync(d.ht_key[t], 0xFF, sizeof(unsigned long long) * cap, s)) ||
             (e = cudaMemsetAsync(d.ht_val[t], 0xFF, sizeof(uint32_t) * cap, s)))
             return fail(e);
-    if ((e = cudaMallocHost(&b.h_g, sizeof(Globals))) || (e = cudaStreamSynchronize(s))) return fail(e);
+    b.h_g = pinned_globals_get();
+    if (!b.h_g) return fail(cudaErrorMemoryAllocation);
+    if ((e = cudaStreamSynchronize(s))) return fail(e);
     memset(b.h_g, 0, sizeof(Globals));
     b.h_state.resize(max_sims);
     const uint32_t sms = sm_count();
