@@ -340,16 +340,20 @@ __device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double
     for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
         if (k0 + 4ull >= (1ull << 52)) return coop_next_poisson(c, loc, tau, lane);
         const uint64_t k = k0 + m;
-        // draw 0 gives the count N; point i is draw 1 + i
-        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
-        const u64x2 bi = stream_block(c.sk0, c.sk1, loc, k, (1u + i) >> 1, TAG_INTERVAL);
+        // draw 0 gives the count N; point i is draw 1 + i.  Lane i of the
+        // group computes block i (0 .. 4: draws 0 .. 9), the group shares
+        // them by shuffle: one block per lane instead of two
+        const u64x2 bl = stream_block(c.sk0, c.sk1, loc, k, min(i, 4u), TAG_INTERVAL);
+        const uint32_t g0 = lane & ~7u, src = g0 + ((1u + i) >> 1);
+        const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, bl.lo, g0);
+        const uint64_t plo = __shfl_sync(0xFFFFFFFFu, bl.lo, src), phi = __shfl_sync(0xFFFFFFFFu, bl.hi, src);
         const int lg = 63 - __clzll((long long)k);  // 0 .. 51
         const uint64_t P0 = k << (52 - lg);
         const int e = lg + d;
-        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, d0);
         uint64_t pb = ~0ull;
         if (i < N) {
-            const uint64_t v = ((i & 1u) ? bi.lo : bi.hi) >> 11;
+            const uint64_t v = ((i & 1u) ? plo : phi) >> 11;
             const int s = lg + 1;  // 1 .. 52
             const uint64_t fl = v >> s, rem = v & ((1ull << s) - 1ull), half = 1ull << (s - 1);
             const uint64_t P = P0 + fl + ((rem > half || (rem == half && (fl & 1ull))) ? 1ull : 0ull);
