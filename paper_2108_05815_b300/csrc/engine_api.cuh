@@ -218,7 +218,7 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
             g_last_cuda_error.store((int)cudaGetLastError());
             return fail(IND_ERR_CUDA);
         }
-        const size_t per_warp = ((size_t)m->n_off * 13 + 15) & ~(size_t)15;
+        const size_t per_warp = alias_build_warp_bytes(m->n_off);
         int warps = (int)std::min<size_t>(8, std::max<size_t>(1, (96 * 1024) / per_warp));
         const size_t shb = per_warp * warps;
         if (cudaFuncSetAttribute(k_alias_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shb) != cudaSuccess) {

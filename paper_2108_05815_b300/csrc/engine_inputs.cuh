@@ -16,9 +16,9 @@ __global__ void k_habitat(uint8_t* out, uint32_t W, uint32_t H, uint32_t sk0, ui
     }
 }
 
-// one warp per habitable cell: weights, then integer Vose on lane 0.  Rows
-// are indexed by cell (those of cells without habitat are never read), and
-// an entry holds everything a dispersal needs besides the offset table:
+// one warp per habitable cell: weights, then integer Vose.  Rows are
+// indexed by cell (those of cells without habitat are never read), and an
+// entry holds everything a dispersal needs besides the offset table:
 // threshold q (bits 0-31), alias column (32-44), the deme of the column's
 // own target (45-52) and of the alias column's target (53-60), and bit 63
 // for a column that is always taken
@@ -28,16 +28,29 @@ __device__ __forceinline__ uint64_t alias_entry(uint64_t q, uint32_t col, uint32
            (full ? (1ull << 63) : 0ull);
 }
 
+// shared-memory bytes of one warp of k_alias_build for n_off offsets
+__host__ __device__ constexpr size_t alias_build_warp_bytes(uint32_t n_off) {
+    return ((size_t)n_off * 15 + 15) & ~(size_t)15;
+}
+
+constexpr uint16_t ALIAS_FULL = 0xFFFFu;  // a column that is always taken
+
+// Vose's pairing is sequential (lane 0 pops the small and large stacks in
+// order); the threshold of a column depends only on its scaled weight when
+// it was popped as small, which never changes afterwards.  So lane 0 only
+// pairs (alias column per column, full marks), and then all lanes compute
+// the thresholds floor(s_a 2^32 / W) by restoring division and write the
+// entries, 32 columns at a time.
 __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint32_t H,
                               const uint32_t* __restrict__ cells, uint32_t n_rows, const int8_t* __restrict__ off,
                               uint32_t n_off, const uint64_t* __restrict__ kw, uint64_t* __restrict__ alias) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t warps = blockDim.x >> 5, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const size_t per_warp = ((size_t)n_off * 13 + 15) & ~(size_t)15;  // 16-byte aligned regions
-    uint64_t* s = (uint64_t*)(smem + per_warp * w);
+    uint64_t* s = (uint64_t*)(smem + alias_build_warp_bytes(n_off) * w);  // 16-byte aligned regions
     uint16_t* small_ = (uint16_t*)(s + n_off);
     uint16_t* large_ = small_ + n_off;
-    uint8_t* tdeme = (uint8_t*)(large_ + n_off);  // deme of each offset's target
+    uint16_t* alias_of = large_ + n_off;                // alias column, or ALIAS_FULL
+    uint8_t* tdeme = (uint8_t*)(alias_of + n_off);      // deme of each offset's target
     for (uint32_t row = blockIdx.x * warps + w; row < n_rows; row += gridDim.x * warps) {
         const uint32_t cell = cells[row];
         const uint32_t cx = cell % W, cy = cell / W;
@@ -53,10 +66,9 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        const uint64_t Wt = part;
         __syncwarp();
         if (lane == 0) {
-            const uint64_t Wt = part;
-            uint64_t* e = alias + (size_t)cell * n_off;
             uint32_t ns = 0, nl = 0;
             for (uint32_t o = 0; o < n_off; ++o) {
                 if (s[o] < Wt) small_[ns++] = (uint16_t)o;
@@ -65,29 +77,33 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
             while (ns > 0 && nl > 0) {
                 const uint32_t a = small_[--ns];
                 const uint32_t b = large_[--nl];
-                // q = floor(s_a 2^32 / W) by restoring division (s_a < W < 2^56)
-                uint64_t rem = s[a], q = 0;
-                for (int bit = 0; bit < 32; ++bit) {
-                    rem <<= 1;
-                    q <<= 1;
-                    if (rem >= Wt) {
-                        rem -= Wt;
-                        q |= 1ull;
-                    }
-                }
-                e[a] = alias_entry(q, a, b, tdeme[a], tdeme[b], false);
+                alias_of[a] = (uint16_t)b;  // s[a] stays as it is: a's threshold comes from it
                 s[b] = s[b] + s[a] - Wt;
                 if (s[b] < Wt) small_[ns++] = (uint16_t)b;
                 else large_[nl++] = (uint16_t)b;
             }
-            while (nl > 0) {
-                const uint32_t b = large_[--nl];
-                e[b] = alias_entry(0xFFFFFFFFull, b, b, tdeme[b], tdeme[b], true);
+            while (nl > 0) alias_of[large_[--nl]] = ALIAS_FULL;
+            while (ns > 0) alias_of[small_[--ns]] = ALIAS_FULL;
+        }
+        __syncwarp();
+        uint64_t* e = alias + (size_t)cell * n_off;
+        for (uint32_t o = lane; o < n_off; o += 32) {
+            const uint32_t b = alias_of[o];
+            if (b == ALIAS_FULL) {
+                e[o] = alias_entry(0xFFFFFFFFull, o, o, tdeme[o], tdeme[o], true);
+                continue;
             }
-            while (ns > 0) {
-                const uint32_t a = small_[--ns];
-                e[a] = alias_entry(0xFFFFFFFFull, a, a, tdeme[a], tdeme[a], true);
+            // q = floor(s_o 2^32 / W) by restoring division (s_o < W < 2^56)
+            uint64_t rem = s[o], q = 0;
+            for (int bit = 0; bit < 32; ++bit) {
+                rem <<= 1;
+                q <<= 1;
+                if (rem >= Wt) {
+                    rem -= Wt;
+                    q |= 1ull;
+                }
             }
+            e[o] = alias_entry(q, o, b, tdeme[o], tdeme[b], false);
         }
         __syncwarp();
     }
