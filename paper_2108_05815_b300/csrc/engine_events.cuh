@@ -575,11 +575,11 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
 }
 
 // A map lineage's next dispersal reads one entry of its cell's alias row.
-// Once the lineage has moved, the warp prefetches that row (n_off x 8 bytes,
-// two lines per lane for the 797 offsets of radius 16) into its SM's L1
-// while it searches for the next event, so that the dispersal's load does not
-// wait on HBM (L1 measured slightly faster than L2 here).  Every address lies
-// in the row.
+// Where the warp kernel has no shared-memory buffer for the row (the server,
+// or a kernel too large for one), the warp prefetches the row (n_off x 8
+// bytes, two lines per lane for the 797 offsets of radius 16) into its SM's
+// L1 once the lineage has moved, while it searches for the next event.
+// Every address lies in the row.
 __device__ __forceinline__ void prefetch_alias_row(const SimParams* __restrict__ P, const LaneSim& c, uint64_t loc,
                                                    uint32_t lane) {
     const SimParams* p = P + c.sim;
