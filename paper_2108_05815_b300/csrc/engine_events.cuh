@@ -460,10 +460,9 @@ __device__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, 
         const int lg3 = 63 - __clzll((long long)(k0 + 3ull));
         const int lg = 63 - __clzll((long long)k);
         const int sft = min(max(lg + d + 6, 0), 63);  // x / u = RN53(q) 2^-sft
-        const int sh = max(52 - lg, 0), sh0 = max(52 - lg0, 0);  // in range below: 1 .. 52
+        const int sh = max(52 - lg, 0);  // in range below: 1 .. 52
         const uint64_t P0 = k << sh;
         const uint64_t E = (k + 1ull) << sh;
-        const uint64_t E0 = (k0 + 1ull) << sh0;
         if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52))
             return coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
         uint64_t a = R >> sft;
@@ -473,7 +472,16 @@ __device__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, 
             a += rem > half ? 1ull : 0ull;
             tie = rem == half;
         }
+        // prefix sums as if no draw were a tie (rare); the tie vote runs
+        // beside them and a tie redoes them.  A draw of more than 2^54 u
+        // ends the interval whatever follows.
         const unsigned ties = __ballot_sync(0xFFFFFFFFu, tie);
+        uint64_t S = a < (1ull << 54) ? a : (1ull << 54);
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+            const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, S, off, 8);
+            if (i >= (uint32_t)off) S += o;
+        }
         if (ties) {
             // parity of the sum below lane i: the parities of the draws after
             // the last tie below i (a tie leaves an even sum; P0 is even)
@@ -483,27 +491,29 @@ __device__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, 
             const unsigned upto = tb ? (2u << (31 - __clz(tb))) - 1u : 0u;
             const unsigned parity = (unsigned)__popc(om & below & ~upto) & 1u;
             if (tie) a += (parity ^ (unsigned)a) & 1u;
-        }
-        // a draw of more than 2^54 u ends the interval whatever follows
-        uint64_t S = a < (1ull << 54) ? a : (1ull << 54);
+            S = a < (1ull << 54) ? a : (1ull << 54);
 #pragma unroll
-        for (int off = 1; off < 8; off <<= 1) {
-            const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, S, off, 8);
-            if (i >= (uint32_t)off) S += o;
+            for (int off = 1; off < 8; off <<= 1) {
+                const uint64_t o = __shfl_up_sync(0xFFFFFFFFu, S, off, 8);
+                if (i >= (uint32_t)off) S += o;
+            }
         }
         const uint64_t P = P0 + S;
+        // this lane's point as binary64 bits (meaningful where P < E), and
+        // the three votes side by side: interval k0's first point after tau,
+        // its end, and the later intervals' first points
+        const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
         const uint64_t tu = round == 0 ? T : 0ull;  // later rounds: every point is after tau
-        const unsigned hit = __ballot_sync(0xFFFFFFFFu, m == 0u && (P >= E || P > tu));
-        if (!hit) return coop_next_exp<true>(c, loc, tau, ln, lane);  // eight points up to tau
-        const uint64_t Pj = __shfl_sync(0xFFFFFFFFu, P, __ffs(hit) - 1);
-        if (Pj < E0) return __longlong_as_double((long long)(((uint64_t)(lg0 + d + 1023) << 52) | (Pj & 0xFFFFFFFFFFFFFull)));
-        // interval k0 ended first: the first point of the lowest later
-        // interval that has one inside it
+        const unsigned found = __ballot_sync(0xFFFFFFFFu, m == 0u && P > tu && P < E);
+        const unsigned ended = __ballot_sync(0xFFFFFFFFu, m == 0u && P >= E);
         const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
-        if (later) {
-            const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
-            return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, bits, __ffs(later) - 1));
-        }
+        const unsigned hit = found | ended;
+        if (!hit) return coop_next_exp<true>(c, loc, tau, ln, lane);  // eight points up to tau
+        const int j = __ffs(hit) - 1;
+        // the first point of interval k0 after tau, else (interval k0 ended
+        // first) the first point of the lowest later interval that has one
+        const int w = (found >> j) & 1u ? j : (later ? __ffs(later) - 1 : -1);
+        if (w >= 0) return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, bits, w));
     }
     return -1.0;
 }
