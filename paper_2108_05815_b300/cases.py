@@ -15,6 +15,12 @@
       (--block-threads 64 --blocks-per-sm 1) leaves few idle warps beside the
       working one, so that a profiler's per-warp figures are its own
 
+  python -m paper_2108_05815_b300.cases alias [--reps 3]
+      config 3's habitat map (1024 x 1024, 60 % habitable, demes 1..8) and
+      its dispersal tables: sim_create builds one alias row of 797 offsets
+      per habitable cell (k_alias_build); prints the wall time of each
+      sim_create
+
 Every run prints one JSON line with what it did.  The device memory held is
 well under 1 GB in all cases.
 """
@@ -83,9 +89,25 @@ def run_tail(ind, sampler, only=None, reps=3, launch=None):
     return dict(case="tail", **out)
 
 
+def run_alias(ind, reps):
+    import torch
+    c = W.config3()
+    dm = ind.habitat(c["map_seed"], c["width"], c["height"], c["p_habitable"], c["max_deme"])
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = ind.Simulation(c["kind"], c["nu"], c["seed"], width=c["width"], height=c["height"], sigma=c["sigma"],
+                           radius=c["radius"], deme_map=dm)
+        torch.cuda.synchronize()
+        times.append(round((time.perf_counter() - t0) * 1e3, 2))
+        s.close()
+    return dict(case="alias", habitable_cells=int((dm > 0).sum()), sim_create_ms=times)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["config2", "busy", "tail"])
+    ap.add_argument("case", choices=["config2", "busy", "tail", "alias"])
     ap.add_argument("--sampler", default="exp", choices=sorted(SAMPLERS))
     ap.add_argument("--rounds", type=int, default=6)
     ap.add_argument("--events", action="store_true")
@@ -103,6 +125,8 @@ def main(argv=None):
         r = run_config2(ind, sampler, a.events)
     elif a.case == "busy":
         r = run_busy(ind, sampler, a.rounds)
+    elif a.case == "alias":
+        r = run_alias(ind, a.reps)
     else:
         launch = {}
         if a.block_threads:
