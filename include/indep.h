@@ -376,6 +376,22 @@ ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, u
 ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const double* tau, uint64_t n,
                                double* out);
 
+/* The alias row of habitable cell (x, y) of a map simulation, as the device
+ * built it (inspection and tests; the dispersal of the section "Spatially
+ * Explicit Scenario with Maps", sampled through one alias table per
+ * habitable cell as in the paper's map benchmarks).  Entry o of the row is
+ * column o of the cell's integer
+ * Vose table over the dispersal kernel's offsets (row-major (dy, dx) within
+ * the radius), packed in 64 bits: threshold q (bits 0-31; column o is taken
+ * iff the 32 low bits of the draw are below q), alias column (bits 32-44),
+ * deme of column o's target cell (45-52) and of the alias column's target
+ * cell (53-60), and bit 63 set when column o is always taken.  *n_out
+ * receives the number of columns; with out == NULL that is all the call
+ * does.  out (host or device, caller-owned) holds cap >= *n_out entries.
+ * IND_ERR_ARG for a simulation that is not a map, a cell outside the map or
+ * without habitat, or a short buffer. */
+ind_status sim_alias_row(ind_sim* m, uint32_t x, uint32_t y, uint64_t* out, uint32_t cap, uint32_t* n_out);
+
 /* Species ranking that allocates nothing (the paper has no counterpart: it
  * exists for callers that must not allocate device memory while they run,
  * e.g. a process that plans all of its device memory at start-up, or code

@@ -107,6 +107,8 @@ EXPORTS = {
                                     ctypes.c_void_p]),
     "sim_selftest_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_uint64, ctypes.c_void_p]),
+    "sim_alias_row": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.c_uint32, ctypes.c_void_p]),
     "ind_species_rank_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "srv_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
@@ -314,6 +316,16 @@ class Simulation:
         _check(lib().sim_selftest_search(self._h, int(form), ctypes.c_void_p(lv.ctypes.data),
                                          ctypes.c_void_p(tv.ctypes.data), lv.size, ctypes.c_void_p(out.ctypes.data)),
                "sim_selftest_search")
+        return out
+
+    def alias_row(self, x, y):
+        """the device's alias row of habitable cell (x, y) of a map simulation
+        (sim_alias_row): packed uint64 entries, one per dispersal offset"""
+        n = ctypes.c_uint32(0)
+        _check(lib().sim_alias_row(self._h, int(x), int(y), None, 0, ctypes.byref(n)), "sim_alias_row")
+        out = np.zeros(n.value, dtype=np.uint64)
+        _check(lib().sim_alias_row(self._h, int(x), int(y), ctypes.c_void_p(out.ctypes.data), n.value,
+                                   ctypes.byref(n)), "sim_alias_row")
         return out
 
     def species_keys(self):

@@ -579,4 +579,26 @@ ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const 
     return IND_OK;
 }
 
+ind_status sim_alias_row(ind_sim* m, uint32_t x, uint32_t y, uint64_t* out, uint32_t cap, uint32_t* n_out) {
+    if (!m || !n_out || m->land.kind != IND_MAP || x >= m->land.width || y >= m->land.height) return IND_ERR_ARG;
+    *n_out = m->n_off;
+    if (!out) return IND_OK;
+    if (cap < m->n_off) return IND_ERR_ARG;
+    const size_t cell = (size_t)y * m->land.width + x;
+    uint8_t deme = 0;
+    if (cudaMemcpyAsync(&deme, m->d_deme + cell, 1, cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        g_last_cuda_error.store((int)cudaGetLastError());
+        return IND_ERR_CUDA;
+    }
+    if (deme == 0) return IND_ERR_ARG;  // rows exist for habitable cells only
+    if (cudaMemcpyAsync(out, m->d_alias + cell * m->n_off, (size_t)m->n_off * 8, cudaMemcpyDefault, m->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess) {
+        g_last_cuda_error.store((int)cudaGetLastError());
+        return IND_ERR_CUDA;
+    }
+    return IND_OK;
+}
+
 }  // extern "C"

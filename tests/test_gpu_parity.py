@@ -397,3 +397,34 @@ def test_implicit_sampled_fraction():
     cfg = IMPLICIT_CFGS[1]
     assert_same(run_gpu(cfg, fraction=0.3, sample_seed=5), run_oracle(cfg, fraction=0.3, sample_seed=5))
 
+
+
+def test_alias_rows_equal_oracle():
+    """The device's alias rows (k_alias_build) against the oracle's alias
+    construction, entry by entry: threshold, alias column, the always-taken
+    mark, and the demes of both target cells that the packed entry carries."""
+    W_, H_ = 97, 83
+    dm = O.habitat(5, W_, H_)
+    cfg = dict(kind=W.MAP, width=W_, height=H_, sigma=4.0, radius=16, nu=1e-3, seed=3)
+    s = gpu_sim(cfg, dm)
+    m = oracle_model(cfg, dm)
+    rng = np.random.default_rng(9)
+    cells = np.flatnonzero(dm.reshape(-1) > 0)
+    pick = rng.choice(cells, size=min(250, cells.size), replace=False)
+    try:
+        for cell in pick:
+            cx, cy = int(cell % W_), int(cell // W_)
+            e = s.alias_row(cx, cy)
+            q, al, full, dx, dy = m.alias_row(cx, cy)
+            assert e.size == q.size
+            assert np.array_equal(e & 0xFFFFFFFF, q.astype(np.uint64))
+            assert np.array_equal((e >> 32) & 0x1FFF, al.astype(np.uint64))
+            assert np.array_equal(e >> 63, full.astype(np.uint64))
+            tdeme = dm.reshape(H_, W_)[(cy + dy.astype(np.int64)) % H_, (cx + dx.astype(np.int64)) % W_]
+            assert np.array_equal((e >> 45) & 0xFF, tdeme.astype(np.uint64))
+            assert np.array_equal((e >> 53) & 0xFF, tdeme[al].astype(np.uint64))
+        with pytest.raises(ind.IndError):  # a cell without habitat has no row
+            empty = np.flatnonzero(dm.reshape(-1) == 0)[0]
+            s.alias_row(int(empty % W_), int(empty // W_))
+    finally:
+        s.close()
