@@ -366,10 +366,12 @@ ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, u
  * simulation m (its seed, sampler, lambda and delta_t; sections "Memoryless
  * sums of exponentials" and "Homogeneous Poisson Point Process" under
  * "Exponential inter-event Times"), computed by search form `form`: 0 and 1 the
- * one-lane searches (one or two draw blocks per step), 2 the warp-
- * cooperative general search, 3 the short warp search in binary64, 4 the
- * short warp search as the tail kernel runs it (integer sums for lambda =
- * 1).  Every form returns the same value; a negative value reports a search
+ * one-lane searches as the one-lane kernel runs them (one or two draw blocks
+ * per step; integer sums for lambda = 1 and integer Poisson points), 2 the
+ * warp-cooperative general search, 3 the short warp search in binary64, 4
+ * the short warp search as the tail kernel runs it (integer sums for lambda
+ * = 1), 5 the one-lane search in binary64 throughout.  Every form returns
+ * the same value; a negative value reports a search
  * beyond the interval limits (IND_ERR_DEVICE in a run).  tau[i] >= 0
  * finite; loc[i] any packed location.  Pointers host or device, owned by
  * the caller; 1 <= n <= 2^26; runs on m's stream and returns after it. */

@@ -535,7 +535,7 @@ ind_status ind_selftest(const uint64_t* in, uint64_t n, uint64_t* exp_q58_out, u
 
 ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const double* tau, uint64_t n,
                                double* out) {
-    if (!m || !loc || !tau || !out || n == 0 || n > (1ull << 26) || form < 0 || form > 4) return IND_ERR_ARG;
+    if (!m || !loc || !tau || !out || n == 0 || n > (1ull << 26) || form < 0 || form > 5) return IND_ERR_ARG;
     cudaStream_t s = m->stream;
     ind_status st = ensure_ln_tables(s);
     if (st != IND_OK) return st;
@@ -558,13 +558,15 @@ ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const 
               cudaMemcpyAsync(d_tau, tau, n * 8, cudaMemcpyDefault, s) == cudaSuccess;
     if (ok) {
         const uint32_t threads = 256;
-        const uint32_t grid = form <= 1 ? grid_for(n, threads, sm_count() * 8) : grid_for(n * 32, threads, sm_count() * 8);
+        const bool lane_form = form <= 1 || form == 5;
+        const uint32_t grid = lane_form ? grid_for(n, threads, sm_count() * 8) : grid_for(n * 32, threads, sm_count() * 8);
         switch (form) {
             case 0: k_selftest_search<0><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
             case 1: k_selftest_search<1><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
             case 2: k_selftest_search<2><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
             case 3: k_selftest_search<3><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
-            default: k_selftest_search<4><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
+            case 4: k_selftest_search<4><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
+            default: k_selftest_search<5><<<grid, threads, 0, s>>>(d_p, d_s, d_loc, d_tau, n, d_out); break;
         }
         g_launches.fetch_add(1);
         ok = cudaGetLastError() == cudaSuccess;

@@ -99,6 +99,16 @@ __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const Lane
     return __ddiv_rn(x, c.lam);
 }
 
+// q 2^-58 rounded to binary64 (53 significant bits, nearest, ties to even),
+// as the multiple of 2^-58 it equals (q < 2^63.5, so no overflow)
+__device__ __forceinline__ uint64_t rn53_q58(uint64_t q) {
+    const int lz = __clzll((long long)q);
+    if (lz >= 11) return q;  // below 2^53: exact
+    const int sh = 11 - lz;
+    const uint64_t mant = q >> sh, rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    return (mant + ((rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull)) << sh;
+}
+
 // first point of loc's event process strictly after tau; negative on overflow.
 // Times are non-negative binary64, so they order like their bit patterns: the
 // compares, floor(tau / delta_t) and k delta_t are done on the bits.  WIDE
@@ -131,6 +141,68 @@ __device__ double next_event_time_exp(const LaneSim& c, uint64_t loc, double tau
                     break;
                 }
                 if (pb > tau_b) return p;
+            }
+            if (next_interval) break;
+        }
+        if (!next_interval) return -1.0;
+        ++k;
+    }
+    return -1.0;
+}
+
+// The same search for lambda = 1 in integer arithmetic (see
+// coop_next_exp_int): in interval k >= 1 the points are the multiples of
+// u = 2^(e-52), e = floor(log2 k) + d, the start is P = k 2^(52 - floor(log2 k))
+// and a draw adds its value in u rounded to the nearest integer (a tie to
+// the even sum).  The rounding of each draw is independent of the sum, so
+// only an integer add and two compares per draw remain sequential, where
+// the binary64 form waits 64 cycles per add on B300.  Intervals outside
+// the range (k = 0, extreme delta_t) go to the binary64 form.
+template <int WIDE>
+__device__ double next_event_time_exp_int(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const int d = c.dt_log2;
+    uint64_t k = floor_div_pow2(tau_b, d);
+    // tau in units of its own interval (later intervals: every point is after tau)
+    uint64_t T = (tau_b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv, T = 0ull) {
+        if (k >= (1ull << 52)) return -1.0;
+        const int lg = 63 - __clzll((long long)k);
+        const int sft = lg + d + 6;
+        if (k == 0ull || sft < 0 || sft > 63) return next_event_time_exp<WIDE, true>(c, loc, tau, ln);
+        const int sh = 52 - lg;
+        uint64_t P = k << sh;
+        const uint64_t E = (k + 1ull) << sh;
+        bool next_interval = false;
+        for (uint32_t j = 0; j < INTERVAL_BLOCK_LIMIT; j += WIDE) {
+            uint64_t fl[2 * WIDE];
+            uint32_t rnd[2 * WIDE];  // 0: round down, 1: up, 2: a tie
+#pragma unroll
+            for (int w = 0; w < WIDE; ++w) {
+                const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t R = rn53_q58(exp1_q58((h ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+                    fl[2 * w + h] = R >> sft;
+                    uint32_t r = 0;
+                    if (sft > 0) {
+                        const uint64_t rem = R & ((1ull << sft) - 1ull), half = 1ull << (sft - 1);
+                        r = rem > half ? 1u : rem == half ? 2u : 0u;
+                    }
+                    rnd[2 * w + h] = r;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2 * WIDE; ++q) {
+                // a draw of 2^54 u or more ends the interval whatever the rounding
+                const uint64_t a = fl[q] < (1ull << 54) ? fl[q] : (1ull << 54);
+                P += a + (rnd[q] == 1u ? 1ull : rnd[q] == 2u ? ((P + a) & 1ull) : 0ull);
+                if (P >= E) {
+                    next_interval = true;
+                    break;
+                }
+                if (P > T) return __longlong_as_double((long long)(((uint64_t)(lg + d + 1023) << 52) |
+                                                                  (P & 0xFFFFFFFFFFFFFull)));
             }
             if (next_interval) break;
         }
@@ -182,14 +254,52 @@ __device__ double next_event_time_poisson(const LaneSim& c, uint64_t loc, double
     return -1.0;
 }
 
+// The same search with the points in integer arithmetic (see
+// coop_next_poisson_short): point i of interval k >= 1 is
+// P0 + (U dt / u rounded to the nearest integer, ties to even) in units
+// u = 2^(e-52) of the interval's binade, P0 = k 2^(52 - floor(log2 k)) even.
+// k = 0 goes to the binary64 form.
+__device__ double next_event_time_poisson_int(const LaneSim& c, uint64_t loc, double tau) {
+    const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
+    const int d = c.dt_log2;
+    uint64_t k = floor_div_pow2(tau_b, d);
+    if (k == 0ull) return next_event_time_poisson(c, loc, tau);
+    for (uint32_t iv = 0; iv < INTERVAL_LIMIT; ++iv) {
+        if (k >= (1ull << 52)) return -1.0;
+        const int lg = 63 - __clzll((long long)k);  // 0 .. 51
+        const int s = lg + 1;
+        const uint64_t P0 = k << (52 - lg);
+        const uint64_t ehi = (uint64_t)(lg + d + 1023) << 52;
+        const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, k, 0, TAG_INTERVAL);
+        const uint32_t N = guided_count(c.pois_cdf, c.pois_guide, c.pois_n, b0.lo);
+        uint64_t best = ~0ull;
+        auto consider = [&](uint64_t r) {
+            const uint64_t v = r >> 11;
+            const uint64_t fl = v >> s, rem = v & ((1ull << s) - 1ull), half = 1ull << (s - 1);
+            const uint64_t P = P0 + fl + ((rem > half || (rem == half && (fl & 1ull))) ? 1ull : 0ull);
+            const uint64_t pb = P < (1ull << 53) ? (ehi | (P & 0xFFFFFFFFFFFFFull)) : ehi + (1ull << 52);
+            if (pb > tau_b && pb < best) best = pb;
+        };
+        if (N >= 1) consider(b0.hi);
+        for (uint32_t j = 1; 2 * j <= N; ++j) {
+            const u64x2 bj = stream_block(c.sk0, c.sk1, loc, k, j, TAG_INTERVAL);
+            consider(bj.lo);
+            if (2 * j + 1 <= N) consider(bj.hi);
+        }
+        if (best != ~0ull) return __longlong_as_double((long long)best);
+        ++k;
+    }
+    return -1.0;
+}
+
 // the searches return a time >= 0, or -1 when they give up: a sign-bit test
 // rather than a binary64 compare, which is slow on B300 and on the chain
 __device__ __forceinline__ bool search_failed(double t) { return __double_as_longlong(t) < 0; }
 
 template <int WIDE>
 __device__ __forceinline__ double next_event_time(const LaneSim& c, uint64_t loc, double tau, const LnC& ln) {
-    if (c.sampler == 1) return next_event_time_poisson(c, loc, tau);
-    return c.lam1 ? next_event_time_exp<WIDE, true>(c, loc, tau, ln) : next_event_time_exp<WIDE, false>(c, loc, tau, ln);
+    if (c.sampler == 1) return next_event_time_poisson_int(c, loc, tau);
+    return c.lam1 ? next_event_time_exp_int<WIDE>(c, loc, tau, ln) : next_event_time_exp<WIDE, false>(c, loc, tau, ln);
 }
 
 // ---------------------------------------------------------------------------
@@ -416,16 +526,6 @@ __device__ double coop_next_exp_short_fp(const LaneSim& c, uint64_t loc, double 
         if (bal) return __shfl_sync(0xFFFFFFFFu, first, __ffs(bal) - 1);
     }
     return -1.0;
-}
-
-// q 2^-58 rounded to binary64 (53 significant bits, nearest, ties to even),
-// as the multiple of 2^-58 it equals (q < 2^63.5, so no overflow)
-__device__ __forceinline__ uint64_t rn53_q58(uint64_t q) {
-    const int lz = __clzll((long long)q);
-    if (lz >= 11) return q;  // below 2^53: exact
-    const int sh = 11 - lz;
-    const uint64_t mant = q >> sh, rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    return (mant + ((rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull)) << sh;
 }
 
 // The short search for lambda = 1 in integer arithmetic, with the same

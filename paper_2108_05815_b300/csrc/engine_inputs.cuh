@@ -157,18 +157,25 @@ __global__ void k_selftest(const uint64_t* __restrict__ in, uint64_t n, uint64_t
 
 // event-time search probe (sim_selftest_search): the first event time after
 // tau[q] at loc[q] by one search form; forms 0 and 1 one lane per query
-// (one or two draw blocks per step), 2 to 4 one warp per query (general,
-// short in binary64, short as the tail kernel runs it)
+// (one or two draw blocks per step, as the one-lane kernel runs them), 2 to
+// 4 one warp per query (general, short in binary64, short as the tail
+// kernel runs it), 5 one lane per query in binary64 throughout
 template <int FORM>
 __global__ void k_selftest_search(const SimParams* __restrict__ P, const SimState* S, const uint64_t* __restrict__ loc,
                                   const double* __restrict__ tau, uint64_t n, double* __restrict__ out) {
     LaneSim c;
     load_lanesim(c, P, S, 0);
     const LnC ln = ln_tables();
-    if (FORM <= 1) {
+    if (FORM <= 1 || FORM == 5) {
         for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n;
-             q += (uint64_t)gridDim.x * blockDim.x)
-            out[q] = next_event_time<FORM + 1>(c, loc[q], tau[q], ln);
+             q += (uint64_t)gridDim.x * blockDim.x) {
+            if (FORM == 5)
+                out[q] = c.sampler == 1 ? next_event_time_poisson(c, loc[q], tau[q])
+                         : c.lam1       ? next_event_time_exp<1, true>(c, loc[q], tau[q], ln)
+                                        : next_event_time_exp<1, false>(c, loc[q], tau[q], ln);
+            else
+                out[q] = next_event_time<FORM + 1>(c, loc[q], tau[q], ln);
+        }
         return;
     }
     const uint32_t lane = threadIdx.x & 31u;

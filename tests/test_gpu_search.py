@@ -1,9 +1,10 @@
 """GPU parity of the event-time searches, one query at a time.
 
 Every search form of the device (one lane per lineage, one or two draw
-blocks per step; the warp-cooperative general search; the short warp search
-in binary64; the short warp search as the tail kernel runs it, with integer
-sums for lambda = 1) must return, for any (location, tau), the first point
+blocks per step, as the one-lane kernel runs them with integer sums; the
+warp-cooperative general search; the short warp search in binary64; the
+short warp search as the tail kernel runs it, with integer sums for lambda
+= 1; the one-lane search in binary64 throughout) must return, for any (location, tau), the first point
 of that location's event process strictly after tau: the oracle's
 next_event_time, bit for bit.  The queries mix times in the first interval,
 small interval indices (where the integer sums meet rounding ties most
@@ -19,7 +20,7 @@ from paper_2108_05815_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-FORMS = (0, 1, 2, 3, 4)
+FORMS = (0, 1, 2, 3, 4, 5)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -105,7 +106,7 @@ def test_search_probe_rejects_bad_arguments():
     s = ind.Simulation(W.NONSPATIAL, 1e-3, 1, deme=10)
     try:
         with pytest.raises(ind.IndError):
-            s.selftest_search(5, np.zeros(1, np.uint64), np.zeros(1))
+            s.selftest_search(6, np.zeros(1, np.uint64), np.zeros(1))
         with pytest.raises(ind.IndError):
             s.selftest_search(0, np.zeros(0, np.uint64), np.zeros(0))
     finally:
