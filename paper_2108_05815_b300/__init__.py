@@ -308,7 +308,7 @@ class Simulation:
 
     def selftest_search(self, form, locs, taus):
         """device probe (sim_selftest_search): the first event time after each
-        taus[i] at locs[i] by search form 0..4, float64 numpy array"""
+        taus[i] at locs[i] by search form 0..5, float64 numpy array"""
         lv = np.ascontiguousarray(locs, dtype=np.uint64)
         tv = np.ascontiguousarray(taus, dtype=np.float64)
         assert lv.shape == tv.shape

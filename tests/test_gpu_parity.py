@@ -84,6 +84,20 @@ def test_device_exp_and_philox_bitexact():
     e, p = ind.selftest(v)
     for i in range(0, len(v), 97):
         assert int(e[i]) == O.exp1_q58(int(v[i]) >> 11), i
+    # every value of a set aimed at the logarithm's table buckets: U = (r + 1)
+    # 2^-53 just around bucket edges m = 1 + j 2^-12 for every binade
+    edges = []
+    for ex in range(0, 53):
+        for j in rng.integers(0, 4096, size=40):
+            base = (1 << ex) + ((int(j) << ex) >> 12)
+            for dlt in (-2, -1, 0, 1, 2):
+                r = base + dlt - 1
+                if 0 <= r < (1 << 53):
+                    edges.append(r << 11)
+    ev = np.array(edges, dtype=np.uint64)
+    ee, _ = ind.selftest(ev, want_philox=False)
+    want = np.array([O.exp1_q58(int(x) >> 11) for x in ev], dtype=np.uint64)
+    assert np.array_equal(ee, want)
     for i in range(0, len(v), 211):
         w, z = int(v[(i + 1) % len(v)]), int(v[(i + 2) % len(v)])
         key = [int(v[i]) & 0xFFFFFFFF, int(v[i]) >> 32]
