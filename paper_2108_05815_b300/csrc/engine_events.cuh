@@ -76,20 +76,12 @@ __device__ __forceinline__ LnC ln_tables_shared(unsigned char* smem) {
     return LnC{(const uint64_t*)smem, (const uint32_t*)(smem + sizeof(uint64_t) * LN_N), g_ln.ln2_q64, g_ln.c3};
 }
 
-// binary64 of q 2^-58: the hardware conversion rounds q to nearest even, and
-// the scaling by 2^-58 is exact (normal range), applied to the exponent field
-__device__ __forceinline__ double q58_to_double_hw(uint64_t q) {
-    if (q == 0ull) return 0.0;
-    const uint64_t b = (uint64_t)__double_as_longlong(__ull2double_rn(q));
-    return __longlong_as_double((long long)(b - (58ull << 52)));
-}
-
 // Exp(lambda) draw.  LAM1 (lambda = 1) is a template argument rather than a
 // select: given both operands the compiler evaluates the binary64 division
 // even where it is not used, on the latency chain and on B300's narrow FP64
 // pipe.  Callers branch on c.lam1 once per search.
-// the division out of line, for code whose lanes mix lambdas: a call is
-// not evaluated speculatively
+// div_rn_call: the division out of line, for code whose lanes mix lambdas
+// (a call is not evaluated speculatively)
 __device__ __noinline__ double div_rn_call(double x, double y) { return __ddiv_rn(x, y); }
 
 template <bool LAM1>
