@@ -15,6 +15,9 @@
       (--block-threads 64 --blocks-per-sm 1) leaves few idle warps beside the
       working one, so that a profiler's per-warp figures are its own
 
+  python -m paper_2108_05815_b300.cases implicit [--sampler ...]
+      the spatially implicit workload (local community of 10^5, migration
+      0.01, metacommunity of 10^9 with nu 1e-4) once, without CUDA graphs
   python -m paper_2108_05815_b300.cases alias [--reps 3]
       config 3's habitat map (1024 x 1024, 60 % habitable, demes 1..8) and
       its dispersal tables: sim_create builds one alias row of 797 offsets
@@ -53,6 +56,18 @@ def run_config2(ind, sampler, events=False):
         out.update(distinct_events=len(ev), coalescences=len(co))
     s.close()
     return out
+
+
+def run_implicit(ind, sampler):
+    c = W.implicit()
+    s = _sim(ind, c["kind"], c["nu"], c["seed"], sampler, dict(use_graph=0), deme=c["deme"],
+             migration=c["migration"], meta_size=c["meta_size"], meta_nu=c["meta_nu"])
+    s.sample()
+    assert s.run()
+    _, K = s.species()
+    st = s.stats()
+    s.close()
+    return dict(case="implicit", species=K, **{k: st[k] for k in ("rounds", "raw_events", "critical_events")})
 
 
 def run_busy(ind, sampler, rounds):
@@ -107,7 +122,7 @@ def run_alias(ind, reps):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["config2", "busy", "tail", "alias"])
+    ap.add_argument("case", choices=["config2", "busy", "tail", "alias", "implicit"])
     ap.add_argument("--sampler", default="exp", choices=sorted(SAMPLERS))
     ap.add_argument("--rounds", type=int, default=6)
     ap.add_argument("--events", action="store_true")
@@ -127,6 +142,8 @@ def main(argv=None):
         r = run_busy(ind, sampler, a.rounds)
     elif a.case == "alias":
         r = run_alias(ind, a.reps)
+    elif a.case == "implicit":
+        r = run_implicit(ind, sampler)
     else:
         launch = {}
         if a.block_threads:

@@ -206,7 +206,11 @@ static void fill_params(const ind_sim* m, const ind_tuning& tun, SimParams& p) {
     p.tail_events = tun.tail_events;
     p.busy_lineages = tun.busy_lineages;
     p.max_step_events = tun.max_step_events;
-    p.n_slots = (double)m->n_slots;
+    // indexed locations of the water level's occupancy term: the
+    // metacommunity's too in the spatially implicit model, where lineages
+    // that migrated rarely meet (with the local community alone the tail
+    // ran 339 short rounds instead of 19)
+    p.n_slots = (double)slot_span(m);
 }
 
 // dynamic shared memory a block may use, less what the kernel declares statically
