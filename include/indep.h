@@ -240,8 +240,12 @@ ind_status sim_sample(ind_sim* sim, double fraction, uint64_t sample_seed, uint6
  * hold, duplicates and one entry per deduplicated lineage included,
  * 1..2^31) or disable it (0).  Costs 36 bytes per
  * raw event plus 16 per lineage; a run that executes more events than the
- * capacity fails with IND_ERR_DEVICE.  Only sim_run logs: sim_batch_run and
- * srv_submit reject a simulation with a log (IND_ERR_ARG). */
+ * capacity fails with IND_ERR_DEVICE.  sim_run and sim_batch_run log; in a
+ * batch, every simulation has a log or none does (else IND_ERR_ARG), the
+ * batch shares one record of the summed capacities (at most 2^31), and each
+ * simulation receives its own events and coalescences, its lineages
+ * numbered as it samples them.  srv_submit rejects a simulation with a log
+ * (IND_ERR_ARG). */
 ind_status sim_set_event_log(ind_sim* sim, uint64_t capacity);
 
 /* After a logged run: the distinct events in (time, location) order and the

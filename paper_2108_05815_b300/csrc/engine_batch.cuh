@@ -372,11 +372,16 @@ static ind_status batch_build(Batch& b) {
             d.ev_used[t] = P.get<uint32_t>(ec);
         }
     }
-    // event log: one simulation per batch (sim_run)
+    // event log: every simulation of the batch has one, or none does; one
+    // shared record of their summed capacities
     uint64_t log_cap = 0;
-    for (auto* m : b.sims) log_cap = std::max(log_cap, m->log_cap);
+    uint32_t logged = 0;
+    for (auto* m : b.sims) {
+        log_cap += m->log_cap;
+        logged += m->log_cap ? 1u : 0u;
+    }
+    if (logged && (logged != b.n_sims || log_cap > (1ull << 31))) return IND_ERR_ARG;
     if (log_cap) {
-        if (b.n_sims != 1) return IND_ERR_ARG;
         for (int t = 0; t < 2; ++t)
             if (!(d.lin[t].tp = P.get<double>(n))) return IND_ERR_OOM;
         d.log.time = P.get<uint64_t>(log_cap);
@@ -711,27 +716,30 @@ static ind_status batch_finish(Batch& b) {
     return IND_OK;
 }
 
-// the logged run's record -> the distinct events and the coalescences
+// the logged run's record -> the distinct events and the coalescences of
+// every simulation of the batch
 static ind_status process_event_log(Batch& b) {
-    ind_sim* m = b.sims[0];
     cudaStream_t s = b.stream;
     Pool& T = b.scratch;
     const uint32_t sms = sm_count();
-    m->events.release_all();
-    m->events.stream = m->stream;
-    m->d_events = nullptr;
-    m->d_coal = nullptr;
-    m->n_events = m->n_coal = 0;
-    m->events_ready = false;
+    for (auto* m : b.sims) {
+        m->events.release_all();
+        m->events.stream = m->stream;
+        m->d_events = nullptr;
+        m->d_coal = nullptr;
+        m->n_events = m->n_coal = 0;
+        m->events_ready = false;
+    }
     unsigned long long n_log = 0;
     CK(cudaMemcpyAsync(&n_log, &b.d_g->log_n, sizeof(n_log), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (n_log > b.dev.log.cap) return IND_ERR_DEVICE;
     const uint32_t n = (uint32_t)n_log;
+    const bool multi = b.n_sims > 1;
     if (n) {
         // the log's order by stable radix passes, least significant field
-        // first (lineage, prior time, location, time); bytes that are equal
-        // in every entry are skipped
+        // first (lineage, prior time, location, time, and the simulation in
+        // a batch of several); bytes that are equal in every entry are skipped
         const uint32_t nb = (n + RS_TILE - 1) / RS_TILE;
         uint64_t* key0 = T.get<uint64_t>(n);
         uint64_t* key1 = T.get<uint64_t>(n);
@@ -745,8 +753,10 @@ static ind_status process_event_log(Batch& b) {
         uint32_t* coal = T.get<uint32_t>(n);
         uint32_t* incl_head = T.get<uint32_t>(n);
         uint32_t* incl_coal = T.get<uint32_t>(n);
+        uint32_t* lsim = multi ? T.get<uint32_t>(n) : nullptr;  // each log entry's simulation
+        uint32_t* isim = multi ? T.get<uint32_t>(n) : nullptr;  // each sorted item's simulation
         if (!key0 || !key1 || !val0 || !val1 || !counts || !offs || !d_bits || !items || !head || !coal ||
-            !incl_head || !incl_coal)
+            !incl_head || !incl_coal || (multi && (!lsim || !isim)))
             return IND_ERR_OOM;
         unsigned long long h_bits[8];
         for (int f = 0; f < 4; ++f) {
@@ -759,27 +769,43 @@ static ind_status process_event_log(Batch& b) {
         CK(cudaMemcpyAsync(h_bits, d_bits, sizeof(h_bits), cudaMemcpyDeviceToHost, s));
         k_iota<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(val0, n);
         CKL();
+        if (multi) {
+            k_ev_sim<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, n, b.d_gid_base, b.n_sims, lsim);
+            CKL();
+        }
         CK(cudaStreamSynchronize(s));
         ind_status st = IND_OK;
-        for (int f = 0; f < 4; ++f) {
-            const uint64_t varies = h_bits[2 * f] ^ h_bits[2 * f + 1];
-            if (!varies) continue;
-            k_ev_field<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, f, val0, n, key0);
-            CKL();
+        auto radix_passes = [&](uint64_t varies) -> ind_status {
             for (int shift = 0; shift < 64; shift += 8) {
                 if (!((varies >> shift) & 0xFFull)) continue;
                 k_rs_count<<<nb, RS_WARPS * 32, 0, s>>>(key0, n, shift, counts);
                 CKL();
-                if ((st = scan_u32(T, counts, offs, RS_RADIX * nb, false, s)) != IND_OK) return st;
+                ind_status rs = scan_u32(T, counts, offs, RS_RADIX * nb, false, s);
+                if (rs != IND_OK) return rs;
                 k_rs_scatter<<<nb, RS_WARPS * 32, 0, s>>>(key0, val0, n, shift, offs, key1, val1);
                 CKL();
                 std::swap(key0, key1);
                 std::swap(val0, val1);
             }
+            return IND_OK;
+        };
+        for (int f = 0; f < 4; ++f) {
+            const uint64_t varies = h_bits[2 * f] ^ h_bits[2 * f + 1];
+            if (!varies) continue;
+            k_ev_field<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, f, val0, n, key0);
+            CKL();
+            if ((st = radix_passes(varies)) != IND_OK) return st;
         }
-        k_ev_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, val0, n, items);
+        if (multi) {
+            k_ev_key_u32<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(lsim, val0, n, key0);
+            CKL();
+            uint64_t varies = 0;
+            for (uint32_t v = b.n_sims - 1u; v; v >>= 1) varies = (varies << 1) | 1ull;
+            if ((st = radix_passes(varies)) != IND_OK) return st;
+        }
+        k_ev_gather<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(b.dev.log, val0, n, items, lsim, isim);
         CKL();
-        k_ev_marks<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, head, coal);
+        k_ev_marks<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, isim, head, coal);
         CKL();
         if ((st = scan_u32(T, head, incl_head, n, true, s)) != IND_OK) return st;
         if ((st = scan_u32(T, coal, incl_coal, n, true, s)) != IND_OK) return st;
@@ -787,23 +813,60 @@ static ind_status process_event_log(Batch& b) {
         CK(cudaMemcpyAsync(&hn, incl_head + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&cn, incl_coal + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        m->d_events = m->events.get<ind_event>(std::max<uint32_t>(hn, 1u));
-        m->d_coal = m->events.get<ind_coalescence>(std::max<uint32_t>(cn, 1u));
+        // one simulation: straight into its buffers; several: into shared
+        // buffers in (simulation, time, location) order, then each
+        // simulation's range into its own
+        ind_sim* m0 = b.sims[0];
+        ind_event* ev_all = multi ? T.get<ind_event>(std::max<uint32_t>(hn, 1u))
+                                  : (m0->d_events = m0->events.get<ind_event>(std::max<uint32_t>(hn, 1u)));
+        ind_coalescence* co_all = multi ? T.get<ind_coalescence>(std::max<uint32_t>(cn, 1u))
+                                        : (m0->d_coal = m0->events.get<ind_coalescence>(std::max<uint32_t>(cn, 1u)));
         uint32_t* head_pos = T.get<uint32_t>(std::max<uint32_t>(hn, 1u));
-        if (!m->d_events || !m->d_coal || !head_pos) return IND_ERR_OOM;
+        if (!ev_all || !co_all || !head_pos) return IND_ERR_OOM;
         k_ev_events<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, head, incl_head, b.dev.log.target, head_pos,
-                                                               m->d_events);
+                                                               ev_all, isim, b.d_gid_base);
         CKL();
-        k_ev_targets<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, incl_head, b.dev.log.target, m->d_events);
+        k_ev_targets<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, incl_head, b.dev.log.target, ev_all);
         CKL();
         k_ev_coalescences<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(items, n, coal, incl_coal, incl_head, head_pos,
-                                                                     m->d_coal);
+                                                                     co_all, isim, b.d_gid_base);
         CKL();
-        CK(cudaStreamSynchronize(s));
-        m->n_events = hn;
-        m->n_coal = cn;
+        if (!multi) {
+            CK(cudaStreamSynchronize(s));
+            m0->n_events = hn;
+            m0->n_coal = cn;
+        } else {
+            uint32_t* ev_cnt = T.get<uint32_t>(b.n_sims);
+            uint32_t* co_cnt = T.get<uint32_t>(b.n_sims);
+            if (!ev_cnt || !co_cnt) return IND_ERR_OOM;
+            CK(cudaMemsetAsync(ev_cnt, 0, sizeof(uint32_t) * b.n_sims, s));
+            CK(cudaMemsetAsync(co_cnt, 0, sizeof(uint32_t) * b.n_sims, s));
+            k_ev_sim_counts<<<grid_for(n, 256, sms * 16), 256, 0, s>>>(head, coal, isim, n, ev_cnt, co_cnt);
+            CKL();
+            std::vector<uint32_t> he(b.n_sims), hc(b.n_sims);
+            CK(cudaMemcpyAsync(he.data(), ev_cnt, sizeof(uint32_t) * b.n_sims, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(hc.data(), co_cnt, sizeof(uint32_t) * b.n_sims, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            uint64_t eo = 0, co = 0;
+            for (uint32_t si = 0; si < b.n_sims; ++si) {
+                ind_sim* m = b.sims[si];
+                m->d_events = m->events.get<ind_event>(std::max<uint32_t>(he[si], 1u));
+                m->d_coal = m->events.get<ind_coalescence>(std::max<uint32_t>(hc[si], 1u));
+                if (!m->d_events || !m->d_coal) return IND_ERR_OOM;
+                if (he[si])
+                    CK(cudaMemcpyAsync(m->d_events, ev_all + eo, sizeof(ind_event) * he[si], cudaMemcpyDeviceToDevice, s));
+                if (hc[si])
+                    CK(cudaMemcpyAsync(m->d_coal, co_all + co, sizeof(ind_coalescence) * hc[si],
+                                       cudaMemcpyDeviceToDevice, s));
+                m->n_events = he[si];
+                m->n_coal = hc[si];
+                eo += he[si];
+                co += hc[si];
+            }
+            CK(cudaStreamSynchronize(s));
+        }
     }
-    m->events_ready = true;
+    for (auto* m : b.sims) m->events_ready = true;
     return IND_OK;
 }
 

@@ -302,31 +302,69 @@ __global__ void k_ev_bits(EventLog L, uint32_t n, unsigned long long* and_or /* 
     }
 }
 
-// the log in (time, location, prior time, lineage) order as sort items
-__global__ void k_ev_gather(EventLog L, const uint32_t* __restrict__ order, uint32_t n, SortItem* items) {
+// batches of several simulations: each entry's simulation, the last one
+// whose first lineage id is at or below the entry's lineage
+__global__ void k_ev_sim(EventLog L, uint32_t n, const uint32_t* __restrict__ gid_base, uint32_t n_sims,
+                         uint32_t* out) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = order[i];
-        items[i] = SortItem{L.time[k], L.loc[k], L.prior[k], ((unsigned long long)L.gid[k] << 32) | k};
+        const uint32_t g = L.gid[i];
+        uint32_t lo = 0, hi = n_sims;  // gid_base[lo] <= g < gid_base[hi] (hi: past the end)
+        while (hi - lo > 1u) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (gid_base[mid] <= g) lo = mid;
+            else hi = mid;
+        }
+        out[i] = lo;
     }
 }
 
-__global__ void k_ev_marks(const SortItem* __restrict__ x, uint32_t n, uint32_t* head, uint32_t* coal) {
+// radix key of the simulation field, through the current order
+__global__ void k_ev_key_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ order, uint32_t n,
+                             uint64_t* keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        keys[i] = src[order[i]];
+}
+
+// the log in (simulation, time, location, prior time, lineage) order as sort
+// items; isim (batches of several simulations) receives each item's
+// simulation
+__global__ void k_ev_gather(EventLog L, const uint32_t* __restrict__ order, uint32_t n, SortItem* items,
+                            const uint32_t* __restrict__ lsim, uint32_t* isim) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const bool h = i == 0 || x[i].a != x[i - 1].a || x[i].b != x[i - 1].b;
+        const uint32_t k = order[i];
+        items[i] = SortItem{L.time[k], L.loc[k], L.prior[k], ((unsigned long long)L.gid[k] << 32) | k};
+        if (isim) isim[i] = lsim[k];
+    }
+}
+
+// a new distinct event where (simulation, time, location) changes; a
+// coalescence where, within one event, the prior time changes
+__global__ void k_ev_marks(const SortItem* __restrict__ x, uint32_t n, const uint32_t* __restrict__ isim,
+                           uint32_t* head, uint32_t* coal) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool h = i == 0 || x[i].a != x[i - 1].a || x[i].b != x[i - 1].b || (isim && isim[i] != isim[i - 1]);
         head[i] = h ? 1u : 0u;
         coal[i] = (!h && x[i].c != x[i - 1].c) ? 1u : 0u;
     }
 }
 
+// a lineage id as its simulation numbers it (batches: less the simulation's
+// first global id)
+__device__ __forceinline__ uint32_t ev_lineage(const SortItem& x, uint32_t i, const uint32_t* __restrict__ isim,
+                                               const uint32_t* __restrict__ gid_base) {
+    const uint32_t g = (uint32_t)(x.d >> 32);
+    return isim ? g - gid_base[isim[i]] : g;
+}
+
 __global__ void k_ev_events(const SortItem* __restrict__ x, uint32_t n, const uint32_t* head,
                             const uint32_t* incl_head, const uint64_t* __restrict__ target, uint32_t* head_pos,
-                            ind_event* out) {
+                            ind_event* out, const uint32_t* __restrict__ isim, const uint32_t* __restrict__ gid_base) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (!head[i]) continue;
         const uint32_t g = incl_head[i] - 1u;
         head_pos[g] = i;
         const uint32_t idx = (uint32_t)x[i].d;
-        out[g] = ind_event{x[i].a, x[i].c, x[i].b, target[idx], (uint32_t)(x[i].d >> 32), 0u};
+        out[g] = ind_event{x[i].a, x[i].c, x[i].b, target[idx], ev_lineage(x[i], i, isim, gid_base), 0u};
     }
 }
 
@@ -342,11 +380,23 @@ __global__ void k_ev_targets(const SortItem* __restrict__ x, uint32_t n, const u
 
 __global__ void k_ev_coalescences(const SortItem* __restrict__ x, uint32_t n, const uint32_t* coal,
                                   const uint32_t* incl_coal, const uint32_t* incl_head, const uint32_t* head_pos,
-                                  ind_coalescence* out) {
+                                  ind_coalescence* out, const uint32_t* __restrict__ isim,
+                                  const uint32_t* __restrict__ gid_base) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (!coal[i]) continue;
-        const uint32_t parent = (uint32_t)(x[head_pos[incl_head[i] - 1u]].d >> 32);
-        out[incl_coal[i] - 1u] = ind_coalescence{x[i].b, x[i].c, parent, (uint32_t)(x[i].d >> 32)};
+        const uint32_t hp = head_pos[incl_head[i] - 1u];
+        out[incl_coal[i] - 1u] = ind_coalescence{x[i].b, x[i].c, ev_lineage(x[hp], hp, isim, gid_base),
+                                                 ev_lineage(x[i], i, isim, gid_base)};
+    }
+}
+
+// batches: distinct events and coalescences per simulation
+__global__ void k_ev_sim_counts(const uint32_t* __restrict__ head, const uint32_t* __restrict__ coal,
+                                const uint32_t* __restrict__ isim, uint32_t n, uint32_t* ev_count,
+                                uint32_t* co_count) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (head[i]) atomicAdd(ev_count + isim[i], 1u);
+        if (coal[i]) atomicAdd(co_count + isim[i], 1u);
     }
 }
 

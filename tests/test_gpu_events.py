@@ -143,7 +143,8 @@ def test_event_log_capacity_and_state():
     with pytest.raises(ind.IndError):
         s.run()
     s.close()
-    # a logged simulation is not accepted by a batch of several or by the server
+    # a batch mixing logged and unlogged simulations is refused, and so is a
+    # logged simulation by the server
     a = ind.Simulation(cfg["kind"], cfg["nu"], 1, deme=cfg["deme"])
     b = ind.Simulation(cfg["kind"], cfg["nu"], 2, deme=cfg["deme"])
     a.set_event_log(1 << 20)
@@ -157,3 +158,55 @@ def test_event_log_capacity_and_state():
     srv.close()
     a.close()
     b.close()
+
+
+def verify(cfg, sampler, gev, gco, gkl, gkt):
+    """check() for a stream obtained another way (a batch)"""
+    m, locs, okl, okt, U, oev, oco = oracle(cfg, sampler)
+    assert np.array_equal(gkl, okl) and np.array_equal(gkt, okt)
+    assert len(gev) == U
+    for f in ("time_bits", "loc", "prior_bits", "target"):
+        assert np.array_equal(gev[f], oev[f]), f
+    g = sorted(zip(gco["time_bits"].tolist(), gco["loc"].tolist()))
+    o = sorted(zip(oco["time_bits"].tolist(), oco["loc"].tolist()))
+    assert g == o
+    rng = np.random.default_rng(1)
+    for k in rng.choice(len(gev), size=min(100, len(gev)), replace=False):
+        tl, tt = m.trace_log(int(locs[int(gev["lineage"][k])]))
+        assert np.any((tt == gev["time_bits"][k]) & (tl == gev["loc"][k]))
+    for k in range(min(50, len(gco))):
+        cl, ct = m.trace_log(int(locs[int(gco["child"][k])]))
+        j = int(np.nonzero(ct == gco["time_bits"][k])[0][0])
+        assert cl[j + 1] == gco["loc"][k]
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_event_stream_of_a_batch(sampler):
+    """a batch of logged simulations of every landscape kind: each receives
+    the stream the oracle gives it alone, lineages numbered as it samples
+    them"""
+    cfgs = CFGS[:4]
+    caps = []
+    for cfg in cfgs:
+        _, _, _, _, st = gpu(cfg, sampler, None, cap=0)
+        caps.append(st["raw_events"] + st["n_sampled"] + 64)
+    sims = []
+    for cfg, cap in zip(cfgs, caps):
+        s = ind.Simulation(cfg["kind"], cfg["nu"], cfg["seed"], width=cfg.get("width", 1),
+                           height=cfg.get("height", 1), deme=cfg.get("deme", 1), sigma=cfg.get("sigma", 0.0),
+                           radius=cfg.get("radius", 0), deme_map=deme_map() if cfg["kind"] == W.MAP else None,
+                           sampler=sampler, migration=cfg.get("migration", 0.0), meta_size=cfg.get("meta_size", 0),
+                           meta_nu=cfg.get("meta_nu", 0.0))
+        s.set_event_log(cap)
+        s.sample()
+        sims.append(s)
+    ind.batch_run(sims)
+    try:
+        for cfg, s in zip(cfgs, sims):
+            ev, co = s.events()
+            kl, kt = s.species_keys()
+            verify(cfg, sampler, ev, co, kl, kt)
+    finally:
+        for s in sims:
+            s.close()
+
