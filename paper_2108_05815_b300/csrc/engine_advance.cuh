@@ -437,7 +437,19 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     const uint32_t wg = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     if (blockIdx.x >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
-    if (wg >= n) return;  // after the block's table copy
+    // the shared Poisson tables, if every simulation has the same
+    const uint32_t* pguide = nullptr;
+    const uint64_t* pcdf = nullptr;
+    if (B.pois_guide) {
+        uint32_t* g = (uint32_t*)(adv_smem + B.pois_off);
+        uint64_t* cdf = (uint64_t*)(g + GUIDE_N);
+        for (uint32_t k = threadIdx.x; k < GUIDE_N; k += blockDim.x) g[k] = __ldg(B.pois_guide + k);
+        for (uint32_t k = threadIdx.x; k < B.pois_n; k += blockDim.x) cdf[k] = __ldg(B.pois_cdf + k);
+        __syncthreads();
+        pguide = g;
+        pcdf = cdf;
+    }
+    if (wg >= n) return;  // after the block's table copies
     const uint32_t t = B.G->round & 1u;
     const LinPtrs L = B.lin[t];
     const uint32_t lane = threadIdx.x & 31u;
@@ -463,6 +475,10 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         const uint32_t s = L.sim[idx];
         LaneSim c;
         load_lanesim(c, B.P, B.S, s);
+        if (pguide) {
+            c.pois_guide = pguide;
+            c.pois_cdf = pcdf;
+        }
         if (s != cnt_sim) {
             if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
                 atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);

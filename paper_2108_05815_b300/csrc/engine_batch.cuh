@@ -425,13 +425,39 @@ static ind_status batch_build(Batch& b) {
     for (auto* m : b.sims)
         if (m->land.kind == IND_MAP) n_off_max = std::max(n_off_max, m->n_off);
     const size_t ln_bytes = d.need_ln ? LN_SMEM_BYTES : 0;
-    b.coop_smem = ln_bytes;
+    // Poisson points: when every simulation draws them from the same
+    // tables (the same lambda dt), the warp kernel reads the guide and the
+    // thresholds from shared memory; the guide lookup is on the chain of
+    // every event
+    size_t pois_bytes = 0;
+    d.pois_guide = nullptr;
+    d.pois_cdf = nullptr;
+    d.pois_n = 0;
+    d.pois_off = (uint32_t)ln_bytes;
+    {
+        const ind_sim* first = nullptr;
+        bool same = true;
+        for (auto* m : b.sims) {
+            if (m->land.event_sampler != IND_SAMPLER_POISSON) continue;
+            if (!first) first = m;
+            else if (m->land.lambda * m->land.delta_t != first->land.lambda * first->land.delta_t ||
+                     m->pois_n != first->pois_n)
+                same = false;
+        }
+        if (first && same) {
+            d.pois_guide = first->d_pois_guide;
+            d.pois_cdf = first->d_pois;
+            d.pois_n = first->pois_n;
+            pois_bytes = sizeof(uint32_t) * GUIDE_N + (((size_t)first->pois_n * 8 + 15) & ~(size_t)15);
+        }
+    }
+    b.coop_smem = ln_bytes + pois_bytes;
     d.stage_off = d.stage_bytes = 0;
     if (n_off_max) {
         const size_t per = ((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15;  // a row from a 16-byte boundary
-        const size_t total = ln_bytes + (size_t)(b.tun.block_threads / 32) * per;
+        const size_t total = b.coop_smem + (size_t)(b.tun.block_threads / 32) * per;
         if (total <= coop_smem_limit()) {
-            d.stage_off = (uint32_t)ln_bytes;
+            d.stage_off = (uint32_t)b.coop_smem;
             d.stage_bytes = (uint32_t)per;
             b.coop_smem = total;
         }

@@ -205,13 +205,14 @@ __device__ double next_event_time_exp_int(const LaneSim& c, uint64_t loc, double
 }
 
 // number of table entries <= r: the guide entry of r's bucket, and a scan
-// of the table only where a threshold falls inside the bucket
+// of the table only where a threshold falls inside the bucket (plain loads:
+// the warp kernel may pass tables staged in shared memory)
 __device__ __forceinline__ uint32_t guided_count(const uint64_t* __restrict__ t, const uint32_t* __restrict__ guide,
                                                  uint32_t n, uint64_t r) {
-    const uint32_t e = __ldg(guide + (r >> (64 - GUIDE_BITS)));
+    const uint32_t e = guide[r >> (64 - GUIDE_BITS)];
     uint32_t idx = e & ~GUIDE_SCAN;
     if (e & GUIDE_SCAN)
-        while (idx < n && __ldg(t + idx) <= r) ++idx;
+        while (idx < n && t[idx] <= r) ++idx;
     return idx;
 }
 

@@ -348,6 +348,9 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     d.count_unique = 0;  // exact counting is a batch-only measurement mode
     d.need_ln = 1;       // requests of either sampler may arrive
     d.stage_off = d.stage_bytes = 0;  // alias rows of map requests are read from global memory
+    d.pois_guide = nullptr;           // requests of any lambda dt: each reads its own tables
+    d.pois_cdf = nullptr;
+    d.pois_n = d.pois_off = 0;
     b.coop_smem = LN_SMEM_BYTES;
     auto fail = [&](cudaError_t e) {
         g_last_cuda_error.store((int)e);

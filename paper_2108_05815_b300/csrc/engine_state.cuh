@@ -230,6 +230,10 @@ struct BatchDev {
     int need_ln;  // some simulation uses the exponential-sums sampler
     uint32_t events_per_visit;
     uint32_t coop_lineages;  // a round with at most this many active lineages runs one warp per lineage
+    const uint32_t* pois_guide;  // warp kernel: the Poisson guide and thresholds every simulation shares,
+    const uint64_t* pois_cdf;    // staged in shared memory at pois_off (null: each simulation's own)
+    uint32_t pois_n;
+    uint32_t pois_off;
     uint32_t stage_off;      // warp kernel: shared-memory offset of the per-warp alias-row buffers
     uint32_t stage_bytes;    // bytes of one such buffer (0: map rows are read from global memory)
     EventLog log;            // cap 0: no logging
