@@ -438,16 +438,29 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     if (blockIdx.x >= n) return;
     const LnC ln = B.need_ln ? ln_tables_shared(adv_smem) : ln_tables();
     // the shared Poisson tables, if every simulation has the same
+    // and the torus's dispersal tables, likewise
     const uint32_t* pguide = nullptr;
     const uint64_t* pcdf = nullptr;
-    if (B.pois_guide) {
-        uint32_t* g = (uint32_t*)(adv_smem + B.pois_off);
-        uint64_t* cdf = (uint64_t*)(g + GUIDE_N);
-        for (uint32_t k = threadIdx.x; k < GUIDE_N; k += blockDim.x) g[k] = __ldg(B.pois_guide + k);
-        for (uint32_t k = threadIdx.x; k < B.pois_n; k += blockDim.x) cdf[k] = __ldg(B.pois_cdf + k);
+    const uint32_t* gguide = nullptr;
+    const uint64_t* gcdf = nullptr;
+    if (B.pois_guide || B.gauss_guide) {
+        if (B.pois_guide) {
+            uint32_t* g = (uint32_t*)(adv_smem + B.pois_off);
+            uint64_t* cdf = (uint64_t*)(g + GUIDE_N);
+            for (uint32_t k = threadIdx.x; k < GUIDE_N; k += blockDim.x) g[k] = __ldg(B.pois_guide + k);
+            for (uint32_t k = threadIdx.x; k < B.pois_n; k += blockDim.x) cdf[k] = __ldg(B.pois_cdf + k);
+            pguide = g;
+            pcdf = cdf;
+        }
+        if (B.gauss_guide) {
+            uint32_t* g = (uint32_t*)(adv_smem + B.gauss_off);
+            uint64_t* cdf = (uint64_t*)(g + GUIDE_N);
+            for (uint32_t k = threadIdx.x; k < GUIDE_N; k += blockDim.x) g[k] = __ldg(B.gauss_guide + k);
+            for (uint32_t k = threadIdx.x; k < B.gauss_n; k += blockDim.x) cdf[k] = __ldg(B.gauss_cdf + k);
+            gguide = g;
+            gcdf = cdf;
+        }
         __syncthreads();
-        pguide = g;
-        pcdf = cdf;
     }
     if (wg >= n) return;  // after the block's table copies
     const uint32_t t = B.G->round & 1u;
@@ -478,6 +491,10 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         if (pguide) {
             c.pois_guide = pguide;
             c.pois_cdf = pcdf;
+        }
+        if (gguide && c.kind == KIND_TORUS) {
+            c.gauss_guide = gguide;
+            c.gauss = gcdf;
         }
         if (s != cnt_sim) {
             if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {

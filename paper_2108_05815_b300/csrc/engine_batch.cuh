@@ -451,7 +451,30 @@ static ind_status batch_build(Batch& b) {
             pois_bytes = sizeof(uint32_t) * GUIDE_N + (((size_t)first->pois_n * 8 + 15) & ~(size_t)15);
         }
     }
-    b.coop_smem = ln_bytes + pois_bytes;
+    // likewise the torus's discretised-normal guide and thresholds when every
+    // torus simulation has the same sigma (its guide lookups are on the
+    // chain of every dispersal)
+    size_t gauss_bytes = 0;
+    d.gauss_guide = nullptr;
+    d.gauss_cdf = nullptr;
+    d.gauss_n = 0;
+    d.gauss_off = (uint32_t)(ln_bytes + pois_bytes);
+    {
+        const ind_sim* first = nullptr;
+        bool same = true;
+        for (auto* m : b.sims) {
+            if (m->land.kind != IND_TORUS) continue;
+            if (!first) first = m;
+            else if (m->disp.sigma != first->disp.sigma || m->gauss_n != first->gauss_n) same = false;
+        }
+        if (first && same) {
+            d.gauss_guide = first->d_gauss_guide;
+            d.gauss_cdf = first->d_gauss;
+            d.gauss_n = first->gauss_n;
+            gauss_bytes = sizeof(uint32_t) * GUIDE_N + (((size_t)first->gauss_n * 8 + 15) & ~(size_t)15);
+        }
+    }
+    b.coop_smem = ln_bytes + pois_bytes + gauss_bytes;
     d.stage_off = d.stage_bytes = 0;
     if (n_off_max) {
         const size_t per = ((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15;  // a row from a 16-byte boundary

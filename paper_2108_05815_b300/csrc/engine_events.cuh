@@ -659,14 +659,15 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     if (kind == KIND_TORUS) {
         // both guide entries first, so that the two loads overlap; a table
         // scan only for draws in a bucket that holds a threshold
-        const uint32_t ex = __ldg(c.gauss_guide + (d1 >> (64 - GUIDE_BITS)));
-        const uint32_t ey = __ldg(c.gauss_guide + (d2 >> (64 - GUIDE_BITS)));
+        // (plain loads: the warp kernel may pass tables staged in shared memory)
+        const uint32_t ex = c.gauss_guide[d1 >> (64 - GUIDE_BITS)];
+        const uint32_t ey = c.gauss_guide[d2 >> (64 - GUIDE_BITS)];
         uint32_t cx = ex & ~GUIDE_SCAN, cy = ey & ~GUIDE_SCAN;
         if ((ex | ey) & GUIDE_SCAN) {
             if (ex & GUIDE_SCAN)
-                while (cx < c.gauss_n && __ldg(c.gauss + cx) <= d1) ++cx;
+                while (cx < c.gauss_n && c.gauss[cx] <= d1) ++cx;
             if (ey & GUIDE_SCAN)
-                while (cy < c.gauss_n && __ldg(c.gauss + cy) <= d2) ++cy;
+                while (cy < c.gauss_n && c.gauss[cy] <= d2) ++cy;
         }
         const uint32_t tx = wrap_add(x, (int32_t)cx - c.gauss_half, c.W);
         const uint32_t ty = wrap_add(y, (int32_t)cy - c.gauss_half, c.H);

@@ -351,6 +351,9 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     d.pois_guide = nullptr;           // requests of any lambda dt: each reads its own tables
     d.pois_cdf = nullptr;
     d.pois_n = d.pois_off = 0;
+    d.gauss_guide = nullptr;
+    d.gauss_cdf = nullptr;
+    d.gauss_n = d.gauss_off = 0;
     b.coop_smem = LN_SMEM_BYTES;
     auto fail = [&](cudaError_t e) {
         g_last_cuda_error.store((int)e);

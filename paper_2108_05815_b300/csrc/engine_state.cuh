@@ -234,6 +234,10 @@ struct BatchDev {
     const uint64_t* pois_cdf;    // staged in shared memory at pois_off (null: each simulation's own)
     uint32_t pois_n;
     uint32_t pois_off;
+    const uint32_t* gauss_guide;  // likewise the torus dispersal tables (the same sigma everywhere)
+    const uint64_t* gauss_cdf;
+    uint32_t gauss_n;
+    uint32_t gauss_off;
     uint32_t stage_off;      // warp kernel: shared-memory offset of the per-warp alias-row buffers
     uint32_t stage_bytes;    // bytes of one such buffer (0: map rows are read from global memory)
     EventLog log;            // cap 0: no logging
