@@ -443,7 +443,13 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     const uint64_t* pcdf = nullptr;
     const uint32_t* gguide = nullptr;
     const uint64_t* gcdf = nullptr;
-    if (B.pois_guide || B.gauss_guide) {
+    const int8_t* otab = nullptr;
+    if (B.pois_guide || B.gauss_guide || B.off_tab) {
+        if (B.off_tab) {
+            int8_t* o = (int8_t*)(adv_smem + B.off_off);
+            for (uint32_t k = threadIdx.x; k < 2u * B.off_n; k += blockDim.x) o[k] = B.off_tab[k];
+            otab = o;
+        }
         if (B.pois_guide) {
             uint32_t* g = (uint32_t*)(adv_smem + B.pois_off);
             uint64_t* cdf = (uint64_t*)(g + GUIDE_N);
@@ -496,6 +502,7 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             c.gauss_guide = gguide;
             c.gauss = gcdf;
         }
+        if (otab && c.kind == KIND_MAP) c.off = otab;
         if (s != cnt_sim) {
             if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
                 atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);

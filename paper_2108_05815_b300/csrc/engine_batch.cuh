@@ -474,7 +474,27 @@ static ind_status batch_build(Batch& b) {
             gauss_bytes = sizeof(uint32_t) * GUIDE_N + (((size_t)first->gauss_n * 8 + 15) & ~(size_t)15);
         }
     }
-    b.coop_smem = ln_bytes + pois_bytes + gauss_bytes;
+    // and the map's offset table when every map simulation has the same
+    // kernel radius (the same number of offsets)
+    size_t off_bytes = 0;
+    d.off_tab = nullptr;
+    d.off_n = 0;
+    d.off_off = (uint32_t)(ln_bytes + pois_bytes + gauss_bytes);
+    {
+        const ind_sim* first = nullptr;
+        bool same = true;
+        for (auto* m : b.sims) {
+            if (m->land.kind != IND_MAP) continue;
+            if (!first) first = m;
+            else if (m->n_off != first->n_off) same = false;
+        }
+        if (first && same) {
+            d.off_tab = first->d_off;
+            d.off_n = first->n_off;
+            off_bytes = ((size_t)first->n_off * 2 + 15) & ~(size_t)15;
+        }
+    }
+    b.coop_smem = ln_bytes + pois_bytes + gauss_bytes + off_bytes;
     d.stage_off = d.stage_bytes = 0;
     if (n_off_max) {
         const size_t per = ((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15;  // a row from a 16-byte boundary

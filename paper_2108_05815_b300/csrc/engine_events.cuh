@@ -25,6 +25,11 @@ struct LaneSim {
     uint32_t gauss_n;
     const uint64_t* gauss;
     const uint32_t* gauss_guide;
+    // spatially implicit model
+    uint64_t meta_size, m_thr, meta_nu_thr;
+    // habitat map: offsets of the dispersal kernel and their count
+    uint32_t n_off;
+    const int8_t* off;
 };
 
 __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
@@ -50,6 +55,11 @@ __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __rest
     c.gauss_n = __ldg(&p->gauss_n);
     c.gauss = p->gauss;
     c.gauss_guide = p->gauss_guide;
+    c.meta_size = __ldg(&p->meta_size);
+    c.m_thr = __ldg(&p->m_thr);
+    c.meta_nu_thr = __ldg(&p->meta_nu_thr);
+    c.n_off = __ldg(&p->n_off);
+    c.off = p->off;
     c.horizon = *(volatile const double*)&S[sim].horizon;
 }
 
@@ -650,9 +660,9 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
         // in the metacommunity: a uniform parent there (d1); locally:
         // migration iff d1 says so, then the parent's index (d2) in the
         // metacommunity or the local community
-        const uint64_t meta_n = __ldg(&p->meta_size);
+        const uint64_t meta_n = c.meta_size;
         if (in_meta(loc)) return meta_loc(umulhi64(d1, meta_n));
-        if ((d1 >> 11) < __ldg(&p->m_thr)) return meta_loc(umulhi64(d2, meta_n));
+        if ((d1 >> 11) < c.m_thr) return meta_loc(umulhi64(d2, meta_n));
         return pack_loc(0, 0, umulhi64(d2, c.D));
     }
     const uint32_t x = loc_x(loc), y = loc_y(loc);
@@ -676,14 +686,14 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     }
     // habitat map: one load of the origin cell's alias entry, which also
     // carries the target deme (k_alias_build), then the offset table (L1)
-    const uint32_t n_off = __ldg(&p->n_off);
+    const uint32_t n_off = c.n_off;
     const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
     const uint64_t e = srow ? srow[col] : __ldg(p->alias + ((size_t)y * c.W + x) * n_off + col);
     const uint32_t u = (uint32_t)d1;
     const bool take_col = (e >> 63) != 0 || u < (uint32_t)e;
     const uint32_t o = take_col ? col : (uint32_t)((e >> 32) & (ALIAS_MAX_OFFSETS - 1u));
     const uint32_t d = (uint32_t)(e >> (take_col ? 45 : 53)) & 0xFFu;
-    const int8_t* off = p->off;
+    const int8_t* off = c.off;  // plain loads: the warp kernel may stage the table in shared memory
     const int32_t dx = off[2 * o], dy = off[2 * o + 1];
     const uint32_t tx = wrap_add(x, dx, c.W);
     const uint32_t ty = wrap_add(y, dy, c.H);
@@ -735,7 +745,7 @@ __device__ __forceinline__ void alias_row_wait() {
 // implicit model, else the simulation's
 __device__ __forceinline__ uint64_t spec_thr(const LaneSim& c, const SimParams* __restrict__ P, int kind,
                                              uint64_t loc) {
-    return (kind == KIND_IMPLICIT && in_meta(loc)) ? __ldg(&P[c.sim].meta_nu_thr) : c.nu_thr;
+    return (kind == KIND_IMPLICIT && in_meta(loc)) ? c.meta_nu_thr : c.nu_thr;
 }
 
 // one event at (loc, tau); returns true if the lineage speciated, else

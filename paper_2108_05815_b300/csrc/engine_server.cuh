@@ -354,6 +354,8 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     d.gauss_guide = nullptr;
     d.gauss_cdf = nullptr;
     d.gauss_n = d.gauss_off = 0;
+    d.off_tab = nullptr;
+    d.off_n = d.off_off = 0;
     b.coop_smem = LN_SMEM_BYTES;
     auto fail = [&](cudaError_t e) {
         g_last_cuda_error.store((int)e);

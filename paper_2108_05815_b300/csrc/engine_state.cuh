@@ -238,6 +238,9 @@ struct BatchDev {
     const uint64_t* gauss_cdf;
     uint32_t gauss_n;
     uint32_t gauss_off;
+    const int8_t* off_tab;        // likewise the map's dispersal offsets (the same radius everywhere)
+    uint32_t off_n;
+    uint32_t off_off;
     uint32_t stage_off;      // warp kernel: shared-memory offset of the per-warp alias-row buffers
     uint32_t stage_bytes;    // bytes of one such buffer (0: map rows are read from global memory)
     EventLog log;            // cap 0: no logging
