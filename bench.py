@@ -60,6 +60,8 @@ def parse():
                     help="event-time sampler of the headline (the other is reported beside it)")
     ap.add_argument("--window", type=float, default=60.0, help="served: arrival window in seconds")
     ap.add_argument("--plain-subset", type=int, default=32, help="batch: simulations timed one by one")
+    ap.add_argument("--served-plain", type=int, default=16,
+                    help="served: requests re-run one by one on the plain path (0: none)")
     ap.add_argument("--events", action="store_true",
                     help="single workloads: every step also produces the full event stream (distinct events and "
                          "coalescences) on the device")
@@ -577,7 +579,7 @@ def run_served(args, rank, world, local, pg):
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ind.kernel_launches()
-    sims, lat, arrival, tickets = {}, [], {}, {}
+    sims, lat, arrival, index, lat_of = {}, [], {}, {}, {}
     nxt, done = 0, 0
     t0 = time.perf_counter()
     raw = 0
@@ -591,6 +593,7 @@ def run_served(args, rank, world, local, pg):
             tk = srv.submit(x)
             sims[tk] = x
             arrival[tk] = r["arrival"]
+            index[tk] = nxt
             nxt += 1
         fin = srv.step(4)
         t_now = time.perf_counter() - t0
@@ -599,6 +602,7 @@ def run_served(args, rank, world, local, pg):
             x.species()
             raw += x.stats()["raw_events"]
             lat.append(time.perf_counter() - t0 - arrival[tk])
+            lat_of[index[tk]] = lat[-1]
             x.close()
             done += 1
         if not fin and srv.stats()["resident"] == 0 and nxt < len(reqs):
@@ -607,6 +611,7 @@ def run_served(args, rank, world, local, pg):
     clk = clocks.stop()
     st = srv.stats()
     srv.close()
+    plain = served_plain(ind, torch, reqs, lat_of, total, args.served_plain) if args.served_plain > 0 else None
     line = {
         "metric": METRIC, "value": raw / total, "unit": "raw events/s", "n_gpus": world, "steps": 1,
         "warmup": 0, "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -616,10 +621,42 @@ def run_served(args, rank, world, local, pg):
                                % args.window, "requests": len(reqs), "event_sampler": args.sampler},
         "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat),
                       "what": "arrival to species identities on the device"},
-        "server": st, "clocks": clk, "gpu_launches": ind.kernel_launches() - launches0,
+        "plain": plain, "server": st, "clocks": clk, "gpu_launches": ind.kernel_launches() - launches0,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def served_plain(ind, torch, reqs, lat_of, total_s, n):
+    """the plain path on a subset of the served requests, stratified by nu:
+    each request alone, sim_create + sim_sample + sim_run + sim_species one
+    after another on an idle GPU.  Scaled to all requests, the sum of these
+    times is how long a server running one simulation at a time would need
+    for the same work; per request, the served latency over the time alone
+    is what sharing the GPU cost it"""
+    order = sorted(range(len(reqs)), key=lambda k: reqs[k]["nu"])
+    stride = max(1, len(reqs) // n)
+    subset = order[stride // 2::stride][:n]
+    alone, ratio = 0.0, []
+    for k in subset:
+        r = reqs[k]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = _make_from(ind, r, None, _sampler)
+        x.sample(r["fraction"], r["sample_seed"])
+        x.run()
+        x.species()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        x.close()
+        alone += dt
+        ratio.append(lat_of[k] / dt)
+    est = alone * len(reqs) / len(subset)
+    return {"requests_timed": len(subset), "seconds_alone": alone, "seconds_all_estimated": est,
+            "speedup": est / total_s, "served_over_alone": {"p50": pct(ratio, 50), "max": max(ratio)},
+            "what": "each request alone on the plain path (sample, run, species), %d of %d stratified by nu; "
+                    "speedup = their summed time scaled to all requests / the served run's wall time; "
+                    "served_over_alone = a request's served latency / its time alone" % (len(subset), len(reqs))}
 
 
 # --------------------------------------------------------------------------

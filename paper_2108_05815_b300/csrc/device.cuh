@@ -207,21 +207,6 @@ __device__ __forceinline__ uint32_t wrap_add(uint32_t x, int32_t d, uint32_t n) 
     return (uint32_t)(r < 0 ? r + (int32_t)n : r);
 }
 
-// number of table entries <= r (table nondecreasing, length n)
-__device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* __restrict__ t, uint32_t n, uint64_t r) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        uint32_t half = len >> 1;
-        if (t[lo + half] <= r) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     // splitmix64 finaliser (Steele, Lea, Flood 2014)
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
