@@ -363,6 +363,12 @@ def run_ours(args, rank, world, local, pg):
                "frac": lone_ns / crit_ns,
                "what": "step time / (sum over rounds of the most events one lineage ran in the round), against "
                        "the advance-kernel time per event of a few lineages alone on the same landscape"}
+    longest = longest_chain(args.workload, args.sampler)
+    if longest:
+        # no schedule runs the workload in fewer dependent events than its
+        # longest lineage: that many lone-lineage events is the step's floor
+        latency.update({"longest_lineage_events": longest, "chain_floor_ms": longest * lone_ns * 1e-6,
+                        "frac_of_chain_floor": longest * lone_ns * 1e-6 / ms_step})
 
     # roofline of the advance kernel (events per launch / its CUDA-event time)
     raw_per_step = raw / args.steps
@@ -439,6 +445,20 @@ def ops_per_raw_event(sampler=None):
     if sampler == 1:
         return event + 1.6 * (PHILOX_OPS + COUNT_OPS + 1.0 * POINT_OPS)
     return event + 1.35 * PHILOX_OPS + 2.7 * EXP_DRAW_OPS
+
+
+def longest_chain(workload, sampler):
+    """the most events one sampled lineage of the workload (seed 42, all
+    sampled) runs before it speciates: the oracle's mode P traces, stored
+    in the test fixtures by the script that wrote them; None if not stored"""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "longest_chains.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) == 5 and f[0] == workload and f[1] == sampler and f[2] == "42":
+            return int(f[4])
+    return None
 
 
 def busiest(st, ops, peak):

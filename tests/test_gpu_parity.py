@@ -5,6 +5,7 @@ time), dense species identities and species counts are integers, so the
 tolerance is zero.  Inputs are seeded and synthetic (see workloads.py).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -442,3 +443,32 @@ def test_alias_rows_equal_oracle():
             s.alias_row(int(empty % W_), int(empty // W_))
     finally:
         s.close()
+
+
+def _longest_chains():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "longest_chains.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        w, s, seed, n, best = line.split()
+        rows[(w, s)] = (int(seed), int(n), int(best))
+    return rows
+
+
+@pytest.mark.parametrize("tuning", [None, dict(coop_lineages=0), dict(coop_lineages=1 << 30),
+                                    dict(max_step_events=3.0, tail_events=8.0)])
+@pytest.mark.parametrize("sampler", [0, 1])
+@pytest.mark.parametrize("workload", ["config1", "config2"])
+def test_critical_chain_not_below_longest_lineage(workload, sampler, tuning):
+    """Between horizons a lineage's events are run by one lineage of the
+    round (merges happen only at horizons), so the events of any one
+    sampled individual's trace that fall in a round are at most the round's
+    most events on one lineage.  The run's critical-event count (the sum of
+    those maxima) is therefore never below the longest trace of the oracle's
+    mode P, stored with its writer script beside the other fixtures."""
+    seed, n, best = _longest_chains()[(workload, "exp" if sampler == 0 else "poisson")]
+    cfg = dict(getattr(W, workload)(seed), sampler=sampler)
+    g = run_gpu(cfg, tuning=tuning)
+    assert g["n"] == n
+    assert g["stats"]["critical_events"] >= best

@@ -710,3 +710,29 @@ def test_event_stream_against_plain_traces(idx, sampler):
         assert len(hit) == 1
         h = int(hit[0])
         assert h == 0 or _times(pt[h - 1:h])[0] < _times([tb])[0]
+
+
+def test_longest_chain_fixture_config1():
+    """The stored longest mode-P traces of config 1 (both samplers) are the
+    oracle's.  A plausibility tie to the species keys: with lambda = 1 a
+    lineage's events come at rate 1, so a trace of n events ends near time n
+    (standard deviation sqrt(n)), and the latest speciation time lies within
+    40 standard deviations of the longest trace."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2108_05815_b300 import workloads as W
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "longest_chains.txt")):
+        if not line.startswith("#") and line.strip():
+            w, s, seed, n, best = line.split()
+            rows[(w, s)] = (int(seed), int(n), int(best))
+    c = W.config1(42)
+    for sampler, name in ((0, "exp"), (1, "poisson")):
+        seed, n, best = rows[("config1", name)]
+        m = O.Model(c["kind"], 1, 1, c["deme"], c["nu"], seed, sampler=sampler)
+        locs = m.sample()
+        assert len(locs) == n
+        kl, kt, ne = m.trace(locs)
+        assert int(ne.max()) == best
+        times = kt.view(np.float64)
+        assert times.max() <= best + 40.0 * math.sqrt(best)
