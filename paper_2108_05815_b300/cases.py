@@ -130,6 +130,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--block-threads", type=int)
     ap.add_argument("--blocks-per-sm", type=int)
+    ap.add_argument("--tail-events", type=float, help="tail: events per lineage per round (fewer, longer launches)")
     a = ap.parse_args(argv)
     import torch  # noqa: F401  (device memory comes from torch's allocator)
     import paper_2108_05815_b300 as ind
@@ -150,6 +151,8 @@ def main(argv=None):
             launch["block_threads"] = a.block_threads
         if a.blocks_per_sm:
             launch["blocks_per_sm"] = a.blocks_per_sm
+        if a.tail_events:
+            launch["tail_events"] = a.tail_events
         r = run_tail(ind, sampler, a.only, a.reps, launch)
     r["sampler"] = a.sampler
     print(json.dumps(r))
