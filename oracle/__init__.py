@@ -93,6 +93,7 @@ def lib():
                 "or_exp1": (dbl, [u64, vp]),
                 "or_trace": (ctypes.c_int, [vp, u64, u64, vp, vp, vp]),
                 "or_trace_many": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp]),
+                "or_max_threads": (ctypes.c_int, []),
                 "or_run_merge": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp]),
                 "or_run_merge_events": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp, vp]),
                 "or_habitat": (None, [u64, u32, u32, dbl, u32, vp]),
@@ -110,6 +111,11 @@ def lib():
                 f.argtypes = args
             _lib = L
         return _lib
+
+
+def max_threads():
+    """threads a mode-P trace over many lineages may use (OpenMP's default)"""
+    return int(lib().or_max_threads())
 
 
 def _ptr(a):

@@ -44,6 +44,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 typedef __int128 i128;
@@ -494,6 +497,16 @@ int64_t or_trace_log(const or_model* m, uint64_t loc0, uint64_t cap, uint64_t* e
         loc = disperse(m, sk, loc, tau);
     }
     return -1;
+}
+
+/* threads a parallel loop of mode P may use (OpenMP's default team size) */
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Mode P over many lineages (independent; parallel over lineages) */
