@@ -243,6 +243,38 @@ def test_batch_equals_alone():
         s.close()
 
 
+def test_empty_sample():
+    """A sampling fraction that draws nobody: the run ends at once with no
+    species, as in the oracle."""
+    cfg = dict(kind=W.TORUS, width=8, height=8, deme=1, sigma=2.0, nu=1e-2, seed=5)
+    o = run_oracle(cfg, fraction=1e-9, sample_seed=3)
+    g = run_gpu(cfg, fraction=1e-9, sample_seed=3)
+    assert o["n"] == 0 and g["n"] == 0
+    assert o["K"] == 0 and g["K"] == 0
+    assert g["ids"].size == 0 and g["kl"].size == 0
+
+
+def test_batch_with_an_empty_member():
+    """A simulation whose sample is empty shares a batch with others: it
+    finishes with no species and leaves the others' results unchanged."""
+    cfgs = [dict(kind=W.TORUS, width=40, height=30, deme=1, sigma=2.0, nu=3e-3, seed=21),
+            dict(kind=W.TORUS, width=8, height=8, deme=1, sigma=2.0, nu=1e-2, seed=22),
+            dict(kind=W.NONSPATIAL, width=1, height=1, deme=700, nu=2e-3, seed=23)]
+    fractions = [1.0, 1e-9, 0.5]
+    alone = [run_gpu(c, fraction=f, sample_seed=3) for c, f in zip(cfgs, fractions)]
+    assert alone[1]["n"] == 0 and alone[1]["K"] == 0
+    sims = [gpu_sim(c) for c in cfgs]
+    for s, f in zip(sims, fractions):
+        s.sample(f, 3)
+    ind.batch_run(sims)
+    for s, a in zip(sims, alone):
+        ids, K = s.species()
+        kl, kt = s.species_keys()
+        assert K == a["K"] and np.array_equal(ids, a["ids"])
+        assert np.array_equal(kl, a["kl"]) and np.array_equal(kt, a["kt"])
+        s.close()
+
+
 # --------------------------------------------------------------------------
 # edge and degenerate cases
 # --------------------------------------------------------------------------

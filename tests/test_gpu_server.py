@@ -109,6 +109,23 @@ def test_served_matches_oracle_under_tight_budget():
         assert np.array_equal(gkl, kl) and np.array_equal(gkt, kt)
 
 
+def test_served_empty_request_finishes_without_species():
+    """A request whose sample is empty is admitted and reported finished at
+    once; the requests around it are unaffected."""
+    empty = dict(kind=W.TORUS, width=8, height=8, deme=1, sigma=2.0, nu=1e-2, seed=20, fraction=1e-9,
+                 sample_seed=3)
+    reqs = [REQUESTS[0], empty, REQUESTS[3]]
+    ref = [alone(r) for r in reqs]
+    assert ref[1][1] == 0 and ref[1][0].size == 0
+    got, st = serve(reqs, budget=1 << 33, max_sims=8, rounds=2, arrivals=[0, 1, 1])
+    assert st["finished"] == len(reqs)
+    for k in range(len(reqs)):
+        ids, K, kl, kt = got[k]
+        rid, rK, rkl, rkt = ref[k]
+        assert K == rK and np.array_equal(ids, rid)
+        assert np.array_equal(kl, rkl) and np.array_equal(kt, rkt)
+
+
 def test_server_rejects_what_cannot_fit():
     srv = ind.Server(1 << 20, 4)
     s = make(dict(kind=W.NONSPATIAL, width=1, height=1, deme=100000, nu=1e-3, seed=1, fraction=1.0, sample_seed=0))
