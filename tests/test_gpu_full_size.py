@@ -1,0 +1,107 @@
+"""Full-size parity of the batched and served forms.
+
+Config 4 (256 uneven simulations in one batch, sizes up to 10^6, nu down to
+10^-6) and served requests of config 5's shapes are too large for the
+oracle's event-ordered mode, so each simulation is checked on a few sampled
+individuals that the oracle traces alone (mode P: the individual's lineage
+followed to its speciation, section "The Independent Algorithm"), plus two
+properties that hold at any size: the species identities are the dense ranks
+of the speciation keys (the oracle's definition applied to the device's
+keys), and the species count is the number of distinct keys.  Every
+comparison is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2108_05815_b300 as ind
+from paper_2108_05815_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# the launch configuration the batch benchmark's autotuner chose on B300
+TUNED = dict(block_threads=256, blocks_per_sm=8, lineages_per_lane=1, events_per_visit=8, coop_lineages=4096,
+             occupancy_step=1.0, tail_events=32.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2108_05815_b300 import build
+    build.build()
+    yield
+
+
+def _sim(c, sampler):
+    return ind.Simulation(c["kind"], c["nu"], c["seed"], width=c["width"], height=c["height"], deme=c["deme"],
+                          sigma=c.get("sigma", 0.0), sampler=sampler)
+
+
+def _model(c, sampler):
+    return O.Model(c["kind"], c["width"], c["height"], c["deme"], c["nu"], c["seed"], sigma=c.get("sigma"),
+                   sampler=sampler)
+
+
+def _check(c, s, sampler, rng, picks, fraction=1.0, sample_seed=0):
+    ids, K = s.species()
+    kl, kt = s.species_keys()
+    # identities: the oracle's dense ranking of the device's keys
+    oids, oK = O.species_ids(kl, kt)
+    assert K == oK and np.array_equal(ids, oids)
+    # sampled individuals: the oracle traces their lineages alone
+    m = _model(c, sampler)
+    locs = m.sample(fraction, sample_seed)
+    assert len(locs) == s.n_sampled
+    if len(locs) == 0:
+        return
+    pick = rng.choice(len(locs), size=min(picks, len(locs)), replace=False)
+    okl, okt, _ = m.trace(locs[pick])
+    assert np.array_equal(kl[pick], okl) and np.array_equal(kt[pick], okt)
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_config4_full_size_sampled_parity(sampler):
+    specs = W.config4()
+    sims = [_sim(c, sampler) for c in specs]
+    try:
+        for s in sims:
+            s.sample()
+        ind.batch_run(sims, **TUNED)
+        rng = np.random.default_rng(11 + sampler)
+        for c, s in zip(specs, sims):
+            _check(c, s, sampler, rng, picks=2)
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_served_config5_shapes_sampled_parity():
+    """Requests of config 5's shapes (torus sides log-uniform 128..4096,
+    deme 1..4, sample fractions 0.01..1), those with nu >= 1e-5 among the
+    first three seconds of arrivals, all submitted at once to a server
+    whose budget admits them in waves."""
+    reqs = [r for r in W.config5(window_s=3.0) if r["nu"] >= 1e-5][:24]
+    assert len(reqs) >= 12
+    srv = ind.Server(8 * 10 ** 9, max_sims=16)
+    sims, tickets, done = {}, {}, set()
+    try:
+        for k, r in enumerate(reqs):
+            s = _sim(r, 0)
+            s.sample(r["fraction"], r["sample_seed"])
+            sims[k] = s
+            tickets[srv.submit(s)] = k
+        steps = 0
+        while len(done) < len(reqs):
+            for t in srv.step(4):
+                done.add(tickets[t])
+            steps += 1
+            assert steps < 1000000
+        rng = np.random.default_rng(17)
+        for k, r in enumerate(reqs):
+            _check(r, sims[k], 0, rng, picks=3, fraction=r["fraction"], sample_seed=r["sample_seed"])
+    finally:
+        for s in sims.values():
+            s.close()
+        srv.close()
