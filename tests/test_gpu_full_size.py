@@ -105,3 +105,29 @@ def test_served_config5_shapes_sampled_parity():
         for s in sims.values():
             s.close()
         srv.close()
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_implicit_full_size_sampled_parity(sampler):
+    """The spatially implicit workload at full size (a local community of
+    10^5, a static metacommunity of 10^9): too many metacommunity slots for
+    the oracle's event-ordered mode, so 32 sampled lineages are traced alone."""
+    c = W.implicit()
+    s = ind.Simulation(c["kind"], c["nu"], c["seed"], width=1, height=1, deme=c["deme"], sampler=sampler,
+                       migration=c["migration"], meta_size=c["meta_size"], meta_nu=c["meta_nu"])
+    try:
+        s.sample()
+        assert s.run()
+        ids, K = s.species()
+        kl, kt = s.species_keys()
+        oids, oK = O.species_ids(kl, kt)
+        assert K == oK and np.array_equal(ids, oids)
+        m = O.Model(c["kind"], 1, 1, c["deme"], c["nu"], c["seed"], sampler=sampler, migration=c["migration"],
+                    meta_size=c["meta_size"], meta_nu=c["meta_nu"])
+        locs = m.sample()
+        assert len(locs) == s.n_sampled
+        pick = np.random.default_rng(23 + sampler).choice(len(locs), size=32, replace=False)
+        okl, okt, _ = m.trace(locs[pick])
+        assert np.array_equal(kl[pick], okl) and np.array_equal(kt[pick], okt)
+    finally:
+        s.close()
