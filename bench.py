@@ -42,9 +42,9 @@ INT32_LANES_PER_SM = 128  # Blackwell: 128 INT32-capable lanes per SM per clock
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum \
 #       --clock-control none -k regex:k_advance -c 400 --csv \
 #       python -m paper_2108_05815_b300.cases config2 [--sampler poisson]
-# (16.6 MB over the 26 rounds with exponential sums, 14.9 MB over 25 with
-# Poisson points).
-TRAFFIC_PER_ROUND = {"exp": 637e3, "poisson": 594e3}
+# (17.05 MB over the 29 rounds with exponential sums, 15.11 MB over 29 with
+# Poisson points, default tuning).
+TRAFFIC_PER_ROUND = {"exp": 588e3, "poisson": 521e3}
 
 
 def parse():
@@ -400,7 +400,7 @@ def run_ours(args, rank, world, local, pg):
                      "ops_per_event": ops_per_event, "events_per_launch": events_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": adv_n,
                      "dominant": ("k_advance_coop, %s of the step (ncu launch list): latency-bound, see latency_bound"
-                                  % {"exp": "94 %", "poisson": "92 %"}[args.sampler]
+                                  % {"exp": "95 %", "poisson": "93 %"}[args.sampler]
                                   if _single["dataset"] == "config2" else None),
                      "busiest_launch": busiest(best or {}, ops_per_event, peak),
                      "peak_source": "148 SMs x 128 INT32 lanes x 2032 MHz max SM clock (derived)"},

@@ -39,7 +39,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->blocks_per_sm = 8;
     t->lineages_per_lane = 1;
     t->events_per_visit = 8;
-    t->coop_lineages = 4096;
+    t->coop_lineages = 16384;
     t->advance_variant = 1;
     t->rounds_per_check = 16;
     t->use_graph = 1;
@@ -49,7 +49,7 @@ void ind_default_tuning(ind_tuning* t) {
     t->events_per_round = 4194304.0;
     t->min_events_per_lineage = 0.25;
     t->occupancy_step = 0.25;
-    t->tail_events = 128.0;
+    t->tail_events = 64.0;
     t->busy_lineages = 32768.0;
     t->max_step_events = 1024.0;
 }
