@@ -20,7 +20,7 @@ from paper_2108_05815_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 # the launch configuration the batch benchmark's autotuner chose on B300
-TUNED = dict(block_threads=256, blocks_per_sm=8, lineages_per_lane=1, events_per_visit=8, coop_lineages=4096,
+TUNED = dict(block_threads=256, blocks_per_sm=8, lineages_per_lane=1, events_per_visit=8, coop_lineages=16384,
              occupancy_step=1.0, tail_events=32.0)
 
 
