@@ -193,7 +193,11 @@ typedef struct {
      * locations: lambda * step = max(floor, min(occupancy_step * S / n,
      * events_per_round / n)), floor = tail_events while n < busy_lineages
      * (the GPU is latency-bound and duplicates cost no time), else
-     * min_events_per_lineage */
+     * min_events_per_lineage.  In a batch the level is then shared: a
+     * simulation's lambda * step is raised to min(occupancy_step * S / n,
+     * the largest lambda * step of the batch's live simulations) when that
+     * is more, since a round lasts as long as its busiest simulation needs.
+     * None of this changes any result, only how much work a round does. */
     double events_per_round;       /* water level: target events per simulation per round */
     double min_events_per_lineage; /* lower bound of lambda x horizon step */
     double occupancy_step;         /* alpha: duplicate work per round stays near alpha / 2 */
