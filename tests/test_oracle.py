@@ -298,6 +298,30 @@ def test_ewens_expected_richness_config1(sampler):
     assert 0.75 * sd < Ks.std(ddof=1) < 1.3 * sd
 
 
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_wide_torus_is_ewens(sampler):
+    """A 4 x 4 torus of demes of 4 with sigma = 40: each axis's discretised
+    normal, wrapped onto 4 cells, is uniform up to about exp(-2 pi^2 sigma^2
+    / 16) (far below 2^-64), and the deme index is uniform, so every
+    dispersal picks one of the J = 64 individuals uniformly, the parent's own
+    included: the non-spatial model of the appendix "Analytical solutions"
+    (Ewens, theta = J nu / (1 - nu)) run through the torus's dispersal,
+    wrap and slot code."""
+    J, nu = 64, 0.02
+    Ks = []
+    for seed in range(1, 1001):
+        m = O.Model(O.TORUS, 4, 4, 4, nu, seed, sigma=40.0, sampler=sampler)
+        kl, kt, _ = m.run_merge(m.sample())
+        Ks.append(O.species_ids(kl, kt)[1])
+    Ks = np.array(Ks)
+    theta = J * nu / (1 - nu)
+    expected = theta * (special.digamma(theta + J) - special.digamma(theta))
+    se = Ks.std(ddof=1) / math.sqrt(len(Ks))
+    assert abs(Ks.mean() - expected) < 3 * se, (Ks.mean(), expected, se)
+    sd = math.sqrt(sum(theta * k / (theta + k) ** 2 for k in range(J)))
+    assert 0.85 * sd < Ks.std(ddof=1) < 1.15 * sd
+
+
 def _exact_law(path):
     rows = [l.split() for l in open(path) if not l.startswith("#")]
     return {int(k): int(a) / int(b) for k, a, b in rows}
