@@ -322,6 +322,29 @@ def test_wide_torus_is_ewens(sampler):
     assert 0.85 * sd < Ks.std(ddof=1) < 1.15 * sd
 
 
+@pytest.mark.parametrize("sampler", SAMPLERS)
+def test_single_cell_map_is_ewens(sampler):
+    """A habitat map of one cell holding 64 individuals: every alias-table
+    offset wraps back onto that cell, so a dispersal draws its alias column
+    and then a uniform index in the deme: the non-spatial model with J = 64
+    (Ewens, theta = J nu / (1 - nu)) run through the map's alias and deme
+    code."""
+    J, nu = 64, 0.02
+    dm = np.array([J], dtype=np.uint8)
+    Ks = []
+    for seed in range(1, 1001):
+        m = O.Model(O.MAP, 1, 1, 0, nu, seed, sigma=2.0, radius=4, deme_map=dm, sampler=sampler)
+        kl, kt, _ = m.run_merge(m.sample())
+        Ks.append(O.species_ids(kl, kt)[1])
+    Ks = np.array(Ks)
+    theta = J * nu / (1 - nu)
+    expected = theta * (special.digamma(theta + J) - special.digamma(theta))
+    se = Ks.std(ddof=1) / math.sqrt(len(Ks))
+    assert abs(Ks.mean() - expected) < 3 * se, (Ks.mean(), expected, se)
+    sd = math.sqrt(sum(theta * k / (theta + k) ** 2 for k in range(J)))
+    assert 0.85 * sd < Ks.std(ddof=1) < 1.15 * sd
+
+
 def _exact_law(path):
     rows = [l.split() for l in open(path) if not l.startswith("#")]
     return {int(k): int(a) / int(b) for k, a, b in rows}
