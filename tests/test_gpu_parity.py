@@ -243,6 +243,16 @@ def test_batch_equals_alone():
         s.close()
 
 
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_single_cell_map_parity(sampler):
+    """A habitat map of one cell of 64 individuals: every alias offset wraps
+    back onto the cell."""
+    dm = np.array([64], dtype=np.uint8)
+    for seed in (3, 4, 5):
+        cfg = dict(kind=W.MAP, width=1, height=1, sigma=2.0, radius=4, nu=0.02, seed=seed, sampler=sampler)
+        assert_same(run_gpu(cfg, dm), run_oracle(cfg, dm))
+
+
 def test_empty_sample():
     """A sampling fraction that draws nobody: the run ends at once with no
     species, as in the oracle."""
@@ -286,6 +296,8 @@ def test_batch_with_an_empty_member():
     dict(kind=W.TORUS, width=40, height=30, deme=2, sigma=2.0, nu=3e-3, seed=5, lam=2.5, delta_t=0.5),
     dict(kind=W.TORUS, width=40, height=30, deme=2, sigma=2.0, nu=3e-3, seed=6, lam=0.3, delta_t=4.0),
     dict(kind=W.NONSPATIAL, width=1, height=1, deme=2000, nu=1e-2, seed=7, lam=7.0, delta_t=0.125),
+    dict(kind=W.TORUS, width=4, height=4, deme=4, sigma=40.0, nu=0.02, seed=8),   # kernel wider than the torus
+    dict(kind=W.TORUS, width=4, height=4, deme=4, sigma=40.0, nu=0.02, seed=9, sampler=1),
 ])
 def test_edge_cases_parity(cfg):
     o = run_oracle(cfg)
