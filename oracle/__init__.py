@@ -164,11 +164,14 @@ def draw(seed, loc, tkey, tag, idx):
 
 def exp1(draw_u64):
     """Exp(1) = -ln U of the top 53 bits of a 64-bit draw, U = (r + 1) 2^-53.
-    Pinned against the exact logarithm (mpmath) within 2^-56 absolute."""
+    Pinned against the exact logarithm (mpmath) within 2^-57 plus half an ulp."""
     return lib().or_exp1(int(draw_u64), ctypes.byref(_ln()))
 
 
 def exp1_q58(r53):
+    """X58(r53): the frozen fixed-point definition of -ln((r53 + 1) 2^-53) in
+    units of 2^-58 (stated plainly in ln_definition.py, equal to it on every
+    bucket edge of every binade)"""
     return int(lib().or_exp1_q58(int(r53), ctypes.byref(_ln())))
 
 

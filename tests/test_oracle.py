@@ -15,6 +15,7 @@ import pytest
 from scipy import special, stats
 
 import oracle as O
+from oracle import ln_definition as LD
 from oracle import tables as T
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -98,6 +99,33 @@ def test_exp1_matches_exact_logarithm():
         err = abs(mpmath.mpf(x) - exact)
         bound = mpmath.mpf(2) ** -57 + mpmath.mpf(math.ulp(x) if x > 0 else 0) / 2
         assert err <= bound, (r, x, float(exact))
+
+
+def test_exp1_q58_is_its_definition_on_every_bucket_edge():
+    """the oracle's word-size logarithm equals the plain statement of the
+    frozen definition (oracle/ln_definition.py: exact integers, constants
+    computed from their definitions) on the first and last value of every
+    table bucket of every binade, and on the values just across each edge"""
+    n = 0
+    for e in range(54):
+        for r in LD.bucket_edges(e):
+            assert O.exp1_q58(r) == LD.x58(r), (e, r)
+            n += 1
+    assert n > 300000
+
+
+def test_ln_definition_constants_and_accuracy():
+    """the definition's constants are the oracle's tables, and the definition
+    itself is within 2^-57 of the exact logarithm (the values plus half an
+    ulp of binary64 bound the oracle's double above)"""
+    tab, ln2, c3, _ = T.ln_tables()
+    assert ln2 == LD.ln2_units() and c3 == LD.third_units()
+    assert all(tab[j] == LD.bucket_log(j) for j in range(1 << LD.BUCKET_BITS))
+    assert all(O.lib().or_ln_recip(j) == LD.bucket_reciprocal(j) for j in range(1 << LD.BUCKET_BITS))
+    mpmath.mp.dps = 40
+    for r in _r53_cases():
+        exact = -mpmath.log(mpmath.mpf(r + 1) / mpmath.mpf(2) ** 53)
+        assert abs(mpmath.mpf(LD.x58(r)) / mpmath.mpf(2) ** 58 - exact) <= mpmath.mpf(2) ** -57, r
 
 
 def test_exp1_monotone_and_extremes():
