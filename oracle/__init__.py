@@ -96,6 +96,7 @@ def lib():
                 "or_max_threads": (ctypes.c_int, []),
                 "or_run_merge": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp]),
                 "or_run_merge_events": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp, vp]),
+                "or_run_merge_longest": (ctypes.c_int, [vp, vp, u64, u64, vp, vp, vp, vp]),
                 "or_habitat": (None, [u64, u32, u32, dbl, u32, vp]),
                 "or_sample": (u64, [vp, dbl, u64, vp]),
                 "or_gauss_offset": (u64, [vp, u64]),
@@ -260,15 +261,17 @@ class Model:
         lib().or_sample(self._mp, fraction, sample_seed, _ptr(out))
         return out
 
-    def trace(self, locs, max_events=1 << 40):
-        """Mode P: (key_loc, key_time_bits, n_events) per starting location."""
+    def trace(self, locs, max_events=1 << 40, partial=False):
+        """Mode P: (key_loc, key_time_bits, n_events) per starting location.
+        partial: a lineage may stop after max_events events without having
+        speciated (its key is then undefined and its count is max_events)."""
         locs = np.ascontiguousarray(locs, dtype=np.uint64)
         n = locs.size
         kl = np.zeros(n, dtype=np.uint64)
         kt = np.zeros(n, dtype=np.uint64)
         ne = np.zeros(n, dtype=np.uint64)
         st = lib().or_trace_many(self._mp, _ptr(locs), n, max_events, _ptr(kl), _ptr(kt), _ptr(ne))
-        if st != 0:
+        if st != 0 and not (partial and st == -1):
             raise RuntimeError("oracle trace failed with status %d" % st)
         return kl, kt, ne
 
@@ -284,6 +287,23 @@ class Model:
         if st != 0:
             raise RuntimeError("oracle merge run failed with status %d" % st)
         return kl, kt, int(nu.value)
+
+    def run_merge_longest(self, locs, max_events=1 << 40):
+        """Mode M plus the longest line of descent: (key_loc, key_time_bits,
+        n_unique_events, longest), longest = the most events any one sampled
+        individual's lineage runs before it speciates (the longest mode-P
+        trace, found without tracing every lineage alone)."""
+        locs = np.ascontiguousarray(locs, dtype=np.uint64)
+        n = locs.size
+        kl = np.zeros(n, dtype=np.uint64)
+        kt = np.zeros(n, dtype=np.uint64)
+        nu = ctypes.c_uint64(0)
+        lg = ctypes.c_uint64(0)
+        st = lib().or_run_merge_longest(self._mp, _ptr(locs), n, max_events, _ptr(kl), _ptr(kt),
+                                        ctypes.byref(nu), ctypes.byref(lg))
+        if st != 0:
+            raise RuntimeError("oracle merge run failed with status %d" % st)
+        return kl, kt, int(nu.value), int(lg.value)
 
     def run_merge_events(self, locs, max_events=1 << 40):
         """Mode M with its event stream: (key_loc, key_time_bits, n_unique,

@@ -607,12 +607,25 @@ typedef struct {
 } or_event_log;
 
 static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
-                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log);
+                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log,
+                     uint64_t* longest);
 
 int or_run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
                  uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique)
 {
-    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, 0);
+    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, 0, 0);
+}
+
+/* mode M that also reports the longest line of descent: the most events any
+ * one sampled individual's lineage runs before it speciates, which is the
+ * longest mode-P trace.  A lineage carries the most events of any individual
+ * it stands for; on a merge the occupant takes the larger of the two counts,
+ * since from then on both groups share the occupant's events. */
+int or_run_merge_longest(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
+                         uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, uint64_t* longest)
+{
+    *longest = 0;
+    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, 0, longest);
 }
 
 /* mode M with its event stream; -5 if the log's arrays are too small */
@@ -620,11 +633,12 @@ int or_run_merge_events(const or_model* m, const uint64_t* loc0, uint64_t n, uin
                         uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log)
 {
     log->n = log->n_co = 0;
-    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, log);
+    return run_merge(m, loc0, n, max_events, key_loc, key_time, n_unique, log, 0);
 }
 
 static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64_t max_events,
-                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log)
+                     uint64_t* key_loc, uint64_t* key_time, uint64_t* n_unique, or_event_log* log,
+                     uint64_t* longest)
 {
     uint32_t sk[2];
     or_seed_key(m->seed, sk);
@@ -636,8 +650,9 @@ static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64
     int64_t* parent = (int64_t*)malloc(n * sizeof(int64_t));
     double* last = (double*)malloc(n * sizeof(double)); /* each lineage's prior event time */
     or_heap_item* heap = (or_heap_item*)malloc((n + 1) * sizeof(or_heap_item));
+    uint64_t* depth = longest ? (uint64_t*)calloc(n, sizeof(uint64_t)) : 0;
     int status = 0;
-    if (!occupant || !pending || !loc_of || !parent || !last || !heap) {
+    if (!occupant || !pending || !loc_of || !parent || !last || !heap || (longest && !depth)) {
         status = -4;
         goto done;
     }
@@ -675,6 +690,8 @@ static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64
         double tau = it.t;
         occupant[it.slot] = -1;
         events++;
+        if (depth)
+            depth[a]++;
         int spec = speciates(m, sk, loc, tau);
         uint64_t target = spec ? ~0ull : disperse(m, sk, loc, tau);
         if (log) {
@@ -693,6 +710,8 @@ static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64
         if (spec) {
             key_loc[a] = loc;
             key_time[a] = dbl_bits(tau);
+            if (depth && depth[a] > *longest)
+                *longest = depth[a];
             continue;
         }
         uint64_t ts = slot_of(m, target);
@@ -702,6 +721,8 @@ static int run_merge(const or_model* m, const uint64_t* loc0, uint64_t n, uint64
                 goto done;
             }
             parent[a] = occupant[ts];
+            if (depth && depth[a] > depth[occupant[ts]])
+                depth[occupant[ts]] = depth[a];
             if (log) {
                 if (log->n_co >= log->co_cap) {
                     status = -5;
@@ -742,6 +763,7 @@ done:
     free(parent);
     free(last);
     free(heap);
+    free(depth);
     return status;
 }
 

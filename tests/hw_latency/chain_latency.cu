@@ -1,0 +1,203 @@
+// chain_latency.cu -- dependent-latency microbenchmark of the operation
+// classes on one lineage's event chain (measurement tool of the test side;
+// not part of the library).
+//
+// Each kernel runs one dependent chain of STEPS operations of one class in
+// one warp (lane 0's clock) and writes the chain's result, so nothing can
+// be dropped; the cycle count comes from clock64() around the chain.  The
+// chains are built so that no step can start before the previous one ends
+// and no algebra can shorten them: every step feeds a nonlinear operation
+// (a high product, a table index, a shuffle lane, a compare) or is measured
+// as the difference of two such chains.
+//
+//   imad_hi     x = mulhi32(x, y)                       32-bit high product
+//   philox      one Philox4x32 round (two high/low product pairs, xors and
+//               the key schedule): the round's dependent path
+//   hi_xor      x = mulhi32(x, y) ^ z                   high product + xor
+//   umul64hi    x = mulhi64(x, y)                       64-bit high product
+//   imad_wide   x = lo64(lo32(x) * y + x)               32x32 -> 64 multiply-add
+//   add64_sel   x = (x + a < b) ? x + a : x + c         64-bit add, compare, select
+//   clz_norm    x = (x << clz64(x)) ^ a                 normalise: leading-zero count, shift
+//   lds         i = s[i]                                shared-memory load
+//   ldg_l1      i = g[i] (4 KB ring, L1-resident)       global load, L1 hit
+//   ldg_dram    i = g[i] (random ring >> L2)            global load from DRAM
+//   shfl        x = shfl(x, x)                          warp shuffle
+//   ballot      x = ballot(x & bit) ^ x                  warp vote + xor
+//   redux_min   x = redux.min(x) ^ lane-independent    warp reduction
+#include <cstdint>
+#include <cuda_runtime.h>
+
+constexpr int STEPS = 2048;
+
+struct Out {
+    unsigned long long cycles;
+    unsigned long long sink;
+};
+
+__device__ __forceinline__ unsigned long long clk() { return clock64(); }
+
+#define CHAIN_KERNEL(NAME, TYPE, INIT, STEP)                                              \
+    __global__ void k_##NAME(const uint64_t* __restrict__ prm, Out* out) {                \
+        TYPE x = (TYPE)(INIT);                                                            \
+        const uint64_t a = prm[0], b = prm[1], c = prm[2];                                \
+        const uint32_t y = (uint32_t)prm[3], z = (uint32_t)prm[4];                        \
+        (void)a; (void)b; (void)c; (void)y; (void)z;                                       \
+        __syncwarp();                                                                     \
+        const unsigned long long t0 = clk();                                              \
+        _Pragma("unroll 1") for (int it = 0; it < STEPS / 64; ++it) {                      \
+            _Pragma("unroll") for (int s = 0; s < 64; ++s) { STEP; }                       \
+        }                                                                                 \
+        const unsigned long long t1 = clk();                                              \
+        if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;                              \
+        out->sink += (unsigned long long)x;                                               \
+    }
+
+CHAIN_KERNEL(imad_hi, uint32_t, prm[5], x = __umulhi(x, y))
+CHAIN_KERNEL(hi_xor, uint32_t, prm[5], x = __umulhi(x, y) ^ z)
+CHAIN_KERNEL(umul64hi, uint64_t, prm[5], x = __umul64hi(x, a))
+CHAIN_KERNEL(imad_wide, uint64_t, prm[5], x = (uint64_t)(uint32_t)x * y + x)
+CHAIN_KERNEL(add64_sel, uint64_t, prm[5], { const uint64_t s0 = x + a; x = s0 < b ? s0 : x + c; })
+CHAIN_KERNEL(clz_norm, uint64_t, prm[5], x = (x << __clzll((long long)x)) ^ a)
+CHAIN_KERNEL(shfl, uint32_t, prm[5], x = __shfl_sync(0xFFFFFFFFu, x, x))
+CHAIN_KERNEL(ballot, uint32_t, prm[5], x = __ballot_sync(0xFFFFFFFFu, (x >> (threadIdx.x & 31u)) & 1u) ^ z)
+CHAIN_KERNEL(redux_min, uint32_t, prm[5], x = __reduce_min_sync(0xFFFFFFFFu, x ^ threadIdx.x) + z)
+
+// a 32-bit add whose result indexes nothing: x = (x + z) ^ y is one
+// dependent add and one xor per step (measured beside hi_xor and imad_hi)
+CHAIN_KERNEL(add_xor, uint32_t, prm[5], x = (x + z) ^ y)
+
+// one Philox4x32 round per step: the counter words feed the next round,
+// the key words advance by the Weyl increments
+__global__ void k_philox(const uint64_t* __restrict__ prm, Out* out) {
+    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
+    __syncwarp();
+    const unsigned long long t0 = clk();
+#pragma unroll 1
+    for (int it = 0; it < STEPS / 64; ++it) {
+#pragma unroll
+        for (int s = 0; s < 64; ++s) {
+            const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+            const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+            c0 = hi1 ^ c1 ^ k0;
+            c1 = lo1;
+            c2 = hi0 ^ c3 ^ k1;
+            c3 = lo0;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += (unsigned long long)(c0 ^ c1 ^ c2 ^ c3);
+}
+
+// dependent loads: i = table[i] over a ring laid out by the host
+__global__ void k_lds(const uint64_t* __restrict__ prm, Out* out) {
+    __shared__ uint32_t s[1024];
+    for (uint32_t k = threadIdx.x; k < 1024; k += blockDim.x) s[k] = (k * 7u + 13u) & 1023u;
+    __syncthreads();
+    uint32_t i = (uint32_t)prm[5] & 1023u;
+    const unsigned long long t0 = clk();
+#pragma unroll 1
+    for (int it = 0; it < STEPS / 64; ++it) {
+#pragma unroll
+        for (int s2 = 0; s2 < 64; ++s2) i = s[i];
+    }
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += i;
+}
+
+__global__ void k_ldg(const uint32_t* __restrict__ ring, uint32_t start, int steps, Out* out) {
+    uint32_t i = start;
+    const unsigned long long t0 = clk();
+    for (int s = 0; s < steps; ++s) i = __ldcg(ring + i);  // L2-cached load (L1 bypassed): the gather's path
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += i;
+}
+
+__global__ void k_ldg_l1(const uint32_t* __restrict__ ring, uint32_t start, int steps, Out* out) {
+    uint32_t i = start;
+    const unsigned long long t0 = clk();
+    for (int s = 0; s < steps; ++s) i = __ldg(ring + i);
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += i;
+}
+
+// spins for `cycles` SM clock cycles (bounded by the count itself): timed
+// with CUDA events on the host, it gives the SM clock during the run
+__global__ void k_spin(unsigned long long cycles, Out* out) {
+    const unsigned long long t0 = clk();
+    unsigned long long t = t0;
+    while (t - t0 < cycles) t = clk();
+    if (threadIdx.x == 0) out->cycles = t - t0;
+}
+
+extern "C" {
+
+// SM clock in MHz over a spin of `cycles` cycles (negative: CUDA error)
+double hwlat_clock_mhz(unsigned long long cycles, void* out_dev) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+    k_spin<<<1, 32>>>(1000, (Out*)out_dev);  // warm-up launch
+    cudaEventRecord(e0);
+    k_spin<<<1, 32>>>(cycles, (Out*)out_dev);
+    cudaEventRecord(e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return -(double)e;
+    return (double)cycles / ((double)ms * 1e3);
+}
+
+int hwlat_steps() { return STEPS; }
+
+// class ids: 0 imad_hi, 1 hi_xor, 2 umul64hi, 3 imad_wide, 4 add64_sel,
+// 5 clz_norm, 6 add_xor, 7 shfl, 8 ballot, 9 redux_min, 10 philox, 11 lds
+// Runs the chain once in one warp of one block; returns its cycles, or a
+// negative CUDA error.  prm: 6 device words of runtime operands.
+long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
+    Out* o = (Out*)out_dev;
+    switch (cls) {
+        case 0: k_imad_hi<<<1, 32>>>(prm, o); break;
+        case 1: k_hi_xor<<<1, 32>>>(prm, o); break;
+        case 2: k_umul64hi<<<1, 32>>>(prm, o); break;
+        case 3: k_imad_wide<<<1, 32>>>(prm, o); break;
+        case 4: k_add64_sel<<<1, 32>>>(prm, o); break;
+        case 5: k_clz_norm<<<1, 32>>>(prm, o); break;
+        case 6: k_add_xor<<<1, 32>>>(prm, o); break;
+        case 7: k_shfl<<<1, 32>>>(prm, o); break;
+        case 8: k_ballot<<<1, 32>>>(prm, o); break;
+        case 9: k_redux_min<<<1, 32>>>(prm, o); break;
+        case 10: k_philox<<<1, 32>>>(prm, o); break;
+        case 11: k_lds<<<1, 32>>>(prm, o); break;
+        default: return -1;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return -(long long)e;
+    Out h;
+    e = cudaMemcpy(&h, o, sizeof(Out), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return -(long long)e;
+    return (long long)h.cycles;
+}
+
+// dependent global loads over a ring of n entries (device array built by the
+// caller); l1: 1 for the L1-cached form.  Every index stays below n.
+long long hwlat_ring(const uint32_t* ring, uint32_t start, int steps, int l1, void* out_dev) {
+    Out* o = (Out*)out_dev;
+    if (l1) k_ldg_l1<<<1, 32>>>(ring, start, steps, o);
+    else k_ldg<<<1, 32>>>(ring, start, steps, o);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return -(long long)e;
+    Out h;
+    e = cudaMemcpy(&h, o, sizeof(Out), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return -(long long)e;
+    return (long long)h.cycles;
+}
+
+}

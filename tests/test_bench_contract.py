@@ -25,21 +25,24 @@ def test_reference_arm_line():
     d = _line(["--impl", "reference", "--steps", "1", "--warmup", "0"], timeout=600)
     assert BASE_KEYS <= set(d)
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["workload"].startswith("config2")
+    assert d["config"]["workload"].startswith("config3")
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    d = _line(["--steps", "3", "--warmup", "3", "--cpu-seconds", "1"], timeout=1200)
+    """the default line: config 3 headline, batched config 4 and served
+    config 5 beside it (short settings), all rates in unique events"""
+    d = _line(["--steps", "3", "--warmup", "3", "--cpu-seconds", "1", "--batch-steps", "1", "--plain-subset", "4",
+               "--served-window", "1", "--served-plain", "2"], timeout=1800)
     assert BASE_KEYS <= set(d) and d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
     assert d["value"] > 0 and d["unit"] == "events/s" and d["vs_baseline"] is None
-    assert "workload" in d["config"] and "l2" in d["config"]
+    assert d["config"]["workload"].startswith("config3") and "l2" in d["config"]
     rf = d["roofline"]
     assert rf["bound"] in ("hbm", "tensor", "alu") and rf["peak"] > 0
-    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9 and "derived" in rf["peak_source"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
     e2e = d["e2e"]
@@ -47,4 +50,12 @@ def test_gpu_arm_line():
     assert d["gpu_launches"] > 0
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     lb = d["latency_bound"]
-    assert lb["critical_events_per_step"] >= lb["longest_lineage_events"]
+    hw = lb["hw_floor"]
+    assert 0 < hw["ns_per_event"] < lb["lone_lineage_ns_per_event"]
+    if "longest_descent_events" in lb:
+        assert lb["critical_events_per_step"] >= lb["longest_descent_events"]
+        assert 0 < hw["frac_of_longest_floor"] < 1
+    b = d["batched"]
+    assert b["value"] > 0 and b["unit"] == "unique events/s" and b["speedup_vs_plain"] > 0
+    s = d["served"]
+    assert s["requests"] > 0 and s["latency_s"]["p50"] > 0 and s["achieved_rate_per_s"] > 0

@@ -19,11 +19,11 @@ def _rank(rank, world, port, out):
     os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
                        "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
     import bench
-    r, w, local, pg = bench.dist_setup(None)
+    r, w, local, pg = bench.dist_setup()
     assert (r, w) == (rank, world) and pg is not None
     bench.barrier(pg)
-    mx = bench.allreduce_max(pg, 10.0 + rank)
-    sm = bench.allreduce_sum(pg, 1.0 + rank)
+    mx = bench.allreduce(pg, 10.0 + rank, "max")
+    sm = bench.allreduce(pg, 1.0 + rank, "sum")
     out[rank] = (mx, sm)
     pg.destroy_process_group()
 

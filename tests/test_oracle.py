@@ -811,3 +811,30 @@ def test_longest_chain_fixture_config1():
         assert int(ne.max()) == best
         times = kt.view(np.float64)
         assert times.max() <= best + 40.0 * math.sqrt(best)
+
+
+@pytest.mark.parametrize("workload", ["config1", "config2"])
+def test_merge_mode_finds_the_longest_trace(workload):
+    """Mode M's count of the longest line of descent (a lineage carries the
+    most events of any individual it stands for; a merge keeps the larger
+    count) equals the longest mode-P trace, stored for configs 1 and 2 by
+    the script that traces every lineage alone; its keys are mode M's."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2108_05815_b300 import workloads as W
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "longest_chains.txt")):
+        if not line.startswith("#") and line.strip():
+            w, s, seed, n, best = line.split()
+            rows[(w, s)] = (int(seed), int(n), int(best))
+    for sampler, name in ((0, "exp"), (1, "poisson")):
+        seed, n, best = rows[(workload, name)]
+        c = getattr(W, workload)(seed)
+        m = O.Model(c["kind"], c["width"], c["height"], c["deme"], c["nu"], seed, sigma=c.get("sigma", 0.0),
+                    sampler=sampler)
+        locs = m.sample()
+        assert len(locs) == n
+        kl, kt, U, L = m.run_merge_longest(locs)
+        kl2, kt2, U2 = m.run_merge(locs)
+        assert L == best and U == U2
+        assert np.array_equal(kl, kl2) and np.array_equal(kt, kt2)
