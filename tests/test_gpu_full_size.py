@@ -108,6 +108,47 @@ def test_served_config5_shapes_sampled_parity():
 
 
 @pytest.mark.parametrize("sampler", [0, 1])
+def test_served_small_nu_sampled_parity(sampler):
+    """The requests that set config 5's latency: speciation probabilities
+    in [1e-7, 1e-5), whose last lineages run 10^5 to 10^7 events before they
+    speciate.  From the first ten seconds of arrivals: the request of the
+    smallest nu (1.0e-7), the three smallest (by sampled individuals) with
+    nu below 1e-6 and the two smallest with nu in [1e-6, 1e-5) share a
+    server; three individuals of each are traced alone by the oracle, for
+    both event-time samplers."""
+    arr = W.config5(window_s=10.0)
+
+    def size(r):
+        return r["width"] * r["height"] * r["deme"] * r["fraction"]
+    lowest = min(arr, key=lambda r: r["nu"])
+    low = sorted([r for r in arr if r["nu"] < 1e-6 and r is not lowest], key=size)[:3]
+    mid = sorted([r for r in arr if 1e-6 <= r["nu"] < 1e-5], key=size)[:2]
+    reqs = [lowest] + low + mid
+    assert len(reqs) == 6 and lowest["nu"] < 1.1e-7
+    srv = ind.Server(8 * 10 ** 9, max_sims=16)
+    sims, tickets, done = {}, {}, set()
+    try:
+        for k, r in enumerate(reqs):
+            s = _sim(r, sampler)
+            s.sample(r["fraction"], r["sample_seed"])
+            sims[k] = s
+            tickets[srv.submit(s)] = k
+        steps = 0
+        while len(done) < len(reqs):
+            for t in srv.step(8):
+                done.add(tickets[t])
+            steps += 1
+            assert steps < 10000000
+        rng = np.random.default_rng(29 + sampler)
+        for k, r in enumerate(reqs):
+            _check(r, sims[k], sampler, rng, picks=3, fraction=r["fraction"], sample_seed=r["sample_seed"])
+    finally:
+        for s in sims.values():
+            s.close()
+        srv.close()
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
 def test_implicit_full_size_sampled_parity(sampler):
     """The spatially implicit workload at full size (a local community of
     10^5, a static metacommunity of 10^9): too many metacommunity slots for

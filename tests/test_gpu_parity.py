@@ -191,11 +191,18 @@ TUNINGS = [
 ]
 
 
-@pytest.mark.parametrize("tuning", TUNINGS)
+_TUNING_CFG = dict(kind=W.TORUS, width=48, height=40, deme=2, sigma=2.0, nu=2e-3, seed=31)
+_tuning_oracle = {}
+
+
+@pytest.mark.parametrize("tuning", [None] + TUNINGS)
 def test_results_do_not_depend_on_tuning(tuning):
-    cfg = dict(kind=W.TORUS, width=48, height=40, deme=2, sigma=2.0, nu=2e-3, seed=31)
-    ref = run_gpu(cfg)
-    assert_same(run_gpu(cfg, tuning=tuning), ref)
+    """every tuning gives the oracle's result (not merely the default
+    tuning's), including dedup off, no graphs, one-lane and one-warp forms
+    throughout, and extreme water levels"""
+    if "o" not in _tuning_oracle:
+        _tuning_oracle["o"] = run_oracle(_TUNING_CFG)
+    assert_same(run_gpu(_TUNING_CFG, tuning=tuning), _tuning_oracle["o"])
 
 
 def test_round_budget_resumes():
@@ -310,26 +317,65 @@ def test_edge_cases_parity(cfg):
 
 
 # --------------------------------------------------------------------------
-# full-size habitat map (config 3): sampled individuals + properties
+# full-size habitat map (config 3): every individual against the oracle's
+# stored result, sampled individuals against its lone traces
 # --------------------------------------------------------------------------
-def test_config3_full_size_sampled_parity():
-    cfg = W.config3()
-    dm = ind.habitat(cfg["map_seed"], cfg["width"], cfg["height"], cfg["p_habitable"], cfg["max_deme"])
+def _config3_digest():
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "config3_digest.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        w, s, seed, n, U, K, L, h = line.split()
+        rows[s] = dict(seed=int(seed), n=int(n), U=int(U), K=int(K), L=int(L), sha=h)
+    return rows
+
+
+_c3 = {}
+
+
+def _config3_gpu(sampler):
+    """config 3 at full size on the GPU, once per sampler per module"""
+    if sampler not in _c3:
+        cfg = dict(W.config3(), sampler=sampler)
+        dm = ind.habitat(cfg["map_seed"], cfg["width"], cfg["height"], cfg["p_habitable"], cfg["max_deme"])
+        g = run_gpu(cfg, deme_map=dm, tuning=dict(count_unique=1))
+        _c3[sampler] = (cfg, dm, g)
+    return _c3[sampler]
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_config3_full_size_equals_oracle(sampler):
+    """Every one of config 3's 2,829,667 individuals: the speciation keys of
+    the whole sample hash to the digest of the oracle's event-ordered run
+    (written by tests/golden/make_config3.py), and the species count, the
+    unique-event count and the longest line of descent agree with it."""
+    import hashlib
+    want = _config3_digest()["exp" if sampler == 0 else "poisson"]
+    cfg, dm, g = _config3_gpu(sampler)
     assert np.array_equal(dm, O.habitat(cfg["map_seed"], cfg["width"], cfg["height"], cfg["p_habitable"],
                                         cfg["max_deme"]))
-    g = run_gpu(cfg, deme_map=dm)
-    assert g["n"] == int(dm.astype(np.int64).sum())
-    # properties that hold at any size
-    keys = list(zip(g["kl"].tolist(), g["kt"].tolist()))
-    distinct = sorted(set(keys))
-    assert g["K"] == len(distinct)
-    rank = {k: r for r, k in enumerate(distinct)}
-    sub = np.arange(0, g["n"], 9973)
-    assert all(g["ids"][i] == rank[keys[i]] for i in sub)
-    # sampled individuals traced one by one by the oracle (mode P)
+    assert g["n"] == want["n"] == int(dm.astype(np.int64).sum())
+    h = hashlib.sha256(g["kl"].astype("<u8").tobytes() + g["kt"].astype("<u8").tobytes()).hexdigest()
+    assert h == want["sha"]
+    assert g["K"] == want["K"]
+    assert g["stats"]["unique_events"] == want["U"]
+    assert g["stats"]["critical_events"] >= want["L"]
+    # identities: the dense ranks of the keys (the oracle's definition)
+    keys = np.stack([g["kl"], g["kt"]], axis=1)
+    uniq, inv = np.unique(keys, axis=0, return_inverse=True)
+    assert len(uniq) == g["K"] and np.array_equal(g["ids"], inv.reshape(-1).astype(np.uint64))
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_config3_full_size_sampled_parity(sampler):
+    """256 individuals of config 3 picked at random, each traced alone by the
+    oracle (mode P) to its speciation: their keys equal the device's"""
+    cfg, dm, g = _config3_gpu(sampler)
     m = oracle_model(cfg, dm)
     locs = m.sample()
-    pick = np.random.default_rng(0).choice(g["n"], size=6, replace=False)
+    assert len(locs) == g["n"]
+    pick = np.random.default_rng(100 + sampler).choice(g["n"], size=256, replace=False)
     kl, kt, _ = m.trace(locs[pick])
     assert np.array_equal(kl, g["kl"][pick]) and np.array_equal(kt, g["kt"][pick])
 
