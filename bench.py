@@ -314,12 +314,14 @@ class Single:
                                    meta_size=c.get("meta_size", 0), meta_nu=c.get("meta_nu", 0.0), tuning=tuning,
                                    sampler=sampler)
 
-    def count(self, seed=42, sampler=0):
+    def count(self, seed=42, sampler=0, stats=False):
         s = self.make(seed, dict(count_unique=1), sampler)
         s.sample()
         assert s.run()
         st = s.stats()
         s.close()
+        if stats:
+            return st
         return st["unique_events"], st["raw_events"]
 
 
@@ -372,7 +374,8 @@ def run_single(args, name, rank, world, local, pg):
     stream = torch.cuda.current_stream(dev)
     wl = Single(ind, name)
     sampler = SAMPLER[args.sampler]
-    U, R = wl.count(42, sampler)
+    cst = wl.count(42, sampler, stats=True)
+    U, R = cst["unique_events"], cst["raw_events"]
 
     sim = wl.make(42, dict(profile=1), sampler)
     log_cap = int(R) + wl.n + 4096 if args.events else 0
@@ -480,7 +483,8 @@ def run_single(args, name, rank, world, local, pg):
                    "parallelism": "replicas (one independent simulation per GPU)",
                    "l2": "flushed by a 256 MiB write between timed steps",
                    "unique_events_per_step": U, "raw_events_per_step": acc["raw_events"] / args.steps,
-                   "species": acc.get("K"), "lineages": wl.n, "tuning": ind.default_tuning()},
+                   "species": acc.get("K"), "lineages": wl.n, "tuning": ind.default_tuning(),
+                   "dedup": dedup_counts(cst)},
         "latency_ms": {"p50": pct(host_ms, 50), "p99": pct(host_ms, 99),
                        "what": "step start to the species count on the host, one simulation at a time"},
         "raw_events_per_s": acc["raw_events"] / args.steps * world / (ms_step_max * 1e-3),
@@ -504,6 +508,16 @@ def run_single(args, name, rank, world, local, pg):
         "gpu_launches": launches, "clocks": clk, "wall_s_timed": t_wall,
     }
     return line
+
+
+def dedup_counts(st):
+    """the horizon dedup's inserts in the counting pass: a warp pre-collapse
+    of equal slot keys before the table insert could save at most the
+    warp-shadowed ones"""
+    return {"inserts": st["dedup_inserts"], "slot_already_entered": st["dedup_repeats"],
+            "same_slot_same_warp_instruction": st["dedup_warp_repeats"], "rounds": st["rounds"],
+            "what": "counting pass: dedup inserts; inserts whose slot another lineage had entered; inserts "
+                    "shadowed by a lower lane of the same warp inserting the same slot in the same instruction"}
 
 
 def replicas_leg(torch, ind, wl, n, sampler, ids):
@@ -565,6 +579,7 @@ def batched_leg(args, local, sampler_name="exp"):
     st = ind.batch_run(sims, count_unique=1)
     U_each = [x["unique_events"] for x in st]
     U = sum(U_each)
+    dedup = dedup_counts(st[0])
     for x in sims:
         x.close()
     # autotuning on a probe of the same batch with short speciation times
@@ -636,7 +651,7 @@ def batched_leg(args, local, sampler_name="exp"):
         "latency_ms": {"batch": ms, "plain_alone_p50": pct(plain_lat, 50), "plain_alone_p99": pct(plain_lat, 99),
                        "what": "every species count of the batch is ready when the batch ends; plain: one "
                                "simulation's sim_run + sim_species alone"},
-        "tuning": tuned, "autotune": {"trials": n_trials, "probe_seconds": probe_s},
+        "tuning": tuned, "autotune": {"trials": n_trials, "probe_seconds": probe_s}, "dedup": dedup,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit integer)",
                      "frac": achieved / peak, "peak_source": "derived (see the headline)",
                      "ops_per_event": ops, "busiest_launch": busiest(best or {}, ops, peak)},

@@ -144,6 +144,13 @@ typedef struct {
     uint64_t critical_events; /* sum over rounds of the most events one lineage ran in the round:
                                  the dependent chain the rounds' durations are bound by (of the
                                  whole batch for sim_batch_run; 0 for served requests) */
+    /* horizon-dedup inserts (exact only with ind_tuning.count_unique, else 0;
+     * of the whole batch for sim_batch_run): all inserts, those that found
+     * their slot already entered, and those another active lane of the same
+     * warp inserted with the same slot in the same instruction */
+    uint64_t dedup_inserts;
+    uint64_t dedup_repeats;
+    uint64_t dedup_warp_repeats;
 } ind_run_stats;
 
 /* Event stream (section "Reporting Coalescence Events Independently").
@@ -239,6 +246,49 @@ ind_status sim_create(const ind_landscape* landscape, const ind_dispersal* dispe
  * ceil(fraction 2^53).  Individuals are numbered in (cell row-major, i)
  * order.  0 < fraction <= 1.  *n_sampled receives the count (may be NULL). */
 ind_status sim_sample(ind_sim* sim, double fraction, uint64_t sample_seed, uint64_t* n_sampled);
+
+/* Isolated partitions (section "Isolated Partitioning" of the paper's
+ * parallelisation strategies, and its limit analysis): the sampled
+ * individuals of one simulation are split into n_parts disjoint parts, each
+ * simulated on its own (one per GPU, or one after another) with no
+ * communication; lineages of different parts that meet are simulated twice.
+ * Because every lineage of the Independent algorithm depends only on
+ * (seed, location, time), an individual's speciation key is the same in its
+ * part as in the whole simulation, so the only exchange is a merge of the
+ * parts' distinct keys into global species identities at the end
+ * (ind_keys_unique, ind_keys_rank).
+ *   IND_PARTITION_LANDSCAPE: part p holds the individuals of the cells in the
+ *     rows y with floor(y n_parts / height) == p (horizontal bands; lineages
+ *     that stay near their band rarely meet another part's);
+ *   IND_PARTITION_INDIVIDUALS: part p holds the sampled individuals whose
+ *     index j in the whole sample's order has j mod n_parts == p. */
+#define IND_PARTITION_LANDSCAPE 0
+#define IND_PARTITION_INDIVIDUALS 1
+
+/* sim_sample restricted to part `part` (0 <= part < n_parts) of the sample
+ * under `scheme`: the part's individuals in the whole sample's order.
+ * n_parts = 1 is sim_sample.  IND_ERR_ARG for part >= n_parts, n_parts = 0 or
+ * an unknown scheme. */
+ind_status sim_sample_partition(ind_sim* sim, double fraction, uint64_t sample_seed, uint32_t part,
+                                uint32_t n_parts, int32_t scheme, uint64_t* n_sampled);
+
+/* The distinct speciation keys among n (location, time-bits) pairs, sorted
+ * ascending by (location, time bits), into out_loc / out_time (n entries of
+ * room each) and their count into *n_out (host).  Inputs and outputs are
+ * device pointers, owned by the caller; n <= 2^31.  Scratch comes from the
+ * allocator hook (IND_ERR_OOM if it fails).  Work is issued on `stream` and
+ * finished before return.  Section "A Neutral Coalescence-based
+ * Simulation": a species is a distinct speciation event. */
+ind_status ind_keys_unique(const uint64_t* key_loc, const uint64_t* key_time, uint64_t n, uint64_t* out_loc,
+                           uint64_t* out_time, uint64_t* n_out, void* stream);
+
+/* The global species identity of each of n keys: its index among n_ref
+ * distinct reference keys sorted ascending (the output of ind_keys_unique
+ * over every part's distinct keys), into rank_out[n].  Device pointers,
+ * caller-owned; a key missing from the reference gives IND_ERR_ARG (its
+ * entry is UINT64_MAX).  Issued on `stream`, finished before return. */
+ind_status ind_keys_rank(const uint64_t* key_loc, const uint64_t* key_time, uint64_t n, const uint64_t* ref_loc,
+                         const uint64_t* ref_time, uint64_t n_ref, uint64_t* rank_out, void* stream);
 
 /* Enable the event log of the next run (capacity: raw events the device may
  * hold, duplicates and one entry per deduplicated lineage included,

@@ -18,6 +18,7 @@ import numpy as np
 
 NONSPATIAL, TORUS, MAP, IMPLICIT = 0, 1, 2, 3
 SAMPLER_EXP, SAMPLER_POISSON = 0, 1
+PARTITION_LANDSCAPE, PARTITION_INDIVIDUALS = 0, 1
 DISPERSAL_UNIFORM, DISPERSAL_GAUSSIAN, DISPERSAL_ALIAS_GAUSSIAN = 0, 1, 2
 
 STATUS = {0: "IND_OK", -1: "IND_ERR_ARG", -2: "IND_ERR_OOM", -3: "IND_ERR_CUDA", -4: "IND_ERR_BUDGET",
@@ -51,7 +52,9 @@ class RunStats(ctypes.Structure):
                                                "n_species", "n_roots")] + \
                [("ms_total", ctypes.c_double), ("advance_ms", ctypes.c_double),
                 ("advance_launches", ctypes.c_uint64), ("busiest_launch_ms", ctypes.c_double),
-                ("busiest_launch_events", ctypes.c_uint64), ("critical_events", ctypes.c_uint64)]
+                ("busiest_launch_events", ctypes.c_uint64), ("critical_events", ctypes.c_uint64),
+                ("dedup_inserts", ctypes.c_uint64), ("dedup_repeats", ctypes.c_uint64),
+                ("dedup_warp_repeats", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -90,6 +93,12 @@ EXPORTS = {
     "sim_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64,
                                   ctypes.c_void_p, ctypes.c_void_p]),
     "sim_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p]),
+    "sim_sample_partition": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_uint32, ctypes.c_int32, ctypes.c_void_p]),
+    "ind_keys_unique": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ind_keys_rank": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "sim_species": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sim_species_keys": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -268,6 +277,14 @@ class Simulation:
         self.n_sampled = int(n.value)
         return self.n_sampled
 
+    def sample_partition(self, part, n_parts, scheme=PARTITION_LANDSCAPE, fraction=1.0, sample_seed=0):
+        """sim_sample_partition: only part `part` of n_parts of the sample"""
+        n = ctypes.c_uint64(0)
+        _check(lib().sim_sample_partition(self._h, float(fraction), int(sample_seed), int(part), int(n_parts),
+                                          int(scheme), ctypes.byref(n)), "sim_sample_partition")
+        self.n_sampled = int(n.value)
+        return self.n_sampled
+
     def run(self, round_budget=0):
         """run until finished (True) or the round budget is used (False)"""
         st = RunStats()
@@ -328,8 +345,16 @@ class Simulation:
                                    ctypes.byref(n)), "sim_alias_row")
         return out
 
-    def species_keys(self):
-        """(speciation location, time bits) per sampled individual, uint64 numpy arrays"""
+    def species_keys(self, device=False):
+        """(speciation location, time bits) per sampled individual, uint64
+        numpy arrays (device=True: device tensors)"""
+        if device:
+            torch = _torch()
+            kl = torch.empty(max(self.n_sampled, 1), dtype=torch.uint64, device="cuda")
+            kt = torch.empty(max(self.n_sampled, 1), dtype=torch.uint64, device="cuda")
+            _check(lib().sim_species_keys(self._h, ctypes.c_void_p(kl.data_ptr()), ctypes.c_void_p(kt.data_ptr())),
+                   "sim_species_keys")
+            return kl[:self.n_sampled], kt[:self.n_sampled]
         kl = np.zeros(self.n_sampled, dtype=np.uint64)
         kt = np.zeros(self.n_sampled, dtype=np.uint64)
         _check(lib().sim_species_keys(self._h, ctypes.c_void_p(kl.ctypes.data), ctypes.c_void_p(kt.ctypes.data)),
@@ -434,6 +459,33 @@ def species_rank_static(key_loc, key_time, out, stream=None):
                                          int(key_loc.numel()), ctypes.c_void_p(out.data_ptr()), ctypes.byref(n),
                                          _stream(stream)), "ind_species_rank_static")
     return int(n.value)
+
+
+def keys_unique(key_loc, key_time, stream=None):
+    """ind_keys_unique: the sorted distinct (location, time bits) keys of two
+    device uint64 tensors, as two new device tensors"""
+    torch = _torch()
+    n = int(key_loc.numel())
+    ol = torch.empty(max(n, 1), dtype=torch.uint64, device=key_loc.device)
+    ot = torch.empty(max(n, 1), dtype=torch.uint64, device=key_loc.device)
+    k = ctypes.c_uint64(0)
+    _check(lib().ind_keys_unique(ctypes.c_void_p(key_loc.data_ptr()), ctypes.c_void_p(key_time.data_ptr()), n,
+                                 ctypes.c_void_p(ol.data_ptr()), ctypes.c_void_p(ot.data_ptr()), ctypes.byref(k),
+                                 _stream(stream)), "ind_keys_unique")
+    return ol[:k.value], ot[:k.value]
+
+
+def keys_rank(key_loc, key_time, ref_loc, ref_time, stream=None):
+    """ind_keys_rank: each key's index among the sorted distinct reference
+    keys (device tensors), as a device uint64 tensor"""
+    torch = _torch()
+    n = int(key_loc.numel())
+    out = torch.empty(max(n, 1), dtype=torch.uint64, device=key_loc.device)
+    _check(lib().ind_keys_rank(ctypes.c_void_p(key_loc.data_ptr()), ctypes.c_void_p(key_time.data_ptr()), n,
+                               ctypes.c_void_p(ref_loc.data_ptr()), ctypes.c_void_p(ref_time.data_ptr()),
+                               int(ref_loc.numel()), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "ind_keys_rank")
+    return out[:n]
 
 
 def kernel_launches():

@@ -1,8 +1,8 @@
 // engine.cu -- kernels and C ABI of the Independent-algorithm engine: one
 // translation unit made of the engine_*.cuh parts included at the end of this
 // file, in order (state, per-lineage event arithmetic, round kernels, species
-// and event-stream reduction, inputs, batch host side, C ABI, allocation-free
-// ranking, server).
+// and event-stream reduction, inputs, batch host side, C ABI, the merge of
+// isolated partitions, allocation-free ranking, server).
 //
 // One engine serves a single simulation and a batch of uneven simulations
 // alike: the lineages of all simulations of a batch share structure-of-arrays
@@ -56,5 +56,6 @@ using namespace indep;
 #include "engine_inputs.cuh"
 #include "engine_batch.cuh"
 #include "engine_api.cuh"
+#include "engine_partition.cuh"
 #include "engine_rank_static.cuh"
 #include "engine_server.cuh"

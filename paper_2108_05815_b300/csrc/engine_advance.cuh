@@ -477,11 +477,13 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     uint32_t lane_max = 0;  // most events of one lineage this round (the same in every lane)
     WarpLogBuf wlog;
     wlog.n = 0;
-    // this warp's alias-row buffer (map lineages; after the tables)
-    uint64_t* const sbuf = (uint64_t*)(adv_smem + B.stage_off + (size_t)(threadIdx.x >> 5) * B.stage_bytes);
+    // this warp's alias-row buffer (map lineages; after the tables): its
+    // mbarrier, then the row
+    unsigned char* const sbuf = adv_smem + B.stage_off + (size_t)(threadIdx.x >> 5) * B.stage_bytes;
+    RowStage rs;
+    rs.pending = false;
+    if (B.stage_bytes) rs = row_stage_init(sbuf, lane);
     for (;;) {
-        // the previous lineage's last row copy lands before the buffer is reused
-        if (B.stage_bytes) asm volatile("cp.async.wait_all;" ::: "memory");
         uint32_t k = 0;
         if (lane == 0) k = atomicAdd(&B.G->work_ctr, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         uint32_t ev_lin = 0;
         // a map lineage's alias row, staged in the warp's buffer
         const bool stage = B.stage_bytes && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP));
-        const uint64_t* srow = stage ? stage_alias_row(sbuf, B.P, c, loc, lane) : nullptr;
+        const uint64_t* srow = stage ? row_stage_issue(rs, sbuf, B.P, c, loc, lane, B) : nullptr;
         for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
             if ((uint64_t)__double_as_longlong(tn) > hz) {
                 if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
@@ -531,13 +533,13 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             const uint64_t at = loc;
-            if (stage) alias_row_wait();
+            if (stage) row_stage_wait(rs, B);
             const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane, srow);
             if (LOG) {
                 warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
                 tprev = tn;
             }
-            if (!speciated && stage) srow = stage_alias_row(sbuf, B.P, c, loc, lane);
+            if (!speciated && stage) srow = row_stage_issue(rs, sbuf, B.P, c, loc, lane, B);
             else if (!speciated && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP)))
                 prefetch_alias_row(B.P, c, loc, lane);
             if (speciated) {
@@ -574,6 +576,8 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             tn = nt;
         }
     }
+    // a row copy still in flight lands before the block's shared memory goes
+    row_stage_wait(rs, B);
     if (lane == 0 && cnt_sim != 0xFFFFFFFFu) {
         atomicAdd((unsigned long long*)&B.S[cnt_sim].raw_events, (unsigned long long)ev_raw);
         if (COUNT) atomicAdd((unsigned long long*)&B.S[cnt_sim].unique_events, (unsigned long long)ev_unique);

@@ -238,8 +238,14 @@ ind_status sim_create(const ind_landscape* L, const ind_dispersal* D, double nu,
     return IND_OK;
 }
 
-ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_t* n_sampled) {
+// the sample of partition `part` of n_parts (n_parts = 1: the whole sample)
+static ind_status sample_impl(ind_sim* m, double fraction, uint64_t sample_seed, uint32_t part, uint32_t n_parts,
+                              int32_t scheme, uint64_t* n_sampled) {
     if (!m || !(fraction > 0.0 && fraction <= 1.0)) return IND_ERR_ARG;
+    if (n_parts == 0 || part >= n_parts) return IND_ERR_ARG;
+    if (n_parts > 1 && scheme != IND_PARTITION_LANDSCAPE && scheme != IND_PARTITION_INDIVIDUALS) return IND_ERR_ARG;
+    const bool band = n_parts > 1 && scheme == IND_PARTITION_LANDSCAPE;
+    const uint32_t stride = n_parts > 1 && scheme == IND_PARTITION_INDIVIDUALS ? n_parts : 1u;
     if (m->batch) {
         delete m->batch;
         m->batch = nullptr;
@@ -269,9 +275,9 @@ ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_
     seed_key(sample_seed, &sk0, &sk1);
     const uint64_t thr = (uint64_t)std::ceil(fraction * 0x1p53);
     const uint32_t sms = sm_count();
-    k_sample_flags<<<grid_for(n_slots, 256, sms * 32), 256, 0, s>>>(flags, n_slots, m->land.kind, m->land.width,
-                                                                   m->land.deme, m->slot_deme, m->d_deme,
-                                                                   fraction >= 1.0 ? 1 : 0, sk0, sk1, thr);
+    k_sample_flags<<<grid_for(n_slots, 256, sms * 32), 256, 0, s>>>(
+        flags, n_slots, m->land.kind, m->land.width, m->land.deme, m->slot_deme, m->d_deme, fraction >= 1.0 ? 1 : 0,
+        sk0, sk1, thr, m->land.height, band ? part : 0u, band ? n_parts : 1u);
     g_launches.fetch_add(1);
     ind_status st = scan_u32(tmp, flags, pos, (uint32_t)n_slots, false, s);
     if (st != IND_OK) {
@@ -286,7 +292,9 @@ ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_
         tmp.release_all();
         return IND_ERR_CUDA;
     }
-    const uint64_t count = (uint64_t)last_pos + last_flag;
+    const uint64_t flagged = (uint64_t)last_pos + last_flag;
+    // an individuals partition keeps every stride-th sampled individual from `part`
+    const uint64_t count = stride > 1u ? (flagged > part ? (flagged - part + stride - 1) / stride : 0) : flagged;
     m->d_sample = m->sample.get<uint64_t>(std::max<uint64_t>(count, 1));
     // result buffers are taken now, so that finishing a run (in a batch or a
     // server) allocates nothing
@@ -298,7 +306,8 @@ ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_
         return IND_ERR_OOM;
     }
     k_sample_write<<<grid_for(n_slots, 256, sms * 32), 256, 0, s>>>(flags, pos, n_slots, m->land.width,
-                                                                   m->slot_deme, m->d_sample);
+                                                                   m->slot_deme, m->d_sample, stride > 1u ? part : 0u,
+                                                                   stride);
     g_launches.fetch_add(1);
     tmp.release_all();
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
@@ -310,6 +319,15 @@ ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_
     m->stats.n_sampled = count;
     if (n_sampled) *n_sampled = count;
     return IND_OK;
+}
+
+ind_status sim_sample(ind_sim* m, double fraction, uint64_t sample_seed, uint64_t* n_sampled) {
+    return sample_impl(m, fraction, sample_seed, 0, 1, IND_PARTITION_LANDSCAPE, n_sampled);
+}
+
+ind_status sim_sample_partition(ind_sim* m, double fraction, uint64_t sample_seed, uint32_t part,
+                                uint32_t n_parts, int32_t scheme, uint64_t* n_sampled) {
+    return sample_impl(m, fraction, sample_seed, part, n_parts, scheme, n_sampled);
 }
 
 ind_status sim_set_tuning(ind_sim* m, const ind_tuning* t) {

@@ -497,7 +497,8 @@ static ind_status batch_build(Batch& b) {
     b.coop_smem = ln_bytes + pois_bytes + gauss_bytes + off_bytes;
     d.stage_off = d.stage_bytes = 0;
     if (n_off_max) {
-        const size_t per = ((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15;  // a row from a 16-byte boundary
+        // the warp's mbarrier slot, then a row copied from a 16-byte boundary
+        const size_t per = ROW_BAR_BYTES + (((size_t)n_off_max * 8 + 8 + 15) & ~(size_t)15);
         const size_t total = b.coop_smem + (size_t)(b.tun.block_threads / 32) * per;
         if (total <= coop_smem_limit()) {
             d.stage_off = (uint32_t)b.coop_smem;
@@ -1003,6 +1004,9 @@ static ind_status batch_run(Batch& b, uint64_t round_budget) {
         m->stats.busiest_launch_ms = b.best_launch_ms;
         m->stats.busiest_launch_events = b.best_launch_events;
         m->stats.critical_events = b.h_g_valid ? b.h_g->critical_events : 0;
+        m->stats.dedup_inserts = b.h_g_valid ? b.h_g->ins_total : 0;
+        m->stats.dedup_repeats = b.h_g_valid ? b.h_g->ins_repeat : 0;
+        m->stats.dedup_warp_repeats = b.h_g_valid ? b.h_g->ins_warp_repeat : 0;
     }
     return result;
 }

@@ -27,9 +27,11 @@ struct LaneSim {
     const uint32_t* gauss_guide;
     // spatially implicit model
     uint64_t meta_size, m_thr, meta_nu_thr;
-    // habitat map: offsets of the dispersal kernel and their count
+    // habitat map: offsets of the dispersal kernel and their count, and the
+    // alias rows (register copies: the row address is on the event chain)
     uint32_t n_off;
     const int8_t* off;
+    const uint64_t* alias;
 };
 
 __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __restrict__ P,
@@ -60,6 +62,7 @@ __device__ __forceinline__ void load_lanesim(LaneSim& c, const SimParams* __rest
     c.meta_nu_thr = __ldg(&p->meta_nu_thr);
     c.n_off = __ldg(&p->n_off);
     c.off = p->off;
+    c.alias = p->alias;
     c.horizon = *(volatile const double*)&S[sim].horizon;
 }
 
@@ -655,7 +658,6 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
                                             const uint64_t* srow = nullptr) {
     const int kind = KIND >= 0 ? KIND : c.kind;
     if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
-    const SimParams* p = P + c.sim;
     if (kind == KIND_IMPLICIT) {
         // in the metacommunity: a uniform parent there (d1); locally:
         // migration iff d1 says so, then the parent's index (d2) in the
@@ -688,7 +690,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     // carries the target deme (k_alias_build), then the offset table (L1)
     const uint32_t n_off = c.n_off;
     const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
-    const uint64_t e = srow ? srow[col] : __ldg(p->alias + ((size_t)y * c.W + x) * n_off + col);
+    const uint64_t e = srow ? srow[col] : __ldg(c.alias + ((size_t)y * c.W + x) * n_off + col);
     const uint32_t u = (uint32_t)d1;
     const bool take_col = (e >> 63) != 0 || u < (uint32_t)e;
     const uint32_t o = take_col ? col : (uint32_t)((e >> 32) & (ALIAS_MAX_OFFSETS - 1u));
@@ -714,31 +716,84 @@ __device__ __forceinline__ void prefetch_alias_row(const SimParams* __restrict__
     for (uint32_t o = lane * 128u; o < bytes; o += 32u * 128u) asm volatile("prefetch.global.L1 [%0];" ::"l"(row + o));
 }
 
-// The warp kernel's alternative: copy the row into the warp's shared-memory
-// buffer (cp.async, 16-byte pieces from the 16-byte boundary at or below the
-// row's start; the allocation has two entries of padding for the last row)
-// while the search runs.  Returns the buffer address of the row's entry 0.
-// Every lane issues its pieces and one commit; alias_row_wait() makes the
-// whole row visible to every lane of the warp.
-__device__ __forceinline__ const uint64_t* stage_alias_row(uint64_t* buf, const SimParams* __restrict__ P,
-                                                           const LaneSim& c, uint64_t loc, uint32_t lane) {
-    const SimParams* p = P + c.sim;
-    const uint32_t n_off = __ldg(&p->n_off);
-    const uint64_t* row = p->alias + ((size_t)loc_y(loc) * c.W + loc_x(loc)) * n_off;
-    const uintptr_t a = (uintptr_t)row;
-    const char* src = (const char*)(a & ~(uintptr_t)15);
-    const uint32_t lead = (uint32_t)(a & 15u);  // 0 or 8
-    const uint32_t pieces = (lead + n_off * 8u + 15u) >> 4;
-    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
-    for (uint32_t k = lane; k < pieces; k += 32u)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16u * k), "l"(src + 16u * k) : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    return buf + (lead >> 3);
+// The warp kernel's alternative: one bulk copy (TMA, cp.async.bulk) brings
+// the row into the warp's shared-memory buffer while the search runs.  Lane
+// 0 issues it from the 16-byte boundary at or below the row's start (the
+// allocation has two entries of padding after the last row), with an
+// mbarrier that counts the bytes in; the dispersal waits on that barrier.
+// The warp's buffer starts with its 16-byte barrier slot, then the row.
+constexpr uint32_t ROW_BAR_BYTES = 16;
+constexpr uint32_t ROW_WAIT_LIMIT = 1u << 24;  // try_wait rounds before a wait gives up (error bit 16)
+
+struct RowStage {
+    uint32_t bar;      // shared address of the warp's mbarrier
+    uint32_t data;     // shared address of the row buffer (16-byte aligned)
+    uint32_t issued;   // copies issued so far (the last one completes phase issued - 1)
+    bool pending;      // a copy is issued and not yet waited for
+};
+
+__device__ __forceinline__ RowStage row_stage_init(unsigned char* warp_buf, uint32_t lane) {
+    RowStage r;
+    r.bar = (uint32_t)__cvta_generic_to_shared(warp_buf);
+    r.data = r.bar + ROW_BAR_BYTES;
+    r.issued = 0;
+    r.pending = false;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(r.bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncwarp();
+    return r;
 }
 
-__device__ __forceinline__ void alias_row_wait() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
+// every lane waits until the last issued copy has landed (bounded; on the
+// limit the device error bit 16 is set and the row is not used for results:
+// the run fails)
+__device__ __forceinline__ void row_stage_wait(RowStage& r, const BatchDev& B) {
+    if (!r.pending) return;
+    const uint32_t parity = (r.issued - 1u) & 1u;
+    uint32_t done = 0;
+    // the copy was issued a whole search earlier: it has almost always landed
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(r.bar), "r"(parity)
+                 : "memory");
+    for (uint32_t it = 0; it < ROW_WAIT_LIMIT && !done; ++it)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(r.bar), "r"(parity)
+                     : "memory");
+    if (!done) atomicOr(&B.G->error, 16u);
+    r.pending = false;
     __syncwarp();
+}
+
+// stage the alias row of loc's cell; returns the buffer address of entry 0
+__device__ __forceinline__ const uint64_t* row_stage_issue(RowStage& r, unsigned char* warp_buf,
+                                                           const SimParams* __restrict__ P, const LaneSim& c,
+                                                           uint64_t loc, uint32_t lane, const BatchDev& B) {
+    row_stage_wait(r, B);  // a copy still in flight lands before the buffer is written again
+    const uint32_t n_off = c.n_off;
+    const uint64_t* row = c.alias + ((size_t)loc_y(loc) * c.W + loc_x(loc)) * n_off;
+    const uintptr_t a = (uintptr_t)row;
+    const uint32_t lead = (uint32_t)(a & 15u);  // 0 or 8
+    const uint32_t bytes = (lead + n_off * 8u + 15u) & ~15u;
+    __syncwarp();  // every lane has read the previous row
+    // lane 0 issues, predicated rather than branched, so that the warp does
+    // not diverge and the issue can overlap the search that follows
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.eq.u32 p, %0, 0;\n\t"
+        "@p fence.proxy.async.shared::cta;\n\t"
+        "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t"
+        "@p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%3], [%4], %2, [%1];\n\t"
+        "}" ::"r"(lane),
+        "r"(r.bar), "r"(bytes), "r"(r.data), "l"(a & ~(uintptr_t)15)
+        : "memory");
+    r.issued += 1u;
+    r.pending = true;
+    return (const uint64_t*)(warp_buf + ROW_BAR_BYTES + lead);
 }
 
 // speciation threshold at loc: the metacommunity's in the spatially
@@ -888,6 +943,13 @@ __device__ __forceinline__ void warp_log_event(const BatchDev& B, WarpLogBuf& w,
 }
 
 __device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint64_t skey, uint32_t gid) {
+    if (B.count_unique) {
+        const unsigned act = __activemask();
+        const unsigned same = __match_any_sync(act, skey);
+        const bool shadowed = (same & ((1u << (threadIdx.x & 31u)) - 1u)) != 0u;
+        atomicAdd(&B.G->ins_total, 1ull);
+        if (shadowed) atomicAdd(&B.G->ins_warp_repeat, 1ull);
+    }
     const uint32_t mask = B.G->mask[t];
     uint32_t h = (uint32_t)mix64(skey) & mask;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
@@ -899,6 +961,7 @@ __device__ __forceinline__ void dedup_insert(const BatchDev& B, uint32_t t, uint
             return;
         }
         if (old == skey) {
+            if (B.count_unique) atomicAdd(&B.G->ins_repeat, 1ull);
             atomicMin(&B.ht_val[t][h], gid);
             return;
         }

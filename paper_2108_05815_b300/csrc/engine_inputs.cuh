@@ -109,15 +109,17 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
     }
 }
 
+// band: a landscape partition keeps only the cells of rows y with
+// floor(y n_parts / H) == part (n_parts = 1: every row)
 __global__ void k_sample_flags(uint32_t* flags, uint64_t n_slots, int kind, uint32_t W, uint32_t D,
                                uint32_t slot_deme, const uint8_t* deme, int all, uint32_t sk0, uint32_t sk1,
-                               uint64_t thr) {
+                               uint64_t thr, uint32_t H, uint32_t part, uint32_t n_parts) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
          s += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t cell = s / slot_deme;
         const uint32_t i = (uint32_t)(s % slot_deme);
         const uint32_t d = kind == KIND_MAP ? deme[cell] : D;
-        bool keep = i < d;
+        bool keep = i < d && (n_parts <= 1u || (cell / W) * n_parts / H == part);
         if (keep && !all) {
             const uint64_t loc = pack_loc(cell % W, cell / W, i);
             keep = (stream_block(sk0, sk1, loc, 0, 0, TAG_SAMPLE).lo >> 11) < thr;
@@ -126,13 +128,17 @@ __global__ void k_sample_flags(uint32_t* flags, uint64_t n_slots, int kind, uint
     }
 }
 
+// stride > 1: an individuals partition keeps the sampled individuals whose
+// sample index j has j mod stride == part, as entry j / stride
 __global__ void k_sample_write(const uint32_t* flags, const uint32_t* pos, uint64_t n_slots, uint32_t W,
-                               uint32_t slot_deme, uint64_t* out) {
+                               uint32_t slot_deme, uint64_t* out, uint32_t part, uint32_t stride) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < n_slots;
          s += (uint64_t)gridDim.x * blockDim.x) {
         if (!flags[s]) continue;
+        const uint32_t j = pos[s];
+        if (stride > 1u && j % stride != part) continue;
         const uint64_t cell = s / slot_deme;
-        out[pos[s]] = pack_loc(cell % W, cell / W, s % slot_deme);
+        out[j / stride] = pack_loc(cell % W, cell / W, s % slot_deme);
     }
 }
 

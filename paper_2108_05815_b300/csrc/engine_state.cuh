@@ -182,6 +182,11 @@ struct Globals {
     uint32_t round_max;               // most events one lineage ran in the running round
     unsigned long long critical_events;  // sum of round_max over completed rounds
     unsigned long long log_n;            // events appended to the event log (may pass its capacity)
+    // dedup inserts, counted only in the exact-counting mode (count_unique):
+    // all of them, those whose slot key was already in the table, and those
+    // that another active lane of the same warp inserted in the same
+    // instruction (what a warp pre-collapse of equal keys would save)
+    unsigned long long ins_total, ins_repeat, ins_warp_repeat;
 };
 
 struct __align__(16) EvSlot {

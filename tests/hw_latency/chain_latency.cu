@@ -13,6 +13,7 @@
 //   imad_hi     x = mulhi32(x, y)                       32-bit high product
 //   philox      one Philox4x32 round (two high/low product pairs, xors and
 //               the key schedule): the round's dependent path
+//   philox_split the same with the low products from run-time multipliers
 //   hi_xor      x = mulhi32(x, y) ^ z                   high product + xor
 //   umul64hi    x = mulhi64(x, y)                       64-bit high product
 //   imad_wide   x = lo64(lo32(x) * y + x)               32x32 -> 64 multiply-add
@@ -21,7 +22,6 @@
 //   lds         i = s[i]                                shared-memory load
 //   ldg_l1      i = g[i] (4 KB ring, L1-resident)       global load, L1 hit
 //   ldg_dram    i = g[i] (random ring >> L2)            global load from DRAM
-//   shfl        x = shfl(x, x)                          warp shuffle
 //   ballot      x = ballot(x & bit) ^ x                  warp vote + xor
 //   redux_min   x = redux.min(x) ^ lane-independent    warp reduction
 #include <cstdint>
@@ -58,7 +58,6 @@ CHAIN_KERNEL(umul64hi, uint64_t, prm[5], x = __umul64hi(x, a))
 CHAIN_KERNEL(imad_wide, uint64_t, prm[5], x = (uint64_t)(uint32_t)x * y + x)
 CHAIN_KERNEL(add64_sel, uint64_t, prm[5], { const uint64_t s0 = x + a; x = s0 < b ? s0 : x + c; })
 CHAIN_KERNEL(clz_norm, uint64_t, prm[5], x = (x << __clzll((long long)x)) ^ a)
-CHAIN_KERNEL(shfl, uint32_t, prm[5], x = __shfl_sync(0xFFFFFFFFu, x, x))
 CHAIN_KERNEL(ballot, uint32_t, prm[5], x = __ballot_sync(0xFFFFFFFFu, (x >> (threadIdx.x & 31u)) & 1u) ^ z)
 CHAIN_KERNEL(redux_min, uint32_t, prm[5], x = __reduce_min_sync(0xFFFFFFFFu, x ^ threadIdx.x) + z)
 
@@ -79,6 +78,35 @@ __global__ void k_philox(const uint64_t* __restrict__ prm, Out* out) {
         for (int s = 0; s < 64; ++s) {
             const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
             const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+            c0 = hi1 ^ c1 ^ k0;
+            c1 = lo1;
+            c2 = hi0 ^ c3 ^ k1;
+            c3 = lo0;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += (unsigned long long)(c0 ^ c1 ^ c2 ^ c3);
+}
+
+// the same round with the low products taken from multipliers read at run
+// time (equal to the constants), so that each high product stays a lone
+// high-half multiply rather than one wide multiply giving both halves
+__constant__ uint32_t c_zero = 0;
+__global__ void k_philox_split(const uint64_t* __restrict__ prm, Out* out) {
+    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
+    const uint32_t m0 = 0xD2511F53u ^ c_zero, m1 = 0xCD9E8D57u ^ c_zero;
+    __syncwarp();
+    const unsigned long long t0 = clk();
+#pragma unroll 1
+    for (int it = 0; it < STEPS / 64; ++it) {
+#pragma unroll
+        for (int s = 0; s < 64; ++s) {
+            const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = m0 * c0;
+            const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = m1 * c2;
             c0 = hi1 ^ c1 ^ k0;
             c1 = lo1;
             c2 = hi0 ^ c3 ^ k1;
@@ -158,7 +186,7 @@ double hwlat_clock_mhz(unsigned long long cycles, void* out_dev) {
 int hwlat_steps() { return STEPS; }
 
 // class ids: 0 imad_hi, 1 hi_xor, 2 umul64hi, 3 imad_wide, 4 add64_sel,
-// 5 clz_norm, 6 add_xor, 7 shfl, 8 ballot, 9 redux_min, 10 philox, 11 lds
+// 5 clz_norm, 6 add_xor, 8 ballot, 9 redux_min, 10 philox, 11 lds, 12 philox_split
 // Runs the chain once in one warp of one block; returns its cycles, or a
 // negative CUDA error.  prm: 6 device words of runtime operands.
 long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
@@ -171,11 +199,11 @@ long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
         case 4: k_add64_sel<<<1, 32>>>(prm, o); break;
         case 5: k_clz_norm<<<1, 32>>>(prm, o); break;
         case 6: k_add_xor<<<1, 32>>>(prm, o); break;
-        case 7: k_shfl<<<1, 32>>>(prm, o); break;
         case 8: k_ballot<<<1, 32>>>(prm, o); break;
         case 9: k_redux_min<<<1, 32>>>(prm, o); break;
         case 10: k_philox<<<1, 32>>>(prm, o); break;
         case 11: k_lds<<<1, 32>>>(prm, o); break;
+        case 12: k_philox_split<<<1, 32>>>(prm, o); break;
         default: return -1;
     }
     cudaError_t e = cudaDeviceSynchronize();

@@ -98,7 +98,21 @@ def test_null_arguments(lib):
     assert lib.sim_run(None, 0, None) == -1
     assert lib.sim_species(None, None, None) == -1
     assert lib.sim_batch_run(None, 0, None, None) == -1
+    assert lib.sim_sample_partition(None, 1.0, 0, 0, 2, 0, None) == -1
     lib.sim_destroy(None)
+
+
+def test_partition_merge_arguments(lib):
+    """the merge entry points reject bad sizes and null outputs before any
+    device work, and accept empty inputs without touching the GPU"""
+    n = ctypes.c_uint64(7)
+    assert lib.ind_keys_unique(None, None, 0, None, None, None, None) == -1      # no count output
+    assert lib.ind_keys_unique(None, None, 0, None, None, ctypes.byref(n), None) == 0 and n.value == 0
+    assert lib.ind_keys_unique(None, None, 5, None, None, ctypes.byref(n), None) == -1
+    assert lib.ind_keys_unique(ctypes.c_void_p(8), ctypes.c_void_p(8), (1 << 31) + 1, ctypes.c_void_p(8),
+                               ctypes.c_void_p(8), ctypes.byref(n), None) == -1
+    assert lib.ind_keys_rank(None, None, 0, None, None, 0, None, None) == 0
+    assert lib.ind_keys_rank(None, None, 3, None, None, 0, None, None) == -1
 
 
 def test_mem_estimate_is_host_only_and_monotone(lib):

@@ -170,6 +170,21 @@ def test_unique_event_count_matches_oracle(cfg):
     assert g["stats"]["unique_events"] == o["U"]
 
 
+def test_dedup_insert_counts():
+    """the exact-counting mode also counts the horizon dedup's inserts: all,
+    those whose slot was already entered, and those shadowed by a lower lane
+    of the same warp with the same slot in the same instruction (each of
+    which finds its slot entered); without counting, and with the dedup off,
+    nothing is counted"""
+    cfg = dict(kind=W.TORUS, width=64, height=64, deme=1, sigma=2.0, nu=1e-3, seed=3)
+    st = run_gpu(cfg, tuning=dict(count_unique=1, coop_lineages=0))["stats"]
+    assert st["dedup_inserts"] > 0 and st["dedup_inserts"] >= st["dedup_repeats"] >= st["dedup_warp_repeats"] >= 0
+    assert st["dedup_repeats"] > 0  # lineages meet on a 64 x 64 torus
+    for tun in (dict(), dict(count_unique=1, dedup=0)):
+        st = run_gpu(cfg, tuning=tun)["stats"]
+        assert st["dedup_inserts"] == st["dedup_repeats"] == st["dedup_warp_repeats"] == 0
+
+
 # --------------------------------------------------------------------------
 # invariants: tuning, dedup, graphs, batching, resumption
 # --------------------------------------------------------------------------

@@ -7,6 +7,8 @@ scratch is a fixed device array inside the library.  Two calls in a row on
 different inputs check that a call does not see the previous call's leftovers.
 This file is collected last on purpose.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -60,3 +62,35 @@ def test_static_rank_rejects_too_many_and_handles_empty(torch_cuda):
     assert e.value.status == -1
     empty = torch.zeros(0, dtype=torch.int64, device="cuda")
     assert ind.species_rank_static(empty, empty, empty) == 0
+
+
+def test_static_rank_allocates_nothing(torch_cuda):
+    """its defining property: with an allocator hook that counts every call
+    and refuses every request installed, the call still succeeds, the hook is
+    never called, and torch's allocated device memory is unchanged"""
+    torch = torch_cuda
+    ids_ref, K_ref, kl, kt = _reference(kind=ind.TORUS, nu=2e-3, seed=5, width=64, height=48, deme=1, sigma=2.0)
+    dl = torch.from_numpy(kl.view(np.int64)).cuda()
+    dt = torch.from_numpy(kt.view(np.int64)).cuda()
+    out = torch.full((kl.size,), -1, dtype=torch.int64, device="cuda")
+    calls = {"n": 0}
+
+    def alloc(nbytes, stream, ctx):
+        calls["n"] += 1
+        return None
+
+    def release(ptr, nbytes, stream, ctx):
+        calls["n"] += 1
+
+    refusing = ind.Allocator(ind._ALLOC(alloc), ind._RELEASE(release), None)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    assert ind.lib().ind_set_allocator(ctypes.byref(refusing)) == 0
+    try:
+        K = ind.species_rank_static(dl, dt, out)
+        torch.cuda.synchronize()
+    finally:
+        assert ind.lib().ind_set_allocator(ctypes.byref(ind._torch_alloc)) == 0
+    assert calls["n"] == 0
+    assert torch.cuda.memory_allocated() == before
+    assert K == K_ref and np.array_equal(out.cpu().numpy().view(np.uint64), ids_ref)
