@@ -15,9 +15,12 @@ Default run (one JSON line):
             (autotuned launch shape, CUDA-graph chunks) against the plain
             path (one simulation per sim_run), in unique events per second.
   served    config 5: Poisson arrivals of torus requests into the
-            continuous-batching server; latency p50/p99 from arrival to
-            species identities, offered and achieved request rates, queue
-            length over the window.
+            continuous-batching server at the highest rate this build
+            sustains (10 requests/s: the requests in the system stay
+            bounded), and at the specified 50 requests/s over a short
+            window (beyond capacity); latency p50/p99 from arrival to
+            species identities, offered and achieved request rates, drain
+            time, requests in the system once a second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload all|config2|config3|implicit|batch|served]
@@ -66,10 +69,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--batch-steps", type=int, default=2, help="config 4: timed batches")
     ap.add_argument("--plain-subset", type=int, default=32, help="config 4: simulations timed one by one")
-    ap.add_argument("--served-rate", type=float, default=50.0, help="config 5: offered requests per second")
-    ap.add_argument("--served-window", type=float, default=6.0, help="config 5: arrival window in seconds")
-    ap.add_argument("--served-plain", type=int, default=12,
+    ap.add_argument("--served-rate", type=float, default=10.0,
+                    help="config 5: offered requests per second (10: the highest rate this build sustains)")
+    ap.add_argument("--served-window", type=float, default=20.0, help="config 5: arrival window in seconds")
+    ap.add_argument("--served-plain", type=int, default=8,
                     help="config 5: requests re-run one by one on the plain path (0: none)")
+    ap.add_argument("--served-spec-window", type=float, default=4.0,
+                    help="config 5 at its specified 50 requests/s: arrival window in seconds (0: skip)")
     ap.add_argument("--replicas", type=int, default=16,
                     help="single workloads: replicas in the batched-vs-plain comparison")
     ap.add_argument("--events", action="store_true",
@@ -83,6 +89,7 @@ def parse():
     ap.add_argument("--block-threads", type=int)
     ap.add_argument("--blocks-per-sm", type=int)
     ap.add_argument("--tail-events", type=float, help="case tail: events per lineage per round")
+    ap.add_argument("--map-side", type=int, default=1024, help="case config3: side of the habitat map")
     return ap.parse_args()
 
 
@@ -285,10 +292,12 @@ class Single:
     """one single-simulation workload: parameters, its map (config 3) and the
     simulations made from them"""
 
-    def __init__(self, ind, name):
+    def __init__(self, ind, name, map_side=1024):
         from paper_2108_05815_b300 import workloads as W
         self.ind, self.name = ind, name
         self.params = getattr(W, name)
+        if name == "config3" and map_side != 1024:  # a smaller map of the same recipe (profiling only)
+            self.params = lambda seed=42: W.config3(seed, side=map_side)
         self.desc = WORKLOADS[name]
         self.kind = KIND_NAME[name]
         c = self.params(42)
@@ -882,6 +891,7 @@ def run_case(args):
                 advance launch is a separate kernel launch (--events: with the
                 event stream)
       config3   the 1024 x 1024 habitat map once without CUDA graphs
+                (--map-side: a smaller map of the same recipe)
       busy      a 1024 x 1024 torus (1,048,576 lineages, sigma 2, nu 1e-3) for
                 --rounds rounds: the throughput-bound phase
       tail      one lineage, nu 1e-4 (about 10^4 events) on a non-spatial deme
@@ -906,7 +916,7 @@ def run_case(args):
     if args.tail_events:
         launch["tail_events"] = args.tail_events
     if args.case in ("config2", "config3", "implicit"):
-        wl = Single(ind, args.case)
+        wl = Single(ind, args.case, map_side=args.map_side)
         s = wl.make(42, dict(use_graph=0, profile=1, **launch), sampler)
         if args.events:
             s.set_event_log(8 << 20)
@@ -989,6 +999,8 @@ def main():
             line["batched"] = batched_leg(args, local, args.sampler)
             line["served"] = served_leg(args, local, args.served_rate, args.served_window, args.served_plain,
                                         args.sampler)
+            if args.served_spec_window > 0:
+                line["served_at_50_per_s"] = served_leg(args, local, 50.0, args.served_spec_window, 0, args.sampler)
     elif args.workload == "batch":
         b = batched_leg(args, local, args.sampler)
         line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": b["batches_timed"],
