@@ -87,8 +87,6 @@ __host__ __device__ __forceinline__ uint64_t umulhi64(uint64_t a, uint64_t b) {
 // of m, R_j = round(2^45 / (8193 + 2 j)) and 1 + s = m R_j / 2^32
 // (|s| < 2^-12.9); ln(1 + s) = s - s^2 (1/2 - s/3 + s^2/4) with s in signed
 // Q0.64 and the bracket in Q2.62.  Result in Q6.58, rounded half up.
-// The chain is built for latency: the two 64-bit high products that feed
-// the bracket run in parallel, and (53 - e) ln 2 is formed off the chain.
 // ---------------------------------------------------------------------------
 constexpr int LN_BITS = 12;
 constexpr uint32_t LN_N = 1u << LN_BITS;
@@ -100,38 +98,93 @@ struct __align__(16) LnTables {
     int64_t c3;          // round(2^64 / 3)
 };
 
-__device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64_t* __restrict__ Ltab,
-                                             const uint32_t* __restrict__ Rtab, uint64_t ln2_q64, int64_t c3) {
+// 32-bit leading zeros, funnel shift and signed 64-bit high product, on
+// the device by intrinsic, on the host (tests) in plain C++
+__host__ __device__ __forceinline__ int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+    return __clz((int)x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// high 32 bits of (hi:lo) << sh, 0 <= sh < 32
+__host__ __device__ __forceinline__ uint32_t funnel_l(uint32_t lo, uint32_t hi, int sh) {
+#ifdef __CUDA_ARCH__
+    return __funnelshift_l(lo, hi, (unsigned)sh);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) << sh >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ int64_t mulhi64s(int64_t a, int64_t b) {
+#ifdef __CUDA_ARCH__
+    return __mul64hi(a, b);
+#else
+    return (int64_t)(((__int128)a * b) >> 64);
+#endif
+}
+
+// The chain is built for latency: the normalising shift works on the high
+// word (n >= 2^32 for all but 2^-21 of the draws), the two 64-bit high
+// products that feed the bracket run in parallel, (53 - e) ln 2 plus the
+// rounding's half unit is formed off the chain, and the last step is one
+// two-word subtraction.
+__host__ __device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64_t* __restrict__ Ltab,
+                                                      const uint32_t* __restrict__ Rtab, uint64_t ln2_q64,
+                                                      int64_t c3) {
     const uint64_t n = r53 + 1ull;
-    const int lz = __clzll((long long)n);            // 10 .. 63
-    const uint64_t M = n << lz;                      // m 2^63
-    const uint32_t j = (uint32_t)(M >> (63 - LN_BITS)) & (LN_N - 1u);
+    const uint32_t nh = (uint32_t)(n >> 32), nl = (uint32_t)n;
+    int lz;            // leading zeros of n (64-bit): 10 .. 63
+    uint32_t Mh, Ml;   // m 2^63 = n << lz, as two words
+    if (nh != 0u) {
+        lz = clz32(nh);
+        Mh = funnel_l(nl, nh, lz);
+        Ml = nl << lz;
+    } else {
+        const int l = clz32(nl);
+        lz = 32 + l;
+        Mh = nl << l;
+        Ml = 0u;
+    }
+    const uint32_t j = (Mh >> (31 - LN_BITS)) & (LN_N - 1u);
     const uint32_t R = Rtab[j];   // plain loads: the tables may sit in shared or global memory
     const uint64_t Lj = Ltab[j];
-    // (53 - e) ln 2 in Q0.64, 128-bit, independent of the table lookups
+    // K = (53 - e) ln 2 + 2^5 (the half unit of the final rounding) in Q0.64,
+    // 128-bit, independent of the table lookups
     const uint64_t k = (uint64_t)(lz - 10);
     const uint64_t klo = k * ln2_q64;
-    const uint64_t khi = __umul64hi(k, ln2_q64);
+    const uint64_t Klo = klo + 32ull;
+    const uint64_t Khi = umulhi64(k, ln2_q64) + (Klo < klo ? 1ull : 0ull);
     // P = M R = (Mh R) 2^32 + Ml R; s = low 64 bits of P >> 31
-    const uint64_t pl = (uint64_t)(uint32_t)M * R;
-    const uint64_t ph = (uint64_t)(uint32_t)(M >> 32) * R;
+    const uint64_t pl = (uint64_t)Ml * R;
+    const uint64_t ph = (uint64_t)Mh * R;
     const int64_t s = (int64_t)((ph << 1) + (pl >> 31));
-    const int64_t s2 = __mul64hi(s, s);
-    const int64_t s3 = __mul64hi(s, c3);
+    const int64_t s2 = mulhi64s(s, s);
+    const int64_t s3 = mulhi64s(s, c3);
     const int64_t t = (1ll << 61) - (s3 >> 2) + (s2 >> 4);
-    const int64_t q = (int64_t)__umul64hi((uint64_t)s2, (uint64_t)t);
+    const int64_t q = (int64_t)umulhi64((uint64_t)s2, (uint64_t)t);
     const int64_t ln1p = s - (q << 2);
     const int64_t lnm = (int64_t)Lj + (ln1p >> 2);  // Q2.62
-    // x = k ln2 - 4 lnm (128-bit), clamp at 0, round half up to Q6.58
+    // x = K - 4 lnm (128-bit), 0 if negative, then the Q6.58 result x >> 6
     const uint64_t slo = (uint64_t)lnm << 2;
     const uint64_t shi = (uint64_t)(lnm >> 62);
-    const uint64_t borrow = klo < slo ? 1ull : 0ull;
-    const uint64_t xlo = klo - slo;
-    const uint64_t xhi = khi - shi - borrow;
+    const uint64_t xlo = Klo - slo;
+    const uint64_t xhi = Khi - shi - (Klo < slo ? 1ull : 0ull);
     if ((int64_t)xhi < 0) return 0ull;
-    const uint64_t rlo = xlo + 32ull;
-    const uint64_t rhi = xhi + (rlo < xlo ? 1ull : 0ull);
-    return (rhi << 58) | (rlo >> 6);
+    return (xhi << 58) | (xlo >> 6);
+}
+
+// q rounded to 53 significant bits, to nearest, ties to even (q < 2^63.5):
+// the multiple of 2^-58 that the binary64 value of q 2^-58 equals.  One add
+// and a mask: adding half an ulp less one, plus the ulp bit, carries exactly
+// when the rounding goes up.
+__host__ __device__ __forceinline__ uint64_t rn53(uint64_t q) {
+    const uint32_t qh = (uint32_t)(q >> 32);
+    const int sh = qh >= (1u << 21) ? 11 - clz32(qh) : 0;  // bits below the 53rd significant one
+    const uint64_t mask = (1ull << sh) - 1ull;
+    const uint64_t odd = (uint64_t)(((uint32_t)q >> sh) & (uint32_t)mask & 1u);  // 0 when sh = 0
+    return (q + (mask >> 1) + odd) & ~mask;
 }
 
 // round-to-nearest-even binary64 of q 2^-58 (q < 2^64), by integer assembly

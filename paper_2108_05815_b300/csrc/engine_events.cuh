@@ -104,16 +104,6 @@ __device__ __forceinline__ double exp_draw(uint64_t v, const LnC& ln, const Lane
     return __ddiv_rn(x, c.lam);
 }
 
-// q 2^-58 rounded to binary64 (53 significant bits, nearest, ties to even),
-// as the multiple of 2^-58 it equals (q < 2^63.5, so no overflow)
-__device__ __forceinline__ uint64_t rn53_q58(uint64_t q) {
-    const int lz = __clzll((long long)q);
-    if (lz >= 11) return q;  // below 2^53: exact
-    const int sh = 11 - lz;
-    const uint64_t mant = q >> sh, rem = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-    return (mant + ((rem > half || (rem == half && (mant & 1ull))) ? 1ull : 0ull)) << sh;
-}
-
 // first point of loc's event process strictly after tau; negative on overflow.
 // Times are non-negative binary64, so they order like their bit patterns: the
 // compares, floor(tau / delta_t) and k delta_t are done on the bits.  WIDE
@@ -187,7 +177,7 @@ __device__ double next_event_time_exp_int(const LaneSim& c, uint64_t loc, double
                 const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint64_t R = rn53_q58(exp1_q58((h ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+                    const uint64_t R = rn53(exp1_q58((h ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
                     fl[2 * w + h] = R >> sft;
                     uint32_t r = 0;
                     if (sft > 0) {
@@ -565,7 +555,7 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         // not depend on them and overlap their latency
         const uint64_t k = k0 + m;
         const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, i >> 1, TAG_INTERVAL);
-        const uint64_t R = rn53_q58(exp1_q58(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
+        const uint64_t R = rn53(exp1_q58(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
         const int lg0 = 63 - __clzll((long long)k0);
         const int lg3 = 63 - __clzll((long long)(k0 + 3ull));
         const int lg = 63 - __clzll((long long)k);
