@@ -565,13 +565,12 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         const uint64_t E = (k + 1ull) << sh;
         if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52))
             return coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
-        uint64_t a = R >> sft;
-        bool tie = false;
-        if (sft > 0) {
-            const uint64_t rem = R & ((1ull << sft) - 1ull), half = 1ull << (sft - 1);
-            a += rem > half ? 1ull : 0ull;
-            tie = rem == half;
-        }
+        // x / u to the nearest integer, a tie rounded down here and settled
+        // below by the parity of the sum (R + half - 1 carries exactly when
+        // the remainder is above half)
+        const uint64_t gmask = (1ull << sft) - 1ull;
+        uint64_t a = (R + (gmask >> 1)) >> sft;
+        const bool tie = sft > 0 && (R & gmask) == (gmask >> 1) + 1ull;
         // prefix sums as if no draw were a tie (rare); the tie vote runs
         // beside them and a tie redoes them.  A draw of more than 2^54 u
         // ends the interval whatever follows.
@@ -759,6 +758,33 @@ __device__ __forceinline__ void row_stage_wait(RowStage& r, const BatchDev& B) {
     __syncwarp();
 }
 
+// the wait split in two, so that its first probe overlaps the event's
+// Philox block: poll issues one try_wait and returns its answer; finish
+// acts on it only when the row is needed (bounded further probes if the
+// copy is still in flight)
+__device__ __forceinline__ uint32_t row_stage_poll(const RowStage& r) {
+    if (!r.pending) return 1u;
+    uint32_t done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(r.bar), "r"((r.issued - 1u) & 1u)
+                 : "memory");
+    return done;
+}
+
+__device__ __forceinline__ void row_stage_finish(RowStage& r, const BatchDev& B, uint32_t done) {
+    if (!r.pending) return;
+    const uint32_t parity = (r.issued - 1u) & 1u;
+    for (uint32_t it = 0; it < ROW_WAIT_LIMIT && !done; ++it)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(r.bar), "r"(parity)
+                     : "memory");
+    if (!done) atomicOr(&B.G->error, 16u);
+    r.pending = false;
+    __syncwarp();
+}
+
 // stage the alias row of loc's cell; returns the buffer address of entry 0
 __device__ __forceinline__ const uint64_t* row_stage_issue(RowStage& r, unsigned char* warp_buf,
                                                            const SimParams* __restrict__ P, const LaneSim& c,
@@ -810,26 +836,37 @@ __device__ __forceinline__ bool do_event(const LaneSim& c, const SimParams* __re
     return false;
 }
 
-// do_event for one lineage per warp: lanes of even and odd index compute
-// the event stream's blocks 0 and 1 side by side, then every lane takes the
-// four draws by shuffle (one block's latency instead of two interleaved)
+// The event's draws for one lineage per warp: lanes of even and odd index
+// compute the event stream's blocks 0 and 1 side by side, then every lane
+// takes the four draws by shuffle (one block's latency instead of two
+// interleaved).  spec: the lineage speciates.  The caller computes the move
+// from the draws whether or not it speciates and keeps it only if not, so
+// that no branch on the speciation test sits on the event chain.
+struct EventDraws {
+    uint64_t d1, d2, d3;
+    bool spec;
+};
+
 template <int KIND>
-__device__ __forceinline__ bool do_event_warp(const LaneSim& c, const SimParams* __restrict__ P, uint64_t& loc,
-                                              double tau, uint32_t lane, const uint64_t* srow = nullptr) {
+__device__ __forceinline__ EventDraws event_draws_warp(const LaneSim& c, const SimParams* __restrict__ P,
+                                                       uint64_t loc, double tau, uint32_t lane) {
     const int kind = KIND >= 0 ? KIND : c.kind;
     const uint64_t tk = (uint64_t)__double_as_longlong(tau);
+    EventDraws e;
     if (kind == KIND_NONSPATIAL) {
         const u64x2 b0 = stream_block(c.sk0, c.sk1, loc, tk, 0, TAG_EVENT);
-        if ((b0.lo >> 11) < c.nu_thr) return true;
-        loc = disperse<KIND_NONSPATIAL>(c, P, loc, b0.hi, 0ull, 0ull);
-        return false;
+        e.spec = (b0.lo >> 11) < c.nu_thr;
+        e.d1 = b0.hi;
+        e.d2 = e.d3 = 0ull;
+        return e;
     }
     const u64x2 b = stream_block(c.sk0, c.sk1, loc, tk, lane & 1u, TAG_EVENT);
-    const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0), d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
-    const uint64_t d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1), d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
-    if ((d0 >> 11) < spec_thr(c, P, kind, loc)) return true;
-    loc = disperse<KIND>(c, P, loc, d1, d2, d3, srow);
-    return false;
+    const uint64_t d0 = __shfl_sync(0xFFFFFFFFu, b.lo, 0);
+    e.d1 = __shfl_sync(0xFFFFFFFFu, b.hi, 0);
+    e.d2 = __shfl_sync(0xFFFFFFFFu, b.lo, 1);
+    e.d3 = __shfl_sync(0xFFFFFFFFu, b.hi, 1);
+    e.spec = (d0 >> 11) < spec_thr(c, P, kind, loc);
+    return e;
 }
 
 // global slot index of a location: cells row-major x slot_deme + deme
