@@ -533,8 +533,12 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             const uint64_t at = loc;
-            if (stage) row_stage_wait(rs, B);
-            const bool speciated = do_event_warp<KIND>(c, B.P, loc, tn, lane, srow);
+            const uint32_t row_ready = stage ? row_stage_poll(rs) : 1u;
+            const EventDraws ed = event_draws_warp<KIND>(c, B.P, loc, tn, lane);
+            if (stage) row_stage_finish(rs, B, row_ready);
+            const uint64_t moved = disperse<KIND>(c, B.P, loc, ed.d1, ed.d2, ed.d3, srow);
+            const bool speciated = ed.spec;
+            loc = speciated ? loc : moved;
             if (LOG) {
                 warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
                 tprev = tn;
