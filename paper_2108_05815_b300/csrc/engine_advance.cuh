@@ -520,6 +520,10 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         const bool stage = B.stage_bytes && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP));
         const uint64_t* srow = stage ? row_stage_issue(rs, sbuf, B.P, c, loc, lane, B) : nullptr;
         for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
+            // the event's draws ahead of the horizon test, so that their
+            // Philox block overlaps it (a lineage at its horizon drops them)
+            const uint32_t row_ready = stage ? row_stage_poll(rs) : 1u;
+            const EventDraws ed = event_draws_warp<KIND>(c, B.P, loc, tn, lane);
             if ((uint64_t)__double_as_longlong(tn) > hz) {
                 if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
                     L.loc[idx] = loc;
@@ -533,8 +537,6 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             lane_max = max(lane_max, ++ev_lin);
             if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
             const uint64_t at = loc;
-            const uint32_t row_ready = stage ? row_stage_poll(rs) : 1u;
-            const EventDraws ed = event_draws_warp<KIND>(c, B.P, loc, tn, lane);
             if (stage) row_stage_finish(rs, B, row_ready);
             const uint64_t moved = disperse<KIND>(c, B.P, loc, ed.d1, ed.d2, ed.d3, srow);
             const bool speciated = ed.spec;
