@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--served-window", type=float, default=20.0, help="config 5: arrival window in seconds")
     ap.add_argument("--served-plain", type=int, default=8,
                     help="config 5: requests re-run one by one on the plain path (0: none)")
+    ap.add_argument("--served-tuning", default="",
+                    help="config 5: server tuning overrides, name=value,... (ind_tuning fields)")
     ap.add_argument("--served-spec-window", type=float, default=4.0,
                     help="config 5 at its specified 50 requests/s: arrival window in seconds (0: skip)")
     ap.add_argument("--replicas", type=int, default=16,
@@ -504,7 +506,10 @@ def run_single(args, name, rank, world, local, pg):
                      "busiest_launch": busiest(acc["best"] or {}, ops, peak),
                      "peak_source": "derived, not measured: %d SMs x %d INT32 lanes x %.0f MHz maximum SM clock"
                                     % (sms, INT32_LANES_PER_SM, SM_MAX_MHZ),
-                     "binding": "the dependent chain of the longest lineage (latency_bound), not a pipe"},
+                     "binding": "the dependent chain of the longest lineage (latency_bound), not a pipe",
+                     "chain_floor_frac": chain_floor_frac(latency),
+                     "chain_floor_what": "the binding roofline: (longest line of descent x the hardware floor of "
+                                         "one event, from measured latencies) / step time; see latency_bound"},
         "latency_bound": latency,
         "event_stream": stream_line,
         "cpu_baseline": cpu,
@@ -527,6 +532,18 @@ def dedup_counts(st):
             "same_slot_same_warp_instruction": st["dedup_warp_repeats"], "rounds": st["rounds"],
             "what": "counting pass: dedup inserts; inserts whose slot another lineage had entered; inserts "
                     "shadowed by a lower lane of the same warp inserting the same slot in the same instruction"}
+
+
+def chain_floor_frac(latency):
+    """the step against its hardware chain floor: longest line of descent x
+    floor per event / step when the line is known, else critical events x
+    floor per event / step"""
+    hw = latency.get("hw_floor")
+    if not hw:
+        return None
+    if "frac_of_longest_floor" in hw:
+        return hw["frac_of_longest_floor"]
+    return 1.0 / hw["step_over_critical_floor"]
 
 
 def replicas_leg(torch, ind, wl, n, sampler, ids):
@@ -683,7 +700,7 @@ def served_leg(args, local, rate, window, plain_n, sampler_name="exp"):
     reqs = W.config5(rate=rate, window_s=window)
     srv_stream = torch.cuda.Stream()
     prep_stream = torch.cuda.Stream()
-    srv = ind.Server(150 * 10 ** 9, max_sims=4096, stream=srv_stream)
+    srv = ind.Server(150 * 10 ** 9, max_sims=4096, stream=srv_stream, **served_tuning(args))
     clocks = ClockSampler(local).start()
     launches0 = ind.kernel_launches()
     sims, lat, arrival, index, lat_of = {}, [], {}, {}, {}
@@ -731,6 +748,7 @@ def served_leg(args, local, rate, window, plain_n, sampler_name="exp"):
                     "sample fraction 0.01..1, nu log-uniform 1e-7..1e-3, sigma 1..8, HBM budget 150 GB"
                     % (rate, window),
         "event_sampler": sampler_name, "requests": len(reqs), "offered_rate_per_s": rate, "window_s": window,
+        "server_tuning": dict(ind.default_tuning(), **served_tuning(args)),
         "wall_s": total, "achieved_rate_per_s": len(reqs) / total,
         "drain_s": total - t_last_arrival,
         "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat) if lat else None,
@@ -744,6 +762,15 @@ def served_leg(args, local, rate, window, plain_n, sampler_name="exp"):
     }
     if plain and plain.get("unique_over_raw_alone"):
         out["unique_events_per_s_estimated"] = out["raw_events_per_s"] * plain["unique_over_raw_alone"]
+    return out
+
+
+def served_tuning(args):
+    """--served-tuning name=value,... as a dict of ind_tuning overrides"""
+    out = {}
+    for kv in filter(None, getattr(args, "served_tuning", "").split(",")):
+        k, v = kv.split("=")
+        out[k.strip()] = float(v) if "." in v or "e" in v else int(v)
     return out
 
 
