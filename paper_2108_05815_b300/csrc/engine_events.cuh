@@ -675,17 +675,20 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
         const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
         return pack_loc(tx, ty, ti);
     }
-    // habitat map: one load of the origin cell's alias entry, which also
-    // carries the target deme (k_alias_build), then the offset table (L1)
+    // habitat map: the origin cell's alias entry (which carries the alias
+    // column's offset and both target demes, k_alias_build) and the
+    // column's own offset load side by side, then one choice
     const uint32_t n_off = c.n_off;
     const uint32_t col = (uint32_t)(((d1 >> 32) * (uint64_t)n_off) >> 32);
     const uint64_t e = srow ? srow[col] : __ldg(c.alias + ((size_t)y * c.W + x) * n_off + col);
+    const int8_t* off = c.off;  // plain loads: the warp kernel may stage the table in shared memory
+    const int32_t cdx = off[2 * col], cdy = off[2 * col + 1];
     const uint32_t u = (uint32_t)d1;
     const bool take_col = (e >> 63) != 0 || u < (uint32_t)e;
-    const uint32_t o = take_col ? col : (uint32_t)((e >> 32) & (ALIAS_MAX_OFFSETS - 1u));
-    const uint32_t d = (uint32_t)(e >> (take_col ? 45 : 53)) & 0xFFu;
-    const int8_t* off = c.off;  // plain loads: the warp kernel may stage the table in shared memory
-    const int32_t dx = off[2 * o], dy = off[2 * o + 1];
+    const int32_t adx = (int32_t)((uint32_t)(e >> 32) << 25) >> 25;  // 7-bit two's complement
+    const int32_t ady = (int32_t)((uint32_t)(e >> 39) << 25) >> 25;
+    const int32_t dx = take_col ? cdx : adx, dy = take_col ? cdy : ady;
+    const uint32_t d = (uint32_t)(e >> (take_col ? 46 : 54)) & 0xFFu;
     const uint32_t tx = wrap_add(x, dx, c.W);
     const uint32_t ty = wrap_add(y, dy, c.H);
     return pack_loc(tx, ty, umulhi64(d2, d));

@@ -18,14 +18,17 @@ __global__ void k_habitat(uint8_t* out, uint32_t W, uint32_t H, uint32_t sk0, ui
 
 // one warp per habitable cell: weights, then integer Vose.  Rows are
 // indexed by cell (those of cells without habitat are never read), and an
-// entry holds everything a dispersal needs besides the offset table:
-// threshold q (bits 0-31), alias column (32-44), the deme of the column's
-// own target (45-52) and of the alias column's target (53-60), and bit 63
-// for a column that is always taken
-__device__ __forceinline__ uint64_t alias_entry(uint64_t q, uint32_t col, uint32_t alias_col, uint8_t deme_col,
+// entry holds everything a dispersal that falls on the alias needs:
+// threshold q (bits 0-31), the alias column's offset dx (32-38) and dy
+// (39-45) as 7-bit two's complement, the deme of the column's own target
+// (46-53) and of the alias column's target (54-61), and bit 63 for a column
+// that is always taken.  A dispersal that keeps its column reads the
+// column's offset from the offset table, a load that does not wait for the
+// entry.
+__device__ __forceinline__ uint64_t alias_entry(uint64_t q, int32_t adx, int32_t ady, uint8_t deme_col,
                                                 uint8_t deme_alias, bool full) {
-    return q | ((uint64_t)alias_col << 32) | ((uint64_t)deme_col << 45) | ((uint64_t)deme_alias << 53) |
-           (full ? (1ull << 63) : 0ull);
+    return q | ((uint64_t)((uint32_t)adx & 0x7Fu) << 32) | ((uint64_t)((uint32_t)ady & 0x7Fu) << 39) |
+           ((uint64_t)deme_col << 46) | ((uint64_t)deme_alias << 54) | (full ? (1ull << 63) : 0ull);
 }
 
 // shared-memory bytes of one warp of k_alias_build for n_off offsets
@@ -90,7 +93,7 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
         for (uint32_t o = lane; o < n_off; o += 32) {
             const uint32_t b = alias_of[o];
             if (b == ALIAS_FULL) {
-                e[o] = alias_entry(0xFFFFFFFFull, o, o, tdeme[o], tdeme[o], true);
+                e[o] = alias_entry(0xFFFFFFFFull, off[2 * o], off[2 * o + 1], tdeme[o], tdeme[o], true);
                 continue;
             }
             // q = floor(s_o 2^32 / W) by restoring division (s_o < W < 2^56)
@@ -103,7 +106,7 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
                     q |= 1ull;
                 }
             }
-            e[o] = alias_entry(q, o, b, tdeme[o], tdeme[b], false);
+            e[o] = alias_entry(q, off[2 * b], off[2 * b + 1], tdeme[o], tdeme[b], false);
         }
         __syncwarp();
     }

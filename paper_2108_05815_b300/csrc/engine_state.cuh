@@ -110,7 +110,8 @@ constexpr int GUIDE_BITS = 12;
 constexpr uint32_t GUIDE_N = 1u << GUIDE_BITS;
 constexpr uint32_t GUIDE_SCAN = 0x80000000u;
 
-// alias rows of a habitat map: entries name their alias column in 13 bits
+// alias rows of a habitat map: at most 2^13 columns (the alias build's
+// 16-bit work lists; radius 40 gives 5,025)
 constexpr int ALIAS_COL_BITS = 13;
 constexpr uint32_t ALIAS_MAX_OFFSETS = 1u << ALIAS_COL_BITS;
 

@@ -521,8 +521,9 @@ def test_implicit_sampled_fraction():
 
 def test_alias_rows_equal_oracle():
     """The device's alias rows (k_alias_build) against the oracle's alias
-    construction, entry by entry: threshold, alias column, the always-taken
-    mark, and the demes of both target cells that the packed entry carries."""
+    construction, entry by entry: threshold, the alias column's offset, the
+    always-taken mark, and the demes of both target cells that the packed
+    entry carries."""
     W_, H_ = 97, 83
     dm = O.habitat(5, W_, H_)
     cfg = dict(kind=W.MAP, width=W_, height=H_, sigma=4.0, radius=16, nu=1e-3, seed=3)
@@ -538,11 +539,15 @@ def test_alias_rows_equal_oracle():
             q, al, full, dx, dy = m.alias_row(cx, cy)
             assert e.size == q.size
             assert np.array_equal(e & 0xFFFFFFFF, q.astype(np.uint64))
-            assert np.array_equal((e >> 32) & 0x1FFF, al.astype(np.uint64))
+            full_b = full.astype(bool)
+            al_eff = np.where(full_b, np.arange(q.size), al.astype(np.int64))  # a full column is its own alias
+            sx = (((e >> 32) & 0x7F).astype(np.int64) ^ 0x40) - 0x40  # 7-bit two's complement
+            sy = (((e >> 39) & 0x7F).astype(np.int64) ^ 0x40) - 0x40
+            assert np.array_equal(sx, dx[al_eff].astype(np.int64)) and np.array_equal(sy, dy[al_eff].astype(np.int64))
             assert np.array_equal(e >> 63, full.astype(np.uint64))
             tdeme = dm.reshape(H_, W_)[(cy + dy.astype(np.int64)) % H_, (cx + dx.astype(np.int64)) % W_]
-            assert np.array_equal((e >> 45) & 0xFF, tdeme.astype(np.uint64))
-            assert np.array_equal((e >> 53) & 0xFF, tdeme[al].astype(np.uint64))
+            assert np.array_equal((e >> 46) & 0xFF, tdeme.astype(np.uint64))
+            assert np.array_equal((e >> 54) & 0xFF, tdeme[al_eff].astype(np.uint64))
         with pytest.raises(ind.IndError):  # a cell without habitat has no row
             empty = np.flatnonzero(dm.reshape(-1) == 0)[0]
             s.alias_row(int(empty % W_), int(empty // W_))
