@@ -748,7 +748,7 @@ def served_leg(args, local, rate, window, plain_n, sampler_name="exp"):
                     "sample fraction 0.01..1, nu log-uniform 1e-7..1e-3, sigma 1..8, HBM budget 150 GB"
                     % (rate, window),
         "event_sampler": sampler_name, "requests": len(reqs), "offered_rate_per_s": rate, "window_s": window,
-        "server_tuning": dict(ind.default_tuning(), **served_tuning(args)),
+        "server_tuning": dict(ind.server_default_tuning(), **served_tuning(args)),
         "wall_s": total, "achieved_rate_per_s": len(reqs) / total,
         "drain_s": total - t_last_arrival,
         "latency_s": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat) if lat else None,

@@ -375,9 +375,15 @@ typedef struct {
     uint64_t lineage_capacity;               /* resident-lineage capacity of the buffers */
 } ind_server_stats;
 
+/* The server's default tuning: ind_default_tuning with a higher water level
+ * for requests with many lineages (occupancy_step 1, min_events_per_lineage
+ * 1, events_per_round 2^24), since a shared round lasts as long as the
+ * heaviest lineage in it runs.  Results do not depend on it. */
+void srv_default_tuning(ind_tuning* tuning);
+
 /* hbm_budget: bytes that resident requests may hold (their sim_mem_estimate
  * summed); the lineage buffers are sized from it.  max_sims: resident
- * requests at most (1..65536).  tuning NULL = defaults.  All work runs on
+ * requests at most (1..65536).  tuning NULL = srv_default_tuning.  All work runs on
  * cuda_stream (resolution of finished requests on a stream of the server's
  * own that waits for it). */
 ind_status srv_create(uint64_t hbm_budget, uint32_t max_sims, const ind_tuning* tuning, void* cuda_stream,
@@ -443,9 +449,11 @@ ind_status sim_selftest_search(ind_sim* m, int form, const uint64_t* loc, const 
  * column o of the cell's integer
  * Vose table over the dispersal kernel's offsets (row-major (dy, dx) within
  * the radius), packed in 64 bits: threshold q (bits 0-31; column o is taken
- * iff the 32 low bits of the draw are below q), alias column (bits 32-44),
- * deme of column o's target cell (45-52) and of the alias column's target
- * cell (53-60), and bit 63 set when column o is always taken.  *n_out
+ * iff the 32 low bits of the draw are below q), the alias column's offset
+ * dx (bits 32-38) and dy (39-45) as 7-bit two's complement, the deme of
+ * column o's target cell (46-53) and of the alias column's target cell
+ * (54-61), and bit 63 set when column o is always taken (its alias is then
+ * itself).  *n_out
  * receives the number of columns; with out == NULL that is all the call
  * does.  out (host or device, caller-owned) holds cap >= *n_out entries.
  * IND_ERR_ARG for a simulation that is not a map, a cell outside the map or

