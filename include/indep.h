@@ -247,8 +247,11 @@ ind_status sim_create(const ind_landscape* landscape, const ind_dispersal* dispe
  * order.  0 < fraction <= 1.  *n_sampled receives the count (may be NULL). */
 ind_status sim_sample(ind_sim* sim, double fraction, uint64_t sample_seed, uint64_t* n_sampled);
 
-/* Isolated partitions (section "Isolated Partitioning" of the paper's
- * parallelisation strategies, and its limit analysis): the sampled
+/* Isolated partitions (the IsolatedIndividuals and IsolatedLandscape
+ * strategies of the paper's parallel Independent algorithm, section "The
+ * Independent Algorithm" of its parallelisation chapter, configured as in
+ * the appendix "Parallelism with Isolated Batches", and run at scale in
+ * section "Biodiversity Simulation Limit Analysis"): the sampled
  * individuals of one simulation are split into n_parts disjoint parts, each
  * simulated on its own (one per GPU, or one after another) with no
  * communication; lineages of different parts that meet are simulated twice.

@@ -2,9 +2,11 @@
 
 The Independent algorithm traces every sampled individual's lineage from
 (seed, location, time) alone, so the sample of one simulation can be split
-into parts that run with no communication at all (the paper's isolated
-partitioning strategies, IsolatedIndividuals and IsolatedLandscape, and its
-limit analysis, where 7.1e10 individuals ran as independent partitions).
+into parts that run with no communication at all (the paper's
+IsolatedIndividuals and IsolatedLandscape strategies, section "The
+Independent Algorithm" of its parallelisation chapter, and section
+"Biodiversity Simulation Limit Analysis", where 7.1e10 individuals ran as
+independent partitions).
 Lineages of different parts that meet are simulated once in each part; an
 individual's speciation key is the same in its part as in the whole
 simulation.  The one exchange is at the end: the parts' distinct speciation
