@@ -47,7 +47,8 @@ _SRC = os.path.join(_HERE, "chain_latency.cu")
 _LIB = os.path.join(_HERE, "_build", "libhwlat.so")
 
 CLASSES = {"imad_hi": 0, "hi_xor": 1, "umul64hi": 2, "imad_wide": 3, "add64_sel": 4, "clz_norm": 5,
-           "add_xor": 6, "ballot": 8, "redux_min": 9, "philox_round": 10, "lds": 11, "philox_round_split": 12}
+           "add_xor": 6, "ballot": 8, "redux_min": 9, "philox_round": 10, "lds": 11, "philox_round_split": 12,
+           "philox_round_m1": 13}
 
 
 def build(force=False):
@@ -125,7 +126,7 @@ def measure(reps=3, dram_ring_mib=512, dram_steps=4000):
 
 def derived(lat):
     """latencies of the path's compound steps, in cycles"""
-    philox = 10.0 * min(lat["philox_round"], lat["philox_round_split"])
+    philox = 10.0 * min(lat["philox_round"], lat["philox_round_split"], lat["philox_round_m1"])
     add64 = lat["add_xor"]           # two dependent 32-bit adds (the carry), costed as add + xor
     log = lat["clz_norm"] + lat["lds"] + lat["imad_wide"] + 2.0 * lat["umul64hi"] + 6.0 * add64
     return dict(philox_block=philox, add64=add64, logarithm=log, add_cmp_sel=lat["add64_sel"],

@@ -14,6 +14,7 @@
 //   philox      one Philox4x32 round (two high/low product pairs, xors and
 //               the key schedule): the round's dependent path
 //   philox_split the same with the low products from run-time multipliers
+//   philox_m1   the same with each low product as c (M - 1) + c
 //   hi_xor      x = mulhi32(x, y) ^ z                   high product + xor
 //   umul64hi    x = mulhi64(x, y)                       64-bit high product
 //   imad_wide   x = lo64(lo32(x) * y + x)               32x32 -> 64 multiply-add
@@ -120,6 +121,33 @@ __global__ void k_philox_split(const uint64_t* __restrict__ prm, Out* out) {
     out->sink += (unsigned long long)(c0 ^ c1 ^ c2 ^ c3);
 }
 
+// the same round with each low product written as c (M - 1) + c: equal to
+// c M, but with a multiplier other than the high product's, so that the two
+// need not share one wide multiply
+__global__ void k_philox_m1(const uint64_t* __restrict__ prm, Out* out) {
+    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
+    __syncwarp();
+    const unsigned long long t0 = clk();
+#pragma unroll 1
+    for (int it = 0; it < STEPS / 64; ++it) {
+#pragma unroll
+        for (int s = 0; s < 64; ++s) {
+            const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = c0 * (0xD2511F53u - 1u) + c0;
+            const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = c2 * (0xCD9E8D57u - 1u) + c2;
+            c0 = hi1 ^ c1 ^ k0;
+            c1 = lo1;
+            c2 = hi0 ^ c3 ^ k1;
+            c3 = lo0;
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    const unsigned long long t1 = clk();
+    if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
+    out->sink += (unsigned long long)(c0 ^ c1 ^ c2 ^ c3);
+}
+
 // dependent loads: i = table[i] over a ring laid out by the host
 __global__ void k_lds(const uint64_t* __restrict__ prm, Out* out) {
     __shared__ uint32_t s[1024];
@@ -186,7 +214,7 @@ double hwlat_clock_mhz(unsigned long long cycles, void* out_dev) {
 int hwlat_steps() { return STEPS; }
 
 // class ids: 0 imad_hi, 1 hi_xor, 2 umul64hi, 3 imad_wide, 4 add64_sel,
-// 5 clz_norm, 6 add_xor, 8 ballot, 9 redux_min, 10 philox, 11 lds, 12 philox_split
+// 5 clz_norm, 6 add_xor, 8 ballot, 9 redux_min, 10 philox, 11 lds, 12 philox_split, 13 philox_m1
 // Runs the chain once in one warp of one block; returns its cycles, or a
 // negative CUDA error.  prm: 6 device words of runtime operands.
 long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
@@ -204,6 +232,7 @@ long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
         case 10: k_philox<<<1, 32>>>(prm, o); break;
         case 11: k_lds<<<1, 32>>>(prm, o); break;
         case 12: k_philox_split<<<1, 32>>>(prm, o); break;
+        case 13: k_philox_m1<<<1, 32>>>(prm, o); break;
         default: return -1;
     }
     cudaError_t e = cudaDeviceSynchronize();
