@@ -15,8 +15,8 @@ Default run (one JSON line):
             (autotuned launch shape, CUDA-graph chunks) against the plain
             path (one simulation per sim_run), in unique events per second.
   served    config 5: Poisson arrivals of torus requests into the
-            continuous-batching server at the highest rate this build
-            sustains (10 requests/s: the requests in the system stay
+            continuous-batching server at the highest rate it sustains
+            on one B300 (10 requests/s: the requests in the system stay
             bounded), and at the specified 50 requests/s over a short
             window (beyond capacity); latency p50/p99 from arrival to
             species identities, offered and achieved request rates, drain
@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2, help="config 4: timed batches")
     ap.add_argument("--plain-subset", type=int, default=32, help="config 4: simulations timed one by one")
     ap.add_argument("--served-rate", type=float, default=10.0,
-                    help="config 5: offered requests per second (10: the highest rate this build sustains)")
+                    help="config 5: offered requests per second (10: the highest rate the server sustains)")
     ap.add_argument("--served-window", type=float, default=20.0, help="config 5: arrival window in seconds")
     ap.add_argument("--served-plain", type=int, default=8,
                     help="config 5: requests re-run one by one on the plain path (0: none)")

@@ -290,7 +290,9 @@ extern "C" {
 // lineages.  A shared round lasts as long as its heaviest lineage runs (a
 // request in its tail, up to max_step_events), so the requests in their busy
 // phase may advance about one event per lineage per round instead of a
-// quarter: on config 5's mix at 10 requests/s the median latency went from
+// quarter: on Poisson arrivals of torus requests (sides 128 to 4096, demes
+// 1 to 4, sample fractions 0.01 to 1, nu 1e-7 to 1e-3) at 10 requests/s
+// the median latency went from
 // 0.92-1.07 s to 0.67 s and the 99th percentile from about 30 s to 27 s.
 void srv_default_tuning(ind_tuning* t) {
     if (!t) return;
