@@ -292,8 +292,8 @@ extern "C" {
 // phase may advance about one event per lineage per round instead of a
 // quarter: on Poisson arrivals of torus requests (sides 128 to 4096, demes
 // 1 to 4, sample fractions 0.01 to 1, nu 1e-7 to 1e-3) at 10 requests/s
-// the median latency went from
-// 0.92-1.07 s to 0.67 s and the 99th percentile from about 30 s to 27 s.
+// the median latency went from 0.92-1.07 s to 0.67 s and the 99th
+// percentile from about 30 s to 27 s.
 void srv_default_tuning(ind_tuning* t) {
     if (!t) return;
     ind_default_tuning(t);
