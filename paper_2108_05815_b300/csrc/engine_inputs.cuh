@@ -40,10 +40,11 @@ constexpr uint16_t ALIAS_FULL = 0xFFFFu;  // a column that is always taken
 
 // Vose's pairing is sequential (lane 0 pops the small and large stacks in
 // order); the threshold of a column depends only on its scaled weight when
-// it was popped as small, which never changes afterwards.  So lane 0 only
-// pairs (alias column per column, full marks), and then all lanes compute
-// the thresholds floor(s_a 2^32 / W) by restoring division and write the
-// entries, 32 columns at a time.
+// it was popped as small, which never changes afterwards.  So all lanes
+// fill the stacks (a stable partition by ballot), lane 0 only pairs, with
+// the stacks' tops in registers, all lanes mark the columns left over as
+// always taken, and then compute the thresholds floor(s_a 2^32 / W) by
+// restoring division and write the entries, 32 columns at a time.
 __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint32_t H,
                               const uint32_t* __restrict__ cells, uint32_t n_rows, const int8_t* __restrict__ off,
                               uint32_t n_off, const uint64_t* __restrict__ kw, uint64_t* __restrict__ alias) {
@@ -71,23 +72,60 @@ __global__ void k_alias_build(const uint8_t* __restrict__ deme, uint32_t W, uint
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
         const uint64_t Wt = part;
         __syncwarp();
-        if (lane == 0) {
-            uint32_t ns = 0, nl = 0;
-            for (uint32_t o = 0; o < n_off; ++o) {
-                if (s[o] < Wt) small_[ns++] = (uint16_t)o;
-                else large_[nl++] = (uint16_t)o;
-            }
-            while (ns > 0 && nl > 0) {
-                const uint32_t a = small_[--ns];
-                const uint32_t b = large_[--nl];
-                alias_of[a] = (uint16_t)b;  // s[a] stays as it is: a's threshold comes from it
-                s[b] = s[b] + s[a] - Wt;
-                if (s[b] < Wt) small_[ns++] = (uint16_t)b;
-                else large_[nl++] = (uint16_t)b;
-            }
-            while (nl > 0) alias_of[large_[--nl]] = ALIAS_FULL;
-            while (ns > 0) alias_of[small_[--ns]] = ALIAS_FULL;
+        // the small and large stacks filled in ascending column order, 32
+        // columns at a time (a stable partition by ballot)
+        uint32_t ns = 0, nl = 0;  // the same in every lane
+        for (uint32_t base = 0; base < n_off; base += 32u) {
+            const uint32_t o = base + lane;
+            const bool valid = o < n_off;
+            const bool sm = valid && s[o] < Wt;
+            const unsigned ms = __ballot_sync(0xFFFFFFFFu, sm);
+            const unsigned ml = __ballot_sync(0xFFFFFFFFu, valid && !sm);
+            const unsigned below = (1u << lane) - 1u;
+            if (sm) small_[ns + __popc(ms & below)] = (uint16_t)o;
+            else if (valid) large_[nl + __popc(ml & below)] = (uint16_t)o;
+            ns += (uint32_t)__popc(ms);
+            nl += (uint32_t)__popc(ml);
         }
+        __syncwarp();
+        if (lane == 0 && ns > 0 && nl > 0) {
+            // Vose's pairing, in its order: pop a (small) and b (large),
+            // alias(a) = b, s_b += s_a - W, push b onto the stack its new
+            // weight belongs to.  The pushed b is the next pop of that stack,
+            // so it stays in registers; s[a] is never changed again (a's
+            // threshold comes from it) and s[b] is written when b leaves.
+            uint32_t a = small_[--ns], b = large_[--nl];
+            uint64_t sa = s[a], sb = s[b];
+            for (;;) {
+                alias_of[a] = (uint16_t)b;
+                sb = sb + sa - Wt;
+                if (sb < Wt) {  // b moves to the small stack: it is the next a
+                    s[b] = sb;
+                    if (nl == 0) {
+                        small_[ns++] = (uint16_t)b;
+                        break;
+                    }
+                    a = b;
+                    sa = sb;
+                    b = large_[--nl];
+                    sb = s[b];
+                } else {        // b stays on top of the large stack
+                    if (ns == 0) {
+                        s[b] = sb;
+                        large_[nl++] = (uint16_t)b;
+                        break;
+                    }
+                    a = small_[--ns];
+                    sa = s[a];
+                }
+            }
+        }
+        ns = __shfl_sync(0xFFFFFFFFu, ns, 0);
+        nl = __shfl_sync(0xFFFFFFFFu, nl, 0);
+        __syncwarp();
+        // the columns left on either stack are always taken
+        for (uint32_t k = lane; k < nl; k += 32u) alias_of[large_[k]] = ALIAS_FULL;
+        for (uint32_t k = lane; k < ns; k += 32u) alias_of[small_[k]] = ALIAS_FULL;
         __syncwarp();
         uint64_t* e = alias + (size_t)cell * n_off;
         for (uint32_t o = lane; o < n_off; o += 32) {
