@@ -260,17 +260,23 @@ def hw_latencies():
 def hw_floor(sampler, kind, crit, longest, ms_step):
     H, lat = hw_latencies()
     cyc = H.event_floor(lat, sampler, kind)
+    cyc_compute = H.event_floor(lat, sampler, kind, memory=False)
     ns = cyc / lat["clock_mhz"] * 1e3
     out = {"cycles_per_event": cyc, "ns_per_event": ns, "clock_mhz": lat["clock_mhz"],
+           "compute_cycles_per_event": cyc_compute,
            "critical_events_x_floor_ms": crit * ns * 1e-6, "step_over_critical_floor": ms_step / (crit * ns * 1e-6),
            "latencies_cycles": {k: round(v, 2) for k, v in lat.items() if k not in ("clock_mhz", "steps_per_chain")},
            "path": {k: round(v, 1) for k, v in H.derived(lat).items()},
            "what": "cycles of one event on the method's critical path (two Philox blocks, the dispersal's lookups, "
-                   "one logarithm or point count, the running sum's dependent adds), each operation costed at its "
-                   "dependent latency measured on this GPU by tests/hw_latency; SM clock from a timed spin"}
+                   "one logarithm or point count, the running sum's dependent adds; on a habitat map also the alias "
+                   "row's fetch latency that the next search and event cannot cover), each operation costed at its "
+                   "dependent latency measured on this GPU by tests/hw_latency; compute_*: without the row's "
+                   "fetch; SM clock from a timed spin"}
     if longest:
+        ns_c = cyc_compute / lat["clock_mhz"] * 1e3
         out.update({"longest_descent_events": longest, "longest_x_floor_ms": longest * ns * 1e-6,
-                    "frac_of_longest_floor": longest * ns * 1e-6 / ms_step})
+                    "frac_of_longest_floor": longest * ns * 1e-6 / ms_step,
+                    "frac_of_longest_compute_floor": longest * ns_c * 1e-6 / ms_step})
     return out
 
 

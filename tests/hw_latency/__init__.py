@@ -19,9 +19,10 @@ exponentials", Poisson points per "Homogeneous Poisson Point Process"):
   2. dispersal from those draws: non-spatial, one 64-bit high product; torus,
      one table lookup (shared memory) per axis, side by side, and the
      wrap-around add; habitat map, the column (a 32-bit high product), the
-     alias entry (a staged, shared-memory read: the row's address is known
-     one whole event earlier), the take-or-alias choice, the offset-table
-     read and the wrap-around add;
+     alias entry (its cell is known one event before its column: the
+     cheaper of the row copy's measured latency beyond what the next search
+     and event's Philox block cover, and a dependent DRAM load), the
+     take-or-alias choice, the offset-table read and the wrap-around add;
   3. the next event time at the new location after the event time: the
      interval's index is known before the move, so the interval block's
      first product is off the path; nine rounds and the key's xor remain.
@@ -48,7 +49,7 @@ _LIB = os.path.join(_HERE, "_build", "libhwlat.so")
 
 CLASSES = {"imad_hi": 0, "hi_xor": 1, "umul64hi": 2, "imad_wide": 3, "add64_sel": 4, "clz_norm": 5,
            "add_xor": 6, "ballot": 8, "redux_min": 9, "philox_round": 10, "lds": 11, "philox_round_split": 12,
-           "philox_round_m1": 13}
+           "philox_round_m1": 13, "shfl_add": 14}
 
 
 def build(force=False):
@@ -75,6 +76,9 @@ def lib():
         L.hwlat_run.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         L.hwlat_ring.restype = ctypes.c_longlong
         L.hwlat_ring.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+        L.hwlat_bulk_row.restype = ctypes.c_longlong
+        L.hwlat_bulk_row.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_int, ctypes.c_void_p]
         L.hwlat_clock_mhz.restype = ctypes.c_double
         L.hwlat_clock_mhz.argtypes = [ctypes.c_ulonglong, ctypes.c_void_p]
         _lib = L
@@ -119,9 +123,26 @@ def measure(reps=3, dram_ring_mib=512, dram_steps=4000):
     c = L.hwlat_ring(ctypes.c_void_p(big.data_ptr()), b0, dram_steps, 0, ctypes.c_void_p(out.data_ptr()))
     res["ldg_dram"] = c / dram_steps
     del big
+    # the map row's bulk copy: 6,384 bytes (a 797-entry row from its 16-byte
+    # boundary) from random rows of a buffer larger than L2, whole or in
+    # 4, 8 or 31 pieces issued side by side; the fastest is the row's latency
+    stride = ROW_BYTES
+    rows = (dram_ring_mib << 20) // stride
+    buf = torch.zeros(rows * stride, dtype=torch.uint8, device="cuda")
+    for pieces, piece in ((1, 6384), (4, 1600), (8, 800), (31, 208)):
+        c = L.hwlat_bulk_row(ctypes.c_void_p(buf.data_ptr()), rows, stride, ROW_BYTES, piece, 1000,
+                             ctypes.c_void_p(out.data_ptr()))
+        if c < 0:
+            raise RuntimeError("bulk row copy probe failed (%d)" % c)
+        res["bulk_row_%d" % pieces] = c / 1000
+    res["bulk_row"] = min(res["bulk_row_%d" % k] for k in (1, 4, 8, 31))
+    del buf
     res["clock_mhz"] = L.hwlat_clock_mhz(200_000_000, ctypes.c_void_p(out.data_ptr()))
     res["steps_per_chain"] = steps
     return res
+
+
+ROW_BYTES = 6384  # an alias row of 797 entries, copied from its 16-byte boundary
 
 
 def derived(lat):
@@ -133,8 +154,10 @@ def derived(lat):
                 interval_block=philox - lat["imad_hi"])
 
 
-def event_floor(lat, sampler="exp", kind="torus"):
-    """cycles of one event on the critical path (see the module docstring)"""
+def event_floor(lat, sampler="exp", kind="torus", memory=True):
+    """cycles of one event on the critical path (see the module docstring);
+    memory=False leaves out the map row's fetch latency (the compute-only
+    floor)"""
     d = derived(lat)
     event = d["philox_block"]
     if kind == "nonspatial":
@@ -149,4 +172,13 @@ def event_floor(lat, sampler="exp", kind="torus"):
         search = d["interval_block"] + d["logarithm"] + 3.0 * d["add_cmp_sel"] + d["add_cmp_sel"]
     else:
         search = d["interval_block"] + lat["lds"] + d["add_cmp_sel"] + 2.0 * d["add_cmp_sel"]
-    return event + move + search
+    wait = 0.0
+    if kind == "map" and memory and "bulk_row" in lat:
+        # The entry's cell is known after a move, its column only after the
+        # next event's draws.  Either the row is fetched whole when the cell
+        # is known (read after the next search and event's Philox block:
+        # whatever of the copy's latency those do not cover is on the path),
+        # or the entry alone once the column is known (a dependent DRAM load,
+        # all of it on the path); the cheaper of the two.
+        wait = min(lat["ldg_dram"], max(0.0, lat["bulk_row"] - (search + event)))
+    return event + move + search + wait

@@ -3,8 +3,10 @@
 // not part of the library).
 //
 // Each kernel runs one dependent chain of STEPS operations of one class in
-// one warp (lane 0's clock) and writes the chain's result, so nothing can
-// be dropped; the cycle count comes from clock64() around the chain.  The
+// one warp (lane 0's clock), every lane from a different value (a chain of
+// warp-uniform values may run on the uniform datapath instead of the
+// per-lane pipes the kernels use), and writes the chain's result, so
+// nothing can be dropped; the cycle count comes from clock64() around the chain.  The
 // chains are built so that no step can start before the previous one ends
 // and no algebra can shorten them: every step feeds a nonlinear operation
 // (a high product, a table index, a shuffle lane, a compare) or is measured
@@ -25,6 +27,9 @@
 //   ldg_dram    i = g[i] (random ring >> L2)            global load from DRAM
 //   ballot      x = ballot(x & bit) ^ x                  warp vote + xor
 //   redux_min   x = redux.min(x) ^ lane-independent    warp reduction
+//   shfl_add    x = shfl(x, lane x & 31) + z            shuffle and add
+//   bulk_row    one 6.4 KB bulk copy (TMA) of a random row into shared
+//               memory, issue to mbarrier completion
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -37,9 +42,16 @@ struct Out {
 
 __device__ __forceinline__ unsigned long long clk() { return clock64(); }
 
+// the clock read after a value is known (its data dependence keeps it last)
+__device__ __forceinline__ unsigned long long clk_after_u32(uint32_t x) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t) : "r"(x) : "memory");
+    return t;
+}
+
 #define CHAIN_KERNEL(NAME, TYPE, INIT, STEP)                                              \
     __global__ void k_##NAME(const uint64_t* __restrict__ prm, Out* out) {                \
-        TYPE x = (TYPE)(INIT);                                                            \
+        TYPE x = (TYPE)(INIT) ^ (TYPE)(threadIdx.x * 0x9E3779B9u); /* lane-dependent */  \
         const uint64_t a = prm[0], b = prm[1], c = prm[2];                                \
         const uint32_t y = (uint32_t)prm[3], z = (uint32_t)prm[4];                        \
         (void)a; (void)b; (void)c; (void)y; (void)z;                                       \
@@ -66,10 +78,17 @@ CHAIN_KERNEL(redux_min, uint32_t, prm[5], x = __reduce_min_sync(0xFFFFFFFFu, x ^
 // dependent add and one xor per step (measured beside hi_xor and imad_hi)
 CHAIN_KERNEL(add_xor, uint32_t, prm[5], x = (x + z) ^ y)
 
+// a shuffle whose source lane comes from the data, then an add (a bare
+// shuffle chain is not kept intact by the compiler)
+CHAIN_KERNEL(shfl_add, uint32_t, prm[5], x = __shfl_sync(0xFFFFFFFFu, x, (int)(x & 31u)) + z)
+
 // one Philox4x32 round per step: the counter words feed the next round,
 // the key words advance by the Weyl increments
 __global__ void k_philox(const uint64_t* __restrict__ prm, Out* out) {
-    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    // lane-dependent counters: the chain runs on the per-lane pipes, as in
+    // the kernels (a warp-uniform chain may run on the uniform datapath)
+    uint32_t c0 = (uint32_t)prm[0] ^ threadIdx.x, c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2] + threadIdx.x,
+             c3 = (uint32_t)prm[3];
     uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
     __syncwarp();
     const unsigned long long t0 = clk();
@@ -97,7 +116,10 @@ __global__ void k_philox(const uint64_t* __restrict__ prm, Out* out) {
 // high-half multiply rather than one wide multiply giving both halves
 __constant__ uint32_t c_zero = 0;
 __global__ void k_philox_split(const uint64_t* __restrict__ prm, Out* out) {
-    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    // lane-dependent counters: the chain runs on the per-lane pipes, as in
+    // the kernels (a warp-uniform chain may run on the uniform datapath)
+    uint32_t c0 = (uint32_t)prm[0] ^ threadIdx.x, c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2] + threadIdx.x,
+             c3 = (uint32_t)prm[3];
     uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
     const uint32_t m0 = 0xD2511F53u ^ c_zero, m1 = 0xCD9E8D57u ^ c_zero;
     __syncwarp();
@@ -125,7 +147,10 @@ __global__ void k_philox_split(const uint64_t* __restrict__ prm, Out* out) {
 // c M, but with a multiplier other than the high product's, so that the two
 // need not share one wide multiply
 __global__ void k_philox_m1(const uint64_t* __restrict__ prm, Out* out) {
-    uint32_t c0 = (uint32_t)prm[0], c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2], c3 = (uint32_t)prm[3];
+    // lane-dependent counters: the chain runs on the per-lane pipes, as in
+    // the kernels (a warp-uniform chain may run on the uniform datapath)
+    uint32_t c0 = (uint32_t)prm[0] ^ threadIdx.x, c1 = (uint32_t)prm[1], c2 = (uint32_t)prm[2] + threadIdx.x,
+             c3 = (uint32_t)prm[3];
     uint32_t k0 = (uint32_t)prm[4], k1 = (uint32_t)prm[5];
     __syncwarp();
     const unsigned long long t0 = clk();
@@ -153,7 +178,7 @@ __global__ void k_lds(const uint64_t* __restrict__ prm, Out* out) {
     __shared__ uint32_t s[1024];
     for (uint32_t k = threadIdx.x; k < 1024; k += blockDim.x) s[k] = (k * 7u + 13u) & 1023u;
     __syncthreads();
-    uint32_t i = (uint32_t)prm[5] & 1023u;
+    uint32_t i = ((uint32_t)prm[5] + threadIdx.x * 37u) & 1023u;
     const unsigned long long t0 = clk();
 #pragma unroll 1
     for (int it = 0; it < STEPS / 64; ++it) {
@@ -181,6 +206,66 @@ __global__ void k_ldg_l1(const uint32_t* __restrict__ ring, uint32_t start, int 
     const unsigned long long t1 = clk();
     if ((threadIdx.x & 31u) == 0u) out->cycles = t1 - t0;
     out->sink += i;
+}
+
+// The map row's copy: bulk copies (cp.async.bulk, TMA) of `bytes` in pieces
+// of `piece` bytes from a pseudo-random 16-byte-aligned row of a device buffer of
+// `n_rows` rows into shared memory, completing an mbarrier; every lane then
+// waits on it (bounded: at most 2^22 probes, else error bit 1 in out->sink's
+// high word and the loop stops).  Cycles per copy, issue to completion.
+// Every source address lies in the buffer: row < n_rows, row * stride +
+// bytes <= n_rows * stride.
+__global__ void k_bulk_row(const unsigned char* __restrict__ buf, uint32_t n_rows, uint32_t stride, uint32_t bytes,
+                           uint32_t piece, int copies, Out* out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t dst = bar + 16u;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncwarp();
+    uint32_t row = 12345u % n_rows;
+    unsigned long long err = 0;
+    const unsigned long long t0 = clk();
+    for (int c = 0; c < copies; ++c) {
+        const unsigned char* src = buf + (size_t)row * stride;
+        __syncwarp();
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        }
+        // the row in pieces of `piece` bytes (the last one shorter), issued
+        // one per lane side by side, all completing the one barrier
+        const uint32_t first = lane * piece;
+        if (first < bytes) {
+            const uint32_t len = min(piece, bytes - first);
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             dst + first),
+                         "l"(src + first), "r"(len), "r"(bar)
+                         : "memory");
+        }
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < (1u << 22) && !done; ++it)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done)
+                         : "r"(bar), "r"((uint32_t)c & 1u)
+                         : "memory");
+        if (!done) {
+            err = 1;
+            break;
+        }
+        // the next row depends on the copied data, so copies do not overlap
+        const uint32_t v = *(volatile const uint32_t*)(sm + 16);
+        row = (uint32_t)(((uint64_t)(row * 2654435761u + v + 1u)) % n_rows);
+    }
+    const unsigned long long t1 = clk_after_u32(row);
+    if (lane == 0) {
+        out->cycles = t1 - t0;
+        out->sink = (err << 32) | row;
+    }
 }
 
 // spins for `cycles` SM clock cycles (bounded by the count itself): timed
@@ -214,7 +299,7 @@ double hwlat_clock_mhz(unsigned long long cycles, void* out_dev) {
 int hwlat_steps() { return STEPS; }
 
 // class ids: 0 imad_hi, 1 hi_xor, 2 umul64hi, 3 imad_wide, 4 add64_sel,
-// 5 clz_norm, 6 add_xor, 8 ballot, 9 redux_min, 10 philox, 11 lds, 12 philox_split, 13 philox_m1
+// 5 clz_norm, 6 add_xor, 8 ballot, 9 redux_min, 10 philox, 11 lds, 12 philox_split, 13 philox_m1, 14 shfl_add
 // Runs the chain once in one warp of one block; returns its cycles, or a
 // negative CUDA error.  prm: 6 device words of runtime operands.
 long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
@@ -233,6 +318,7 @@ long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
         case 11: k_lds<<<1, 32>>>(prm, o); break;
         case 12: k_philox_split<<<1, 32>>>(prm, o); break;
         case 13: k_philox_m1<<<1, 32>>>(prm, o); break;
+        case 14: k_shfl_add<<<1, 32>>>(prm, o); break;
         default: return -1;
     }
     cudaError_t e = cudaDeviceSynchronize();
@@ -240,6 +326,24 @@ long long hwlat_run(int cls, const uint64_t* prm, void* out_dev) {
     Out h;
     e = cudaMemcpy(&h, o, sizeof(Out), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return -(long long)e;
+    return (long long)h.cycles;
+}
+
+// cycles per bulk row copy (see k_bulk_row); negative: CUDA error, or -1000
+// if a wait gave up
+long long hwlat_bulk_row(const unsigned char* buf, uint32_t n_rows, uint32_t stride, uint32_t bytes, uint32_t piece,
+                         int copies, void* out_dev) {
+    if (bytes % 16u || stride % 16u || bytes > stride || bytes > 32768u || n_rows == 0) return -1;
+    if (piece % 16u || piece == 0 || (uint64_t)piece * 32u < bytes) return -1;  // at most 32 pieces, 16-byte multiples
+    Out* o = (Out*)out_dev;
+    cudaFuncSetAttribute(k_bulk_row, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes + 16u));
+    k_bulk_row<<<1, 32, bytes + 16u>>>(buf, n_rows, stride, bytes, piece, copies, o);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return -(long long)e;
+    Out h;
+    e = cudaMemcpy(&h, o, sizeof(Out), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return -(long long)e;
+    if (h.sink >> 32) return -1000;
     return (long long)h.cycles;
 }
 

@@ -31,6 +31,7 @@ def test_latencies_plausible(lat):
     assert lat["hi_xor"] >= lat["imad_hi"]
     assert lat["lds"] < lat["ldg_dram"] and lat["ldg_l1"] < lat["ldg_dram"]
     assert 200.0 < lat["ldg_dram"] < 5000.0
+    assert 0.5 * lat["ldg_dram"] < lat["bulk_row"] < 20000.0
     assert 300.0 < lat["clock_mhz"] < 2200.0
 
 
