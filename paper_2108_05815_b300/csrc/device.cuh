@@ -125,14 +125,52 @@ __host__ __device__ __forceinline__ int64_t mulhi64s(int64_t a, int64_t b) {
 #endif
 }
 
-// The chain is built for latency: the normalising shift works on the high
-// word (n >= 2^32 for all but 2^-21 of the draws), the two 64-bit high
-// products that feed the bracket run in parallel, (53 - e) ln 2 plus the
-// rounding's half unit is formed off the chain, and the last step is one
-// two-word subtraction.
-__host__ __device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64_t* __restrict__ Ltab,
-                                                      const uint32_t* __restrict__ Rtab, uint64_t ln2_q64,
-                                                      int64_t c3) {
+__host__ __device__ __forceinline__ int clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)x);
+#else
+    return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// One exponential draw of the event search, in units of the grid the
+// running event time lives on.  In the interval's binade binary64 values are
+// the multiples of 2^sft units of 2^-58, so the search's draw lands on that
+// grid rounded twice: -ln U to binary64 (rn53 of X58), then the sum to the
+// grid.  Away from a grid midpoint (further than half the draw's binary64
+// ulp from one) the two roundings equal one rounding of X58 itself, which
+// needs neither the draw's binade nor the first rounding on the chain.
+// Returns
+//   x58:  X58, -ln U in units of 2^-58 (the value exp1_q58 returns);
+//   a:    X58 rounded to the grid, half down: (X58 + 2^(sft-1) - 1) >> sft;
+//   near: X58 lies within half its binary64 ulp (an upper bound of it) of a
+//         grid midpoint, or that ulp is not finer than the grid; the caller
+//         then rounds rn53(x58) to the grid itself.
+//
+// X58 follows the logarithm's definition step by step up to the series'
+// products; the last steps are regrouped (exactly):
+//   LN1P = S - 4 Q, LNM = L_j + floor(LN1P / 4) = L_j + floor(S / 4) - Q,
+//   X58 = floor((X64 + 32) / 64), X64 = (53 - e) LN2 - 4 LNM
+//       = floor((A0 - 4 floor(S / 4) + 4 Q) / 64),  A0 = (53 - e) LN2 + 32 - 4 L_j
+//       = U + floor((u - floor(S / 4) + Q) / 16),
+//   U = floor(A0 / 64), u = floor(A0 / 4) mod 16,
+// so that U, u and the bound of the ulp come from the table entry while the
+// series' products run, and three adds and a shift follow the last product.
+// X64 + 32 >= 28 for every draw (X64 = -4 at U = 1, its only negative
+// value), so the definition's clamp of X64 at 0 never changes X58.
+//
+// The rest of the chain is built for latency too: the normalising shift
+// works on the high word (n >= 2^32 for all but 2^-21 of the draws) and the
+// two 64-bit high products that feed the bracket run in parallel.
+struct GridDraw {
+    uint64_t x58;
+    uint64_t a;
+    bool near;
+};
+
+__host__ __device__ __forceinline__ GridDraw exp1_grid(uint64_t r53, const uint64_t* __restrict__ Ltab,
+                                                       const uint32_t* __restrict__ Rtab, uint64_t ln2_q64,
+                                                       int64_t c3, int sft) {
     const uint64_t n = r53 + 1ull;
     const uint32_t nh = (uint32_t)(n >> 32), nl = (uint32_t)n;
     int lz;            // leading zeros of n (64-bit): 10 .. 63
@@ -150,29 +188,45 @@ __host__ __device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64
     const uint32_t j = (Mh >> (31 - LN_BITS)) & (LN_N - 1u);
     const uint32_t R = Rtab[j];   // plain loads: the tables may sit in shared or global memory
     const uint64_t Lj = Ltab[j];
-    // K = (53 - e) ln 2 + 2^5 (the half unit of the final rounding) in Q0.64,
-    // 128-bit, independent of the table lookups
-    const uint64_t k = (uint64_t)(lz - 10);
+    // A0 = (53 - e) LN2 + 32 - 4 L_j, 128-bit two's complement; U and u
+    const uint64_t k = (uint64_t)(lz - 10);  // 53 - e
     const uint64_t klo = k * ln2_q64;
-    const uint64_t Klo = klo + 32ull;
-    const uint64_t Khi = umulhi64(k, ln2_q64) + (Klo < klo ? 1ull : 0ull);
-    // P = M R = (Mh R) 2^32 + Ml R; s = low 64 bits of P >> 31
+    const uint64_t khi = umulhi64(k, ln2_q64);
+    const uint64_t b0 = klo + 32ull;
+    const uint64_t l4 = Lj << 2;
+    const uint64_t alo = b0 - l4;
+    const uint64_t ahi = khi + (b0 < klo ? 1ull : 0ull) - (b0 < l4 ? 1ull : 0ull);
+    const uint64_t U = (ahi << 58) | (alo >> 6);
+    const int64_t u = (int64_t)((alo >> 2) & 15ull);
+    // the draw's binary64 ulp is at most 2^shu units: X58 <= (53 - e) LN2 / 64 + 1
+    const uint64_t xb = ((khi << 58) | (klo >> 6)) + 2ull;
+    const int shu = 11 - clz64(xb) > 0 ? 11 - clz64(xb) : 0;
+    // P = M R = (Mh R) 2^32 + Ml R; S = low 64 bits of P >> 31
     const uint64_t pl = (uint64_t)Ml * R;
     const uint64_t ph = (uint64_t)Mh * R;
     const int64_t s = (int64_t)((ph << 1) + (pl >> 31));
+    const int64_t v = u - (s >> 2);
     const int64_t s2 = mulhi64s(s, s);
     const int64_t s3 = mulhi64s(s, c3);
     const int64_t t = (1ll << 61) - (s3 >> 2) + (s2 >> 4);
     const int64_t q = (int64_t)umulhi64((uint64_t)s2, (uint64_t)t);
-    const int64_t ln1p = s - (q << 2);
-    const int64_t lnm = (int64_t)Lj + (ln1p >> 2);  // Q2.62
-    // x = K - 4 lnm (128-bit), 0 if negative, then the Q6.58 result x >> 6
-    const uint64_t slo = (uint64_t)lnm << 2;
-    const uint64_t shi = (uint64_t)(lnm >> 62);
-    const uint64_t xlo = Klo - slo;
-    const uint64_t xhi = Khi - shi - (Klo < slo ? 1ull : 0ull);
-    if ((int64_t)xhi < 0) return 0ull;
-    return (xhi << 58) | (xlo >> 6);
+    const uint64_t w = (uint64_t)((v + q) >> 4);
+    // the grid: 2^sft units, midpoint M, zone [M - H, M + H] around it
+    const uint64_t half = sft > 0 ? 1ull << (sft - 1) : 0ull;
+    const uint64_t gmask = (1ull << sft) - 1ull;
+    const uint64_t hu = shu > 0 ? 1ull << (shu - 1) : 0ull;
+    GridDraw g;
+    g.x58 = U + w;
+    g.a = ((U + half - 1ull) + w) >> sft;
+    g.near = sft <= shu || (((U - half + hu) + w) & gmask) <= 2ull * hu;
+    return g;
+}
+
+// Exp(1) of the draw r53 in Q6.58 (the grid parts of exp1_grid unused)
+__host__ __device__ __forceinline__ uint64_t exp1_q58(uint64_t r53, const uint64_t* __restrict__ Ltab,
+                                                      const uint32_t* __restrict__ Rtab, uint64_t ln2_q64,
+                                                      int64_t c3) {
+    return exp1_grid(r53, Ltab, Rtab, ln2_q64, c3, 1).x58;
 }
 
 // q rounded to 53 significant bits, to nearest, ties to even (q < 2^63.5):

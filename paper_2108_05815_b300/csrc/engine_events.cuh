@@ -177,13 +177,20 @@ __device__ double next_event_time_exp_int(const LaneSim& c, uint64_t loc, double
                 const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, j + w, TAG_INTERVAL);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint64_t R = rn53(exp1_q58((h ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
-                    fl[2 * w + h] = R >> sft;
+                    // rounded once from X58 away from a midpoint of u, else
+                    // to 53 bits first as binary64 does
+                    const GridDraw g = exp1_grid((h ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3, sft);
+                    uint64_t f = g.a;
                     uint32_t r = 0;
-                    if (sft > 0) {
-                        const uint64_t rem = R & ((1ull << sft) - 1ull), half = 1ull << (sft - 1);
-                        r = rem > half ? 1u : rem == half ? 2u : 0u;
+                    if (g.near) {
+                        const uint64_t R = rn53(g.x58);
+                        f = R >> sft;
+                        if (sft > 0) {
+                            const uint64_t rem = R & ((1ull << sft) - 1ull), half = 1ull << (sft - 1);
+                            r = rem > half ? 1u : rem == half ? 2u : 0u;
+                        }
                     }
+                    fl[2 * w + h] = f;
                     rnd[2 * w + h] = r;
                 }
             }
@@ -555,7 +562,6 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         // not depend on them and overlap their latency
         const uint64_t k = k0 + m;
         const u64x2 b = stream_block(c.sk0, c.sk1, loc, k, i >> 1, TAG_INTERVAL);
-        const uint64_t R = rn53(exp1_q58(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3));
         const int lg0 = 63 - __clzll((long long)k0);
         const int lg3 = 63 - __clzll((long long)(k0 + 3ull));
         const int lg = 63 - __clzll((long long)k);
@@ -565,15 +571,51 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         const uint64_t E = (k + 1ull) << sh;
         if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52))
             return coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
-        // x / u to the nearest integer, a tie rounded down here and settled
-        // below by the parity of the sum (R + half - 1 carries exactly when
-        // the remainder is above half)
-        const uint64_t gmask = (1ull << sft) - 1ull;
-        uint64_t a = (R + (gmask >> 1)) >> sft;
-        const bool tie = sft > 0 && (R & gmask) == (gmask >> 1) + 1ull;
-        // prefix sums as if no draw were a tie (rare); the tie vote runs
-        // beside them and a tie redoes them.  A draw of more than 2^54 u
-        // ends the interval whatever follows.
+        // the lane's draw in u, rounded once from X58 (exact away from a
+        // midpoint of u; the draws near one are rounded twice below)
+        const GridDraw g = exp1_grid(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3, sft);
+        const unsigned nearm = __ballot_sync(0xFFFFFFFFu, g.near);
+        const uint64_t tu = round == 0 ? T : 0ull;  // later rounds: every point is after tau
+        {
+            // The decision from four draws (the usual case): interval k0's
+            // first three points p0 <= p1 <= p2 by broadcast and local adds,
+            // and the later intervals' first points, whose lowest one below
+            // its interval's end is fetched while those adds run.  A draw of
+            // more than 2^54 u ends the interval whatever follows.
+            const uint64_t S = g.a < (1ull << 54) ? g.a : (1ull << 54);
+            const uint64_t P = P0 + S;
+            const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
+            const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
+            const uint64_t bl = __shfl_sync(0xFFFFFFFFu, bits, later ? __ffs(later) - 1 : 0);
+            const uint64_t s0 = __shfl_sync(0xFFFFFFFFu, S, 0);
+            const uint64_t s1 = __shfl_sync(0xFFFFFFFFu, S, 1);
+            const uint64_t s2 = __shfl_sync(0xFFFFFFFFu, S, 2);
+            const int sh0 = max(52 - lg0, 0);
+            const uint64_t p0 = (k0 << sh0) + s0, p1 = p0 + s1, p2 = p1 + s2;
+            // points at or below tau are passed; the first one after it
+            // either lies in interval k0 or ends it
+            if (!(nearm & 0x01010107u) && p2 > tu) {
+                const uint64_t pj = p0 > tu ? p0 : (p1 > tu ? p1 : p2);
+                if (pj < ((k0 + 1ull) << sh0))
+                    return __longlong_as_double(
+                        (long long)(((uint64_t)(lg0 + d + 1023) << 52) | (pj & 0xFFFFFFFFFFFFFull)));
+                if (later) return __longlong_as_double((long long)bl);
+                continue;  // intervals k0 .. k0 + 3 hold no point after tau
+            }
+        }
+        // All eight draws of interval k0 by prefix sums, each draw near a
+        // midpoint of u rounded as binary64 does: to 53 bits, then to u, the
+        // tie rounded down here and settled below by the parity of the sum
+        // (R + half - 1 carries exactly when the remainder is above half).
+        uint64_t a = g.a;
+        bool tie = false;
+        if (nearm) {
+            const uint64_t R = rn53(g.x58);
+            const uint64_t gmask = (1ull << sft) - 1ull;
+            a = (R + (gmask >> 1)) >> sft;
+            tie = sft > 0 && (R & gmask) == (gmask >> 1) + 1ull;
+        }
+        // prefix sums as if no draw were a tie (rare); a tie redoes them
         const unsigned ties = __ballot_sync(0xFFFFFFFFu, tie);
         uint64_t S = a < (1ull << 54) ? a : (1ull << 54);
 #pragma unroll
@@ -602,7 +644,6 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         // the three votes side by side: interval k0's first point after tau,
         // its end, and the later intervals' first points
         const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
-        const uint64_t tu = round == 0 ? T : 0ull;  // later rounds: every point is after tau
         const unsigned found = __ballot_sync(0xFFFFFFFFu, m == 0u && P > tu && P < E);
         const unsigned ended = __ballot_sync(0xFFFFFFFFu, m == 0u && P >= E);
         const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
