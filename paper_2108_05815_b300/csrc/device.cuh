@@ -98,8 +98,8 @@ struct __align__(16) LnTables {
     int64_t c3;          // round(2^64 / 3)
 };
 
-// 32-bit leading zeros, funnel shift and signed 64-bit high product, on
-// the device by intrinsic, on the host (tests) in plain C++
+// 32-bit leading zeros and funnel shift, on the device by intrinsic, on the
+// host (tests) in plain C++
 __host__ __device__ __forceinline__ int clz32(uint32_t x) {
 #ifdef __CUDA_ARCH__
     return __clz((int)x);
@@ -117,12 +117,27 @@ __host__ __device__ __forceinline__ uint32_t funnel_l(uint32_t lo, uint32_t hi, 
 #endif
 }
 
-__host__ __device__ __forceinline__ int64_t mulhi64s(int64_t a, int64_t b) {
+
+// floor(log2 x) for x >= 1: on the device the exponent of x converted to
+// binary32 rounding toward zero (shorter than a leading-zero count on B300)
+__host__ __device__ __forceinline__ int ilog2_32(uint32_t x) {
 #ifdef __CUDA_ARCH__
-    return __mul64hi(a, b);
+    return (int)(__float_as_uint(__uint2float_rz(x)) >> 23) - 127;
 #else
-    return (int64_t)(((__int128)a * b) >> 64);
+    return 31 - __builtin_clz(x);
 #endif
+}
+
+// Signed high products by one unsigned high product and a correction that
+// depends only on the sign (formed beside the product): a signed a < 0 read
+// as unsigned is a + 2^64, so
+//   floor(a b / 2^64) = hi(a b) - b          (b >= 0),
+//   floor(a^2 / 2^64) = hi(a a) - 2 a  mod 2^64.
+__host__ __device__ __forceinline__ int64_t mulhi64s_pos(int64_t a, uint64_t b) {
+    return (int64_t)(umulhi64((uint64_t)a, b) - (a < 0 ? b : 0ull));
+}
+__host__ __device__ __forceinline__ uint64_t sqrhi64s(int64_t a) {
+    return umulhi64((uint64_t)a, (uint64_t)a) - (a < 0 ? 2ull * (uint64_t)a : 0ull);
 }
 
 __host__ __device__ __forceinline__ int clz64(uint64_t x) {
@@ -159,9 +174,12 @@ __host__ __device__ __forceinline__ int clz64(uint64_t x) {
 // X64 + 32 >= 28 for every draw (X64 = -4 at U = 1, its only negative
 // value), so the definition's clamp of X64 at 0 never changes X58.
 //
-// The rest of the chain is built for latency too: the normalising shift
-// works on the high word (n >= 2^32 for all but 2^-21 of the draws) and the
-// two 64-bit high products that feed the bracket run in parallel.
+// The rest of the chain is built for latency too (each choice measured as a
+// dependent chain on B300): the normalising shift works on the high word
+// (n >= 2^32 for all but 2^-21 of the draws), takes its length from a
+// binary32 conversion's exponent and handles n < 2^32 by selects, not a
+// branch; the two high products that feed the bracket run in parallel, each
+// an unsigned product whose sign correction is formed beside it.
 struct GridDraw {
     uint64_t x58;
     uint64_t a;
@@ -173,18 +191,13 @@ __host__ __device__ __forceinline__ GridDraw exp1_grid(uint64_t r53, const uint6
                                                        int64_t c3, int sft) {
     const uint64_t n = r53 + 1ull;
     const uint32_t nh = (uint32_t)(n >> 32), nl = (uint32_t)n;
-    int lz;            // leading zeros of n (64-bit): 10 .. 63
-    uint32_t Mh, Ml;   // m 2^63 = n << lz, as two words
-    if (nh != 0u) {
-        lz = clz32(nh);
-        Mh = funnel_l(nl, nh, lz);
-        Ml = nl << lz;
-    } else {
-        const int l = clz32(nl);
-        lz = 32 + l;
-        Mh = nl << l;
-        Ml = 0u;
-    }
+    // m 2^63 = n << lz as two words, lz the leading zeros of n (10 .. 63);
+    // selects rather than a branch for the rare n < 2^32
+    const bool big = nh != 0u;
+    const int l = 31 - ilog2_32(big ? nh : nl);
+    const int lz = big ? l : 32 + l;
+    const uint32_t Mh = big ? funnel_l(nl, nh, l) : nl << l;
+    const uint32_t Ml = big ? nl << l : 0u;
     const uint32_t j = (Mh >> (31 - LN_BITS)) & (LN_N - 1u);
     const uint32_t R = Rtab[j];   // plain loads: the tables may sit in shared or global memory
     const uint64_t Lj = Ltab[j];
@@ -206,8 +219,8 @@ __host__ __device__ __forceinline__ GridDraw exp1_grid(uint64_t r53, const uint6
     const uint64_t ph = (uint64_t)Mh * R;
     const int64_t s = (int64_t)((ph << 1) + (pl >> 31));
     const int64_t v = u - (s >> 2);
-    const int64_t s2 = mulhi64s(s, s);
-    const int64_t s3 = mulhi64s(s, c3);
+    const int64_t s2 = (int64_t)sqrhi64s(s);
+    const int64_t s3 = mulhi64s_pos(s, (uint64_t)c3);
     const int64_t t = (1ll << 61) - (s3 >> 2) + (s2 >> 4);
     const int64_t q = (int64_t)umulhi64((uint64_t)s2, (uint64_t)t);
     const uint64_t w = (uint64_t)((v + q) >> 4);
