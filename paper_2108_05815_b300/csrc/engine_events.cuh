@@ -550,12 +550,16 @@ __device__ double coop_next_exp_short_fp(const LaneSim& c, uint64_t loc, double 
 // DT: delta_t = 2^DT known at compile time (DT_ANY: the simulation's own)
 constexpr int DT_ANY = 99;
 
+// kio: in, floor(tau / delta_t), the interval index of tau, which the
+// caller carries from the search that returned tau (so that it is not
+// recomputed from tau's bits on the chain); out, that of the result.
 template <int DT>
-__device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane) {
+__device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double tau, const LnC& ln, uint32_t lane,
+                                       uint64_t& kio) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     const uint32_t m = lane >> 3, i = lane & 7u;
     const int d = DT == DT_ANY ? c.dt_log2 : DT;
-    uint64_t k0 = floor_div_pow2(tau_b, d);
+    uint64_t k0 = kio;
     const uint64_t T = (tau_b & 0xFFFFFFFFFFFFFull) | (1ull << 52);  // tau in units of interval k0
     for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
         // the draws first: the range check and the interval bounds below do
@@ -569,8 +573,11 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         const int sh = max(52 - lg, 0);  // in range below: 1 .. 52
         const uint64_t P0 = k << sh;
         const uint64_t E = (k + 1ull) << sh;
-        if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52))
-            return coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
+        if (k0 == 0ull || lg0 + d + 6 < 0 || lg3 + d + 6 > 63 || k0 + 4ull >= (1ull << 52)) {
+            const double r = coop_next_exp_short_fp<true>(c, loc, tau, ln, lane);
+            kio = floor_div_pow2((uint64_t)__double_as_longlong(r), d);
+            return r;
+        }
         // the lane's draw in u, rounded once from X58 (exact away from a
         // midpoint of u; the draws near one are rounded twice below)
         const GridDraw g = exp1_grid(((i & 1u) ? b.hi : b.lo) >> 11, ln.L, ln.R, ln.ln2, ln.c3, sft);
@@ -582,11 +589,14 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
             // and the later intervals' first points, whose lowest one below
             // its interval's end is fetched while those adds run.  A draw of
             // more than 2^54 u ends the interval whatever follows.
-            const uint64_t S = g.a < (1ull << 54) ? g.a : (1ull << 54);
+            // (with delta_t = 1 a draw is below 2^58 u: three of them cannot
+            // overflow, and the cap is left out)
+            const uint64_t S = DT == 0 || g.a < (1ull << 54) ? g.a : (1ull << 54);
             const uint64_t P = P0 + S;
             const uint64_t bits = ((uint64_t)(lg + d + 1023) << 52) | (P & 0xFFFFFFFFFFFFFull);
             const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
-            const uint64_t bl = __shfl_sync(0xFFFFFFFFu, bits, later ? __ffs(later) - 1 : 0);
+            const int wl = (later & 0x100u) ? 8 : ((later & 0x10000u) ? 16 : 24);  // lanes 8, 16, 24 vote
+            const uint64_t bl = __shfl_sync(0xFFFFFFFFu, bits, wl);
             const uint64_t s0 = __shfl_sync(0xFFFFFFFFu, S, 0);
             const uint64_t s1 = __shfl_sync(0xFFFFFFFFu, S, 1);
             const uint64_t s2 = __shfl_sync(0xFFFFFFFFu, S, 2);
@@ -596,10 +606,15 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
             // either lies in interval k0 or ends it
             if (!(nearm & 0x01010107u) && p2 > tu) {
                 const uint64_t pj = p0 > tu ? p0 : (p1 > tu ? p1 : p2);
-                if (pj < ((k0 + 1ull) << sh0))
+                if (pj < ((k0 + 1ull) << sh0)) {
+                    kio = k0;
                     return __longlong_as_double(
                         (long long)(((uint64_t)(lg0 + d + 1023) << 52) | (pj & 0xFFFFFFFFFFFFFull)));
-                if (later) return __longlong_as_double((long long)bl);
+                }
+                if (later) {
+                    kio = k0 + (uint64_t)(wl >> 3);
+                    return __longlong_as_double((long long)bl);
+                }
                 continue;  // intervals k0 .. k0 + 3 hold no point after tau
             }
         }
@@ -648,12 +663,19 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
         const unsigned ended = __ballot_sync(0xFFFFFFFFu, m == 0u && P >= E);
         const unsigned later = __ballot_sync(0xFFFFFFFFu, m > 0u && i == 0u && P < E);
         const unsigned hit = found | ended;
-        if (!hit) return coop_next_exp<true>(c, loc, tau, ln, lane);  // eight points up to tau
+        if (!hit) {  // eight points up to tau
+            const double r = coop_next_exp<true>(c, loc, tau, ln, lane);
+            kio = floor_div_pow2((uint64_t)__double_as_longlong(r), d);
+            return r;
+        }
         const int j = __ffs(hit) - 1;
         // the first point of interval k0 after tau, else (interval k0 ended
         // first) the first point of the lowest later interval that has one
         const int w = (found >> j) & 1u ? j : (later ? __ffs(later) - 1 : -1);
-        if (w >= 0) return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, bits, w));
+        if (w >= 0) {
+            kio = k0 + (uint64_t)(w >> 3);
+            return __longlong_as_double((long long)__shfl_sync(0xFFFFFFFFu, bits, w));
+        }
     }
     return -1.0;
 }
@@ -661,9 +683,14 @@ __device__ double coop_next_exp_int_dt(const LaneSim& c, uint64_t loc, double ta
 // delta_t = 1, the usual case, with its shifts and bounds folded (about 3 %
 // shorter per event than the general form on B300)
 __device__ __forceinline__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, const LnC& ln,
+                                                    uint32_t lane, uint64_t& kio) {
+    return c.dt_log2 == 0 ? coop_next_exp_int_dt<0>(c, loc, tau, ln, lane, kio)
+                          : coop_next_exp_int_dt<DT_ANY>(c, loc, tau, ln, lane, kio);
+}
+__device__ __forceinline__ double coop_next_exp_int(const LaneSim& c, uint64_t loc, double tau, const LnC& ln,
                                                     uint32_t lane) {
-    return c.dt_log2 == 0 ? coop_next_exp_int_dt<0>(c, loc, tau, ln, lane)
-                          : coop_next_exp_int_dt<DT_ANY>(c, loc, tau, ln, lane);
+    uint64_t k = floor_div_pow2((uint64_t)__double_as_longlong(tau), c.dt_log2);
+    return coop_next_exp_int(c, loc, tau, ln, lane, k);
 }
 
 template <bool LAM1>
