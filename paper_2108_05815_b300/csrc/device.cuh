@@ -80,6 +80,18 @@ __host__ __device__ __forceinline__ uint64_t umulhi64(uint64_t a, uint64_t b) {
 #endif
 }
 
+// floor(a b / 2^64) for a 32-bit b, by two 32-bit products: with
+// a = h 2^32 + l, floor(a b / 2^64) = floor((h b + floor(l b / 2^32)) / 2^32)
+// (the sum stays below 2^64); shorter than a 64 x 64 high product
+__host__ __device__ __forceinline__ uint64_t mulhi_u64_u32(uint64_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    const uint64_t hb = (uint64_t)(uint32_t)(a >> 32) * b;
+    return (hb + __umulhi((uint32_t)a, b)) >> 32;
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Exp(1) by inverse transform of U = (r + 1) 2^-53, r the top 53 bits of a
 // draw: -ln U = (53 - e) ln 2 - ln m for r + 1 = m 2^e, m in [1, 2).

@@ -714,7 +714,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
                                             uint64_t d1, uint64_t d2, uint64_t d3,
                                             const uint64_t* srow = nullptr) {
     const int kind = KIND >= 0 ? KIND : c.kind;
-    if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, umulhi64(d1, c.D));
+    if (kind == KIND_NONSPATIAL) return pack_loc(0, 0, mulhi_u64_u32(d1, c.D));
     if (kind == KIND_IMPLICIT) {
         // in the metacommunity: a uniform parent there (d1); locally:
         // migration iff d1 says so, then the parent's index (d2) in the
@@ -722,7 +722,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
         const uint64_t meta_n = c.meta_size;
         if (in_meta(loc)) return meta_loc(umulhi64(d1, meta_n));
         if ((d1 >> 11) < c.m_thr) return meta_loc(umulhi64(d2, meta_n));
-        return pack_loc(0, 0, umulhi64(d2, c.D));
+        return pack_loc(0, 0, mulhi_u64_u32(d2, c.D));
     }
     const uint32_t x = loc_x(loc), y = loc_y(loc);
     if (kind == KIND_TORUS) {
@@ -740,7 +740,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
         }
         const uint32_t tx = wrap_add(x, (int32_t)cx - c.gauss_half, c.W);
         const uint32_t ty = wrap_add(y, (int32_t)cy - c.gauss_half, c.H);
-        const uint64_t ti = c.D > 1 ? umulhi64(d3, c.D) : 0ull;
+        const uint64_t ti = c.D > 1 ? mulhi_u64_u32(d3, c.D) : 0ull;
         return pack_loc(tx, ty, ti);
     }
     // habitat map: the origin cell's alias entry (which carries the alias
@@ -759,7 +759,7 @@ __device__ __forceinline__ uint64_t disperse(const LaneSim& c, const SimParams* 
     const uint32_t d = (uint32_t)(e >> (take_col ? 46 : 54)) & 0xFFu;
     const uint32_t tx = wrap_add(x, dx, c.W);
     const uint32_t ty = wrap_add(y, dy, c.H);
-    return pack_loc(tx, ty, umulhi64(d2, d));
+    return pack_loc(tx, ty, mulhi_u64_u32(d2, d));
 }
 
 // A map lineage's next dispersal reads one entry of its cell's alias row.
