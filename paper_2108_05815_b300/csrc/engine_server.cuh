@@ -76,6 +76,11 @@ struct SrvSlot {
     uint32_t g0 = 0, n = 0;
     uint64_t bytes = 0;
     bool active = false;
+    // what the warp kernel's specialisation depends on: the landscape kind,
+    // and whether the request sums exponentials at lambda = 1 or draws
+    // Poisson points, on the short searches
+    int32_t kind = -1;
+    bool exp1 = false, pois = false;
 };
 
 struct ind_server {
@@ -243,6 +248,9 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         sv->bytes_admitted += bytes;
         SimParams hp;
         fill_params(m, b.tun, hp);
+        sl.kind = hp.kind;
+        sl.exp1 = hp.sampler == IND_SAMPLER_EXP && hp.coop_short && hp.lambda == 1.0;
+        sl.pois = hp.sampler == IND_SAMPLER_POISSON && hp.coop_short;
         hp.n_lineages = n;
         hp.slot_base = (uint64_t)slot << 32;  // slots of different requests never collide
         hp.gid_base = g0;
@@ -282,6 +290,33 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         CK(cudaStreamSynchronize(s));  // the pageable sources above are locals
     }
     return IND_OK;
+}
+
+// The warp kernel's specialisation for the resident requests, as a batch
+// chooses it for its simulations (search form and landscape kind, where all
+// of them share one); a change re-captures the chunk's graph.  The form is
+// chosen between chunks, so the requests of every launched chunk match the
+// kernel that runs them.
+static void srv_specialise(ind_server* sv) {
+    Batch& b = sv->b;
+    bool any = false, all_exp1 = true, all_pois = true;
+    int kind = -1;
+    for (const SrvSlot& sl : sv->slots) {
+        if (!sl.active || sl.n == 0) continue;
+        kind = !any ? sl.kind : (kind == sl.kind ? kind : -1);
+        any = true;
+        all_exp1 &= sl.exp1;
+        all_pois &= sl.pois;
+    }
+    if (!any) return;  // nothing resident: the next admission decides
+    const int mode = all_exp1 ? 1 : all_pois ? 2 : 0;
+    if (mode == b.coop_mode && kind == b.coop_kind) return;
+    b.coop_mode = mode;
+    b.coop_kind = kind;
+    if (b.graph) {
+        cudaGraphExecDestroy(b.graph);
+        b.graph = nullptr;
+    }
 }
 
 extern "C" {
@@ -459,6 +494,7 @@ ind_status srv_step(ind_server* sv, uint32_t rounds, uint64_t* finished, uint32_
     ind_status st = srv_admit(sv, newly_done);  // requests with no lineages finish at once
     if (st != IND_OK) return st;
     // 3. launch the next chunk of rounds on the main stream
+    srv_specialise(sv);
     if (sv->n_total > 0) {
         st = batch_rounds(b, rounds);
         if (st != IND_OK) return st;

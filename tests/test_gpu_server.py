@@ -37,7 +37,8 @@ REQUESTS = [
 def make(r):
     s = ind.Simulation(r["kind"], r["nu"], r["seed"], width=r["width"], height=r["height"], deme=r["deme"],
                        sigma=r.get("sigma", 0.0), migration=r.get("migration", 0.0),
-                       meta_size=r.get("meta_size", 0), meta_nu=r.get("meta_nu", 0.0))
+                       meta_size=r.get("meta_size", 0), meta_nu=r.get("meta_nu", 0.0),
+                       sampler=r.get("sampler", ind.SAMPLER_EXP))
     s.sample(r["fraction"], r["sample_seed"])
     return s
 
@@ -107,6 +108,32 @@ def test_served_matches_oracle_under_tight_budget():
         ids, K, gkl, gkt = got[k]
         assert K == oK and np.array_equal(ids, oids)
         assert np.array_equal(gkl, kl) and np.array_equal(gkt, kt)
+
+
+@pytest.mark.parametrize("sampler", [ind.SAMPLER_EXP, ind.SAMPLER_POISSON])
+def test_served_uniform_requests_use_the_specialised_kernel(sampler):
+    """Requests that all share one landscape kind and search form are run by
+    the warp kernel specialised for them (chosen from the resident requests
+    between chunks); a non-spatial request arriving later switches the form
+    back to the general one and then away again.  Every result equals the
+    request run alone and the oracle's."""
+    tori = [r for r in REQUESTS if r["kind"] == W.TORUS]
+    reqs = [dict(r, sampler=sampler) for r in tori] + [dict(REQUESTS[1], sampler=sampler)]
+    ref = [alone(r) for r in reqs]
+    arrivals = [0, 0, 2, 2, 3, 6][:len(reqs)]
+    assert len(reqs) == 6
+    got, st = serve(reqs, budget=1 << 33, max_sims=16, rounds=3, arrivals=arrivals)
+    assert st["finished"] == len(reqs)
+    for k in range(len(reqs)):
+        ids, K, kl, kt = got[k]
+        rid, rK, rkl, rkt = ref[k]
+        assert K == rK and np.array_equal(ids, rid)
+        assert np.array_equal(kl, rkl) and np.array_equal(kt, rkt)
+    r = reqs[0]
+    m = O.Model(r["kind"], r["width"], r["height"], r["deme"], r["nu"], r["seed"], sigma=r.get("sigma"),
+                sampler=sampler)
+    kl, kt, _ = m.run_merge(m.sample(r["fraction"], r["sample_seed"]))
+    assert np.array_equal(got[0][2], kl) and np.array_equal(got[0][3], kt)
 
 
 def test_served_empty_request_finishes_without_species():
