@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2, help="config 4: timed batches")
     ap.add_argument("--plain-subset", type=int, default=32, help="config 4: simulations timed one by one")
     ap.add_argument("--served-rate", type=float, default=10.0,
-                    help="config 5: offered requests per second (10: at the edge of what the server sustains)")
+                    help="config 5: offered requests per second (10: about the most the server sustains)")
     ap.add_argument("--served-window", type=float, default=20.0, help="config 5: arrival window in seconds")
     ap.add_argument("--served-plain", type=int, default=8,
                     help="config 5: requests re-run one by one on the plain path (0: none)")

@@ -8,6 +8,7 @@ different inputs check that a call does not see the previous call's leftovers.
 This file is collected last on purpose.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -83,14 +84,22 @@ def test_static_rank_allocates_nothing(torch_cuda):
         calls["n"] += 1
 
     refusing = ind.Allocator(ind._ALLOC(alloc), ind._RELEASE(release), None)
-    torch.cuda.synchronize()
-    before = torch.cuda.memory_allocated()
-    assert ind.lib().ind_set_allocator(ctypes.byref(refusing)) == 0
+    # tensors of earlier tests that only the cyclic collector frees must not
+    # be freed inside the measured window: collect first, then hold it off
+    gc.collect()
+    gc.disable()
     try:
-        K = ind.species_rank_static(dl, dt, out)
         torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        assert ind.lib().ind_set_allocator(ctypes.byref(refusing)) == 0
+        try:
+            K = ind.species_rank_static(dl, dt, out)
+            torch.cuda.synchronize()
+        finally:
+            assert ind.lib().ind_set_allocator(ctypes.byref(ind._torch_alloc)) == 0
+        after = torch.cuda.memory_allocated()
     finally:
-        assert ind.lib().ind_set_allocator(ctypes.byref(ind._torch_alloc)) == 0
+        gc.enable()
     assert calls["n"] == 0
-    assert torch.cuda.memory_allocated() == before
+    assert after == before
     assert K == K_ref and np.array_equal(out.cpu().numpy().view(np.uint64), ids_ref)
