@@ -516,8 +516,10 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         }
         const uint64_t hz = (uint64_t)__double_as_longlong(c.horizon);
         uint32_t ev_lin = 0;
-        // MODE 1: the interval index of tn, carried from search to search
-        uint64_t kc = MODE == 1 ? floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2) : 0ull;
+        // MODES 1 and 2: the interval index of tn, carried from search to
+        // search (MODE 2 forms it as soon as the search returns, ahead of the
+        // next event's draws)
+        uint64_t kc = MODE == 1 || MODE == 2 ? floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2) : 0ull;
         // a map lineage's alias row, staged in the warp's buffer
         const bool stage = B.stage_bytes && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP));
         const uint64_t* srow = stage ? row_stage_issue(rs, sbuf, B.P, c, loc, lane, B) : nullptr;
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
             if (MODE == 1) {
                 nt = coop_next_exp_int(c, loc, tn, ln, lane, kc);
             } else if (MODE == 2) {
-                nt = coop_next_poisson_short(c, loc, tn, lane);
+                nt = coop_next_poisson_short(c, loc, tn, lane, kc);
             } else {
                 nt = c.sampler == 1 ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
                                                     : coop_next_poisson(c, loc, tn, lane))
@@ -582,6 +584,7 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
                 break;
             }
             tn = nt;
+            if (MODE == 2) kc = floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2);
         }
     }
     // a row copy still in flight lands before the block's shared memory goes

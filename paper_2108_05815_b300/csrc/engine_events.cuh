@@ -444,11 +444,12 @@ __device__ double coop_next_poisson_short_fp(const LaneSim& c, uint64_t loc, dou
 // A sum that rounds up to (k + 1) dt is that value (2^(e+1) when it starts
 // the next binade).  No binary64 arithmetic is on the chain.  k = 0 and
 // k near 2^52 go to the binary64 form.
-__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+// k0: floor(tau / delta_t), the interval index of tau (the caller may form
+// it ahead, off the event chain)
+__device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane, uint64_t k0) {
     const uint64_t tau_b = (uint64_t)__double_as_longlong(tau);
     const uint32_t m = lane >> 3, i = lane & 7u;
     const int d = c.dt_log2;
-    uint64_t k0 = floor_div_pow2(tau_b, d);
     if (k0 == 0ull) return coop_next_poisson_short_fp(c, loc, tau, lane);
     for (uint32_t round = 0; round < INTERVAL_LIMIT / 4; ++round, k0 += 4ull) {
         if (k0 + 4ull >= (1ull << 52)) return coop_next_poisson(c, loc, tau, lane);
@@ -485,6 +486,9 @@ __device__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double
         }
     }
     return -1.0;
+}
+__device__ __forceinline__ double coop_next_poisson_short(const LaneSim& c, uint64_t loc, double tau, uint32_t lane) {
+    return coop_next_poisson_short(c, loc, tau, lane, floor_div_pow2((uint64_t)__double_as_longlong(tau), c.dt_log2));
 }
 
 // sums of exponentials: every lane runs interval k's binary64 running sum in
