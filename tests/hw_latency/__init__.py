@@ -81,6 +81,8 @@ def lib():
                                      ctypes.c_int, ctypes.c_void_p]
         L.hwlat_clock_mhz.restype = ctypes.c_double
         L.hwlat_clock_mhz.argtypes = [ctypes.c_ulonglong, ctypes.c_void_p]
+        L.hwlat_philox_throughput.restype = ctypes.c_double
+        L.hwlat_philox_throughput.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -96,7 +98,8 @@ def _ring(torch, n, seed):
 def measure(reps=3, dram_ring_mib=512, dram_steps=4000):
     """cycles per dependent step of every class (best of `reps`), dependent
     global-load latencies (L1 hit; L2 miss to DRAM over a ring larger than
-    L2), and the SM clock in MHz during the run"""
+    L2), the SM clock in MHz during the run, and the integer throughput of
+    the Philox mix on all SMs in Tops/s (philox_tput_tops)"""
     import torch
     L = lib()
     steps = L.hwlat_steps()
@@ -138,6 +141,16 @@ def measure(reps=3, dram_ring_mib=512, dram_steps=4000):
     res["bulk_row"] = min(res["bulk_row_%d" % k] for k in (1, 4, 8, 31))
     del buf
     res["clock_mhz"] = L.hwlat_clock_mhz(200_000_000, ctypes.c_void_p(out.data_ptr()))
+    # integer throughput of the library's op mix on every SM: independent
+    # Philox4x32-10 blocks, 100 integer ops each (best of `reps`)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    best = 0.0
+    for _ in range(reps):
+        v = L.hwlat_philox_throughput(sms, 8, 256, ctypes.c_void_p(out.data_ptr()))
+        if v < 0:
+            raise RuntimeError("Philox throughput kernel failed: CUDA error %d" % int(-v))
+        best = max(best, v)
+    res["philox_tput_tops"] = best / 1e12
     res["steps_per_chain"] = steps
     return res
 

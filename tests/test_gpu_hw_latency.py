@@ -48,3 +48,14 @@ def test_floor_below_lone_lineage_event(lat):
     for sampler in ("exp", "poisson"):
         f = H.event_floor(lat, sampler, "torus")
         assert 100.0 < f < cycles_per_event, (sampler, f, cycles_per_event)
+
+
+def test_integer_throughput_plausible(lat):
+    """the measured integer peak of the Philox mix is of the order of every
+    lane issuing one integer instruction per cycle at the measured clock"""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lanes_peak = sms * 128 * lat["clock_mhz"] * 1e6 / 1e12
+    # (a block counts 100 ops for about 45 instructions: a wide product is a
+    # high and a low product, a three-input xor two xors)
+    assert 0.05 * lanes_peak < lat["philox_tput_tops"] < 3.0 * lanes_peak, (lat["philox_tput_tops"], lanes_peak)
