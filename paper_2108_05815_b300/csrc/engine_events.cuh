@@ -549,7 +549,12 @@ __device__ double coop_next_exp_short_fp(const LaneSim& c, uint64_t loc, double 
 // follows from the ties and the parities of the lanes below (two ballots).
 // Prefix sums over lanes 8 m .. 8 m + 7 (shuffles) then give every point of
 // interval k at once, where the binary64 form adds them one after another
-// at 64 cycles per add on B300.  Outside its range (k = 0, extreme delta_t,
+// at 64 cycles per add on B300.  Usually the first point after tau is among
+// the first three of interval k0, or that interval ends first: every lane
+// then decides from interval k0's first three draws (broadcast) and, where
+// that interval ends first, the first point of the lowest later interval
+// that has one (chosen by a vote), without the prefix sums or the tie
+// votes.  Outside its range (k = 0, extreme delta_t,
 // k near 2^52) it hands over to the binary64 form.
 // DT: delta_t = 2^DT known at compile time (DT_ANY: the simulation's own)
 constexpr int DT_ANY = 99;
