@@ -520,71 +520,86 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
         // search (MODE 2 forms it as soon as the search returns, ahead of the
         // next event's draws)
         uint64_t kc = MODE == 1 || MODE == 2 ? floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2) : 0ull;
-        // a map lineage's alias row, staged in the warp's buffer
-        const bool stage = B.stage_bytes && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP));
-        const uint64_t* srow = stage ? row_stage_issue(rs, sbuf, B.P, c, loc, lane, B) : nullptr;
-        for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
-            // the event's draws ahead of the horizon test, so that their
-            // Philox block overlaps it (a lineage at its horizon drops them)
-            const uint32_t row_ready = stage ? row_stage_poll(rs) : 1u;
-            const EventDraws ed = event_draws_warp<KIND>(c, B.P, loc, tn, lane);
-            if ((uint64_t)__double_as_longlong(tn) > hz) {
-                if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
-                    L.loc[idx] = loc;
-                    L.tn[idx] = tn;
-                    if (LOG) L.tp[idx] = tprev;
-                    if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+        // the lineage's events, in the code specialised for its landscape kind:
+        // a kernel for one kind runs that form, the general kernel chooses the
+        // form once per lineage (measured on B300, the general form of the
+        // event's draws and move cost about 100 cycles per event)
+        auto events = [&](auto kind_tag) {
+            constexpr int K = decltype(kind_tag)::value;
+            // a map lineage's alias row, staged in the warp's buffer
+            const bool stage = B.stage_bytes && (K == KIND_MAP || (K < 0 && c.kind == KIND_MAP));
+            const uint64_t* srow = stage ? row_stage_issue(rs, sbuf, B.P, c, loc, lane, B) : nullptr;
+            for (uint32_t guard = 0; guard < 0xFFFFFFFFu; ++guard) {
+                // the event's draws ahead of the horizon test, so that their
+                // Philox block overlaps it (a lineage at its horizon drops them)
+                const uint32_t row_ready = stage ? row_stage_poll(rs) : 1u;
+                const EventDraws ed = event_draws_warp<K>(c, B.P, loc, tn, lane);
+                if ((uint64_t)__double_as_longlong(tn) > hz) {
+                    if (lane == 0 && ev_lin) {  // moved this round (see k_compact)
+                        L.loc[idx] = loc;
+                        L.tn[idx] = tn;
+                        if (LOG) L.tp[idx] = tprev;
+                        if (B.dedup) dedup_insert(B, t, slot_key(B.P, c, loc), gid);
+                    }
+                    break;
                 }
-                break;
-            }
-            ++ev_raw;
-            lane_max = max(lane_max, ++ev_lin);
-            if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
-            const uint64_t at = loc;
-            if (stage) row_stage_finish(rs, B, row_ready);
-            const uint64_t moved = disperse<KIND>(c, B.P, loc, ed.d1, ed.d2, ed.d3, srow);
-            const bool speciated = ed.spec;
-            loc = speciated ? loc : moved;
-            if (LOG) {
-                warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
-                tprev = tn;
-            }
-            if (!speciated && stage) srow = row_stage_issue(rs, sbuf, B.P, c, loc, lane, B);
-            else if (!speciated && (KIND == KIND_MAP || (KIND < 0 && c.kind == KIND_MAP)))
-                prefetch_alias_row(B.P, c, loc, lane);
-            if (speciated) {
-                if (lane == 0) {
-                    B.key_loc[gid] = loc;
-                    B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
-                    L.gid[idx] = gid | DONE_BIT;
+                ++ev_raw;
+                lane_max = max(lane_max, ++ev_lin);
+                if (COUNT && lane == 0) ev_unique += count_event(B, t, slot_key(B.P, c, loc), tn) ? 1u : 0u;
+                const uint64_t at = loc;
+                if (stage) row_stage_finish(rs, B, row_ready);
+                const uint64_t moved = disperse<K>(c, B.P, loc, ed.d1, ed.d2, ed.d3, srow);
+                const bool speciated = ed.spec;
+                loc = speciated ? loc : moved;
+                if (LOG) {
+                    warp_log_event(B, wlog, lane, tn, tprev, at, speciated ? ~0ull : loc, gid);
+                    tprev = tn;
                 }
-                break;
-            }
-            double nt;
-            if (MODE == 1) {
-                nt = coop_next_exp_int(c, loc, tn, ln, lane, kc);
-            } else if (MODE == 2) {
-                nt = coop_next_poisson_short(c, loc, tn, lane, kc);
-            } else {
-                nt = c.sampler == 1 ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
-                                                    : coop_next_poisson(c, loc, tn, lane))
-                     : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
-                                              : coop_next_exp_short<false>(c, loc, tn, ln, lane))
-                                    : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
-                                              : coop_next_exp<false>(c, loc, tn, ln, lane));
-            }
-            if (search_failed(nt)) {
-                if (lane == 0) {
-                    atomicOr(&B.S[c.sim].error, 1u);
-                    atomicOr(&B.G->error, 1u);
-                    B.key_loc[gid] = ~0ull;
-                    B.key_time[gid] = ~0ull;
-                    L.gid[idx] = gid | DONE_BIT;
+                if (!speciated && stage) srow = row_stage_issue(rs, sbuf, B.P, c, loc, lane, B);
+                else if (!speciated && (K == KIND_MAP || (K < 0 && c.kind == KIND_MAP)))
+                    prefetch_alias_row(B.P, c, loc, lane);
+                if (speciated) {
+                    if (lane == 0) {
+                        B.key_loc[gid] = loc;
+                        B.key_time[gid] = (uint64_t)__double_as_longlong(tn);
+                        L.gid[idx] = gid | DONE_BIT;
+                    }
+                    break;
                 }
-                break;
+                double nt;
+                if (MODE == 1) {
+                    nt = coop_next_exp_int(c, loc, tn, ln, lane, kc);
+                } else if (MODE == 2) {
+                    nt = coop_next_poisson_short(c, loc, tn, lane, kc);
+                } else {
+                    nt = c.sampler == 1 ? (c.coop_short ? coop_next_poisson_short(c, loc, tn, lane)
+                                                        : coop_next_poisson(c, loc, tn, lane))
+                         : c.coop_short ? (c.lam1 ? coop_next_exp_short<true>(c, loc, tn, ln, lane)
+                                                  : coop_next_exp_short<false>(c, loc, tn, ln, lane))
+                                        : (c.lam1 ? coop_next_exp<true>(c, loc, tn, ln, lane)
+                                                  : coop_next_exp<false>(c, loc, tn, ln, lane));
+                }
+                if (search_failed(nt)) {
+                    if (lane == 0) {
+                        atomicOr(&B.S[c.sim].error, 1u);
+                        atomicOr(&B.G->error, 1u);
+                        B.key_loc[gid] = ~0ull;
+                        B.key_time[gid] = ~0ull;
+                        L.gid[idx] = gid | DONE_BIT;
+                    }
+                    break;
+                }
+                tn = nt;
+                if (MODE == 2) kc = floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2);
             }
-            tn = nt;
-            if (MODE == 2) kc = floor_div_pow2((uint64_t)__double_as_longlong(tn), c.dt_log2);
+        };
+        if constexpr (KIND >= 0) {
+            events(std::integral_constant<int, KIND>());
+        } else {
+            if (c.kind == KIND_NONSPATIAL) events(std::integral_constant<int, KIND_NONSPATIAL>());
+            else if (c.kind == KIND_TORUS) events(std::integral_constant<int, KIND_TORUS>());
+            else if (c.kind == KIND_MAP) events(std::integral_constant<int, KIND_MAP>());
+            else events(std::integral_constant<int, KIND_IMPLICIT>());
         }
     }
     // a row copy still in flight lands before the block's shared memory goes

@@ -42,7 +42,7 @@ def test_gpu_arm_line():
     assert d["config"]["workload"].startswith("config3") and "l2" in d["config"]
     rf = d["roofline"]
     assert rf["bound"] in ("hbm", "tensor", "alu") and rf["peak"] > 0
-    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9 and "derived" in rf["peak_source"]
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-9 and "measured on this GPU" in rf["peak_source"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0 and cb["sample"]
     e2e = d["e2e"]
