@@ -257,6 +257,22 @@ def longest_descent(workload, sampler):
     return None
 
 
+def config4_longest(sampler):
+    """the longest line of descent of any simulation of config 4 (the oracle's
+    mode M, tests/golden/config4_digest.txt) and that simulation's index and
+    landscape kind; None if not stored"""
+    p = os.path.join(ROOT, "tests", "golden", "config4_digest.txt")
+    if not os.path.exists(p):
+        return None
+    best = None
+    for line in open(p):
+        f = line.split()
+        if len(f) == 9 and f[0] == "config4" and f[1] == sampler:
+            if best is None or int(f[7]) > best[0]:
+                best = (int(f[7]), int(f[2]), f[3])
+    return best
+
+
 _floor_cache = {}
 
 
@@ -684,6 +700,22 @@ def batched_leg(args, local, sampler_name="exp"):
     plain_est_s = plain_s * len(specs) / len(subset)
     ops = ops_per_event(sampler_name, "torus")
     avg_launch_ms = adv_ms / max(adv_n, 1)
+    latency = {"critical_events_per_batch": crit, "ns_per_critical_event": ms * 1e6 / max(crit, 1),
+               "what": "the batch lasts as long as its longest dependent chain of events"}
+    longest = config4_longest(sampler_name)
+    if longest and not args.no_floor:
+        # the binding roofline: no schedule ends the batch before the longest
+        # line of descent of its simulations has run, one hardware-floor event
+        # after another
+        L, k_long, kind = longest
+        H, lat = hw_latencies()
+        ns = H.event_floor(lat, sampler_name, kind) / lat["clock_mhz"] * 1e3
+        latency["hw_floor"] = {"longest_descent_events": L, "simulation": k_long, "kind": kind,
+                               "ns_per_event": ns, "clock_mhz": lat["clock_mhz"],
+                               "longest_x_floor_ms": L * ns * 1e-6, "frac_of_longest_floor": L * ns * 1e-6 / ms,
+                               "what": "the longest line of descent of any simulation of the batch (oracle, mode M) "
+                                       "x the hardware floor of one event of its landscape kind, from latencies "
+                                       "measured on this GPU (tests/hw_latency) / the batch's time"}
     achieved = U * len(step_ms) / max(adv_n, 1) * ops / (avg_launch_ms * 1e-3) / 1e12
     sms, peak, peak_src = int32_peak_tops(torch, torch.device("cuda", local))
     return {
@@ -701,8 +733,8 @@ def batched_leg(args, local, sampler_name="exp"):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit integer)",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "ops_per_event": ops, "busiest_launch": busiest(best or {}, ops, peak)},
-        "latency_bound": {"critical_events_per_batch": crit, "ns_per_critical_event": ms * 1e6 / max(crit, 1),
-                          "what": "the batch lasts as long as its longest dependent chain of events"},
+        "latency_bound": latency,
+        "chain_floor_frac": latency.get("hw_floor", {}).get("frac_of_longest_floor"),
         "gpu_launches": launches, "clocks": clk,
     }
 

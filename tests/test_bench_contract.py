@@ -57,6 +57,9 @@ def test_gpu_arm_line():
         assert 0 < hw["frac_of_longest_floor"] < 1
     b = d["batched"]
     assert b["value"] > 0 and b["unit"] == "unique events/s" and b["speedup_vs_plain"] > 0
+    bf = b["latency_bound"]["hw_floor"]
+    assert b["latency_bound"]["critical_events_per_batch"] >= bf["longest_descent_events"]
+    assert 0 < bf["frac_of_longest_floor"] < 1 and b["chain_floor_frac"] == bf["frac_of_longest_floor"]
     for key in ("served", "served_at_50_per_s"):
         s = d[key]
         assert s["requests"] > 0 and s["latency_s"]["p50"] > 0 and s["achieved_rate_per_s"] > 0

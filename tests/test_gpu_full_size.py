@@ -1,15 +1,20 @@
 """Full-size parity of the batched and served forms.
 
 Config 4 (256 uneven simulations in one batch, sizes up to 10^6, nu down to
-10^-6) and served requests of config 5's shapes are too large for the
-oracle's event-ordered mode, so each simulation is checked on a few sampled
-individuals that the oracle traces alone (mode P: the individual's lineage
-followed to its speciation, section "The Independent Algorithm"), plus two
-properties that hold at any size: the species identities are the dense ranks
-of the speciation keys (the oracle's definition applied to the device's
-keys), and the species count is the number of distinct keys.  Every
-comparison is bit-exact.
+10^-6): every simulation's speciation keys against the digest of the oracle's
+event-ordered run (mode M, stored by tests/golden/make_config4.py), with its
+species count and unique events.  Served requests of config 5's shapes are
+too large for the oracle's event-ordered mode, so each request is checked on
+a few sampled individuals that the oracle traces alone (mode P: the
+individual's lineage followed to its speciation, section "The Independent
+Algorithm"), plus two properties that hold at any size: the species
+identities are the dense ranks of the speciation keys (the oracle's
+definition applied to the device's keys), and the species count is the
+number of distinct keys.  Every comparison is bit-exact.
 """
+import hashlib
+import os
+
 import numpy as np
 import pytest
 
@@ -61,17 +66,46 @@ def _check(c, s, sampler, rng, picks, fraction=1.0, sample_seed=0):
     assert np.array_equal(kl[pick], okl) and np.array_equal(kt[pick], okt)
 
 
+def _config4_digest():
+    """the oracle's event-ordered result of every simulation of config 4
+    (tests/golden/make_config4.py): {(sampler, index): row}"""
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "config4_digest.txt")
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        w, s, k, kind, n, U, K, L, h = line.split()
+        rows[(0 if s == "exp" else 1, int(k))] = dict(kind=kind, n=int(n), U=int(U), K=int(K), L=int(L), sha=h)
+    return rows
+
+
 @pytest.mark.parametrize("sampler", [0, 1])
 def test_config4_full_size_sampled_parity(sampler):
+    """The whole batch of 256 simulations at full size: every simulation's
+    speciation keys hash to the digest of the oracle's event-ordered run, with
+    its species count and unique events; the batch's critical events are never
+    below any simulation's longest line of descent; and two individuals of
+    each simulation equal the oracle's lone traces"""
     specs = W.config4()
+    want = _config4_digest()
     sims = [_sim(c, sampler) for c in specs]
     try:
         for s in sims:
             s.sample()
-        ind.batch_run(sims, **TUNED)
+        st = ind.batch_run(sims, count_unique=1, **TUNED)
         rng = np.random.default_rng(11 + sampler)
-        for c, s in zip(specs, sims):
+        longest = 0
+        for k, (c, s) in enumerate(zip(specs, sims)):
+            w = want[(sampler, k)]
+            kl, kt = s.species_keys()
+            assert s.n_sampled == w["n"]
+            h = hashlib.sha256(kl.astype("<u8").tobytes() + kt.astype("<u8").tobytes()).hexdigest()
+            assert h == w["sha"], "simulation %d differs from the oracle" % k
+            assert st[k]["unique_events"] == w["U"]
+            longest = max(longest, w["L"])
             _check(c, s, sampler, rng, picks=2)
+            assert s.species()[1] == w["K"]
+        assert st[0]["critical_events"] >= longest
     finally:
         for s in sims:
             s.close()
