@@ -273,6 +273,11 @@ def config4_longest(sampler):
     return best
 
 
+# DRAM bytes (read + write) of one step's advance launches, from an ncu
+# capture of this build (profiles/k_advance_coop_config3_dram.md): the
+# roofline's traffic, per round like its achieved figure
+DRAM_BYTES_PER_STEP = {("config3", "exp"): 118.25e9}
+
 _floor_cache = {}
 
 
@@ -515,6 +520,8 @@ def run_single(args, name, rank, world, local, pg):
     unique_per_launch = U * args.steps / adv_n
     achieved = unique_per_launch * ops / (avg_launch_ms * 1e-3) / 1e12
     sms, peak, peak_src = int32_peak_tops(torch, dev)
+    step_bytes = None if log_cap else DRAM_BYTES_PER_STEP.get((name, args.sampler))
+    traffic = step_bytes * args.steps / adv_n if step_bytes else None
     cpu = cpu_baseline(name, args.sampler, args.cpu_seconds) if rank == 0 else None
 
     # batched vs plain on replicas of the workload (different seeds)
@@ -538,7 +545,11 @@ def run_single(args, name, rank, world, local, pg):
         "raw_events_per_s": acc["raw_events"] / args.steps * world / (ms_step_max * 1e-3),
         "roofline": {"bound": "alu", "kernel": "k_advance_coop + k_advance + k_filter (one round's launches)",
                      "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit integer)", "frac": achieved / peak,
-                     "traffic": None, "ops_per_event": ops, "unique_events_per_launch": unique_per_launch,
+                     "traffic": traffic,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one step's advance "
+                                        "launches on B300 (profiles/k_advance_coop_config3_dram.md), per round"
+                                        if traffic else None),
+                     "ops_per_event": ops, "unique_events_per_launch": unique_per_launch,
                      "avg_launch_ms": avg_launch_ms, "launches_timed": acc["advance_launches"],
                      "busiest_launch": busiest(acc["best"] or {}, ops, peak),
                      "peak_source": peak_src,
