@@ -619,11 +619,38 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
 // higher (fewer rounds, nothing else waits)
 constexpr double ALONE_STEP_FACTOR = 16.0;
 
-__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n, uint32_t live) {
+// Relative time of one event per landscape kind in the warp kernel, for
+// pacing rounds that mix kinds: measured on B300 in batches of one kind
+// (config 4's halves), about 0.65 us per critical event non-spatial and
+// 0.84 us on tori; 1.04 us on a habitat map (config 3); the spatially
+// implicit model draws like the non-spatial one.
+__device__ __forceinline__ double kind_event_cost(int kind) {
+    return kind == KIND_TORUS ? 0.84 : (kind == KIND_MAP ? 1.04 : 0.65);
+}
+
+// the least event cost among the kinds of a mask (bit k: kind k live)
+__device__ __forceinline__ double least_event_cost(uint32_t kinds) {
+    double c = 1.0;
+    bool any = false;
+    for (int k = 0; k < 4; ++k)
+        if ((kinds >> k) & 1u) {
+            c = any ? fmin(c, kind_event_cost(k)) : kind_event_cost(k);
+            any = true;
+        }
+    return c;
+}
+
+// pace: the least event cost among the live simulations' kinds over this
+// simulation's own, 1 when every live simulation has one kind.  A shared
+// round lasts as long as its slowest lineage's events, so a simulation of a
+// costlier kind takes proportionally fewer of them: a round that mixes tori
+// with non-spatial demes then lasts about as long as max_step_events
+// non-spatial events instead of as many torus events.
+__device__ __forceinline__ double horizon_step(const SimParams* p, uint32_t n, uint32_t live, double pace = 1.0) {
     const double dn = (double)n;
     const double floor_ev = dn < p->busy_lineages ? p->tail_events : p->min_events;
     const double per = fmax(floor_ev, fmin(p->occupancy_step * p->n_slots / dn, p->events_per_round / dn));
-    const double cap = live > 1u ? p->max_step_events : p->max_step_events * ALONE_STEP_FACTOR;
+    const double cap = live > 1u ? p->max_step_events * pace : p->max_step_events * ALONE_STEP_FACTOR;
     return fmin(per, cap) / p->lambda;
 }
 
@@ -721,8 +748,11 @@ __global__ void k_compact(BatchDev B) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    __shared__ uint32_t live;
-    if (threadIdx.x == 0) live = 0;
+    __shared__ uint32_t live, kinds;
+    if (threadIdx.x == 0) {
+        live = 0;
+        kinds = 0;
+    }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
         SimState* st = B.S + s;
@@ -739,22 +769,27 @@ __global__ void k_compact(BatchDev B) {
             continue;
         }
         atomicAdd(&live, 1u);
+        atomicOr(&kinds, 1u << (B.P[s].kind & 3));
     }
     __syncthreads();
+    const double cmin = least_event_cost(kinds);
     // The water level per simulation, then shared: a round lasts as long as
     // the simulation with the most events per lineage needs, so every other
     // simulation may run as many in it, up to its own occupancy bound
     // (duplicate work), at little cost.  Continuous batching gains most:
     // served requests finish sooner (526 Poisson-arrival torus requests:
     // median latency 8.9 -> 8.0 s, 99th percentile 41.5 -> 38.8 s).  A
-    // simulation alone is unchanged.
+    // simulation alone is unchanged.  Where kinds mix, the level is shared
+    // in time (events x the kind's pace), each simulation taking its own
+    // kind's share of it.
     __shared__ unsigned long long pmax_b;
     if (threadIdx.x == 0) pmax_b = 0ull;
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
         const SimState* st = B.S + s;
         if (!st->done) {
-            const double per = horizon_step(B.P + s, st->n_active, live) * B.P[s].lambda;
+            const double pace = cmin / kind_event_cost(B.P[s].kind);
+            const double per = horizon_step(B.P + s, st->n_active, live, pace) * B.P[s].lambda / pace;
             atomicMax(&pmax_b, (unsigned long long)__double_as_longlong(per));  // per >= 0: bits order as values
         }
     }
@@ -764,9 +799,10 @@ __global__ void k_compact(BatchDev B) {
         SimState* st = B.S + s;
         if (!st->done) {
             const SimParams* p = B.P + s;
-            const double per = horizon_step(p, st->n_active, live) * p->lambda;
+            const double pace = cmin / kind_event_cost(p->kind);
+            const double per = horizon_step(p, st->n_active, live, pace) * p->lambda;
             const double occ = p->occupancy_step * p->n_slots / fmax((double)st->n_active, 1.0);
-            st->horizon = st->horizon + fmax(per, fmin(occ, pmax)) / p->lambda;
+            st->horizon = st->horizon + fmax(per, fmin(occ, pmax * pace)) / p->lambda;
         }
     }
     __syncthreads();
@@ -807,19 +843,26 @@ __global__ void k_compact(BatchDev B) {
 
 // initial horizons and counters of a fresh batch
 __global__ void k_start(BatchDev B, uint32_t n_lin) {
-    __shared__ uint32_t live;
-    if (threadIdx.x == 0) live = 0;
+    __shared__ uint32_t live, kinds;
+    if (threadIdx.x == 0) {
+        live = 0;
+        kinds = 0;
+    }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x)
-        if (B.P[s].n_lineages) atomicAdd(&live, 1u);
+        if (B.P[s].n_lineages) {
+            atomicAdd(&live, 1u);
+            atomicOr(&kinds, 1u << (B.P[s].kind & 3));
+        }
     __syncthreads();
+    const double cmin = least_event_cost(kinds);
     for (uint32_t s = threadIdx.x; s < B.n_sims; s += blockDim.x) {
         const SimParams* p = B.P + s;
         SimState* st = B.S + s;
         const uint32_t na = p->n_lineages;
         st->n_active = na;
         st->done = na == 0 ? 1u : 0u;
-        st->horizon = horizon_step(p, max(na, 1u), live);
+        st->horizon = horizon_step(p, max(na, 1u), live, cmin / kind_event_cost(p->kind));
     }
     if (threadIdx.x == 0) {
         Globals* G = B.G;

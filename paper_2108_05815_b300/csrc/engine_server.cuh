@@ -260,7 +260,8 @@ static ind_status srv_admit(ind_server* sv, std::vector<uint32_t>& empty_admitte
         hs.done = n == 0 ? 1u : 0u;
         {
             // first horizon step, as horizon_step() computes it on the device
-            // for a simulation that shares the rounds
+            // for a simulation that shares the rounds with others of its kind
+            // (later rounds pace mixed kinds on the device)
             const double dn = (double)std::max<uint32_t>(n, 1u);
             const double floor_ev = dn < hp.busy_lineages ? hp.tail_events : hp.min_events;
             const double per = std::max(floor_ev, std::min(hp.occupancy_step * hp.n_slots / dn, hp.events_per_round / dn));
