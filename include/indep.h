@@ -204,6 +204,11 @@ typedef struct {
      * simulation's lambda * step is raised to min(occupancy_step * S / n,
      * the largest lambda * step of the batch's live simulations) when that
      * is more, since a round lasts as long as its busiest simulation needs.
+     * Where the live simulations mix landscape kinds, that level and
+     * max_step_events are counted in time: a simulation of a kind whose
+     * events cost more (relative costs 0.65 non-spatial and spatially
+     * implicit, 0.84 torus, 1.04 habitat map, measured on B300) takes them
+     * scaled by the least live kind's cost over its own.
      * None of this changes any result, only how much work a round does. */
     double events_per_round;       /* water level: target events per simulation per round */
     double min_events_per_lineage; /* lower bound of lambda x horizon step */
