@@ -34,20 +34,46 @@ __global__ void k_init(BatchDev B, const uint32_t* __restrict__ gid_base, uint32
     }
 }
 
+// a lineage with at least this many events (expected) before its horizon
+// runs in the warp kernel in a round of the one-lane form
+constexpr double HEAVY_EVENTS = 256.0;
+
 // The round's work list: the lineages whose next event lies before their
 // simulation's horizon (warp-aggregated appends).  The others have nothing
 // to do in the round: no event, no state to write, no dedup entry.
+// In a round of the one-lane form, a lineage of a simulation in its tail
+// (HEAVY_EVENTS or more before the horizon) goes on the warp kernel's list
+// instead, while it has room: one lane would run those events one after
+// another at about twice the warp's time per event, and the round would
+// last as long as that chain.
 __global__ void k_filter(BatchDev B) {
     const uint32_t n = B.G->n_total;
     const LinPtrs L = B.lin[B.G->round & 1u];
     const uint32_t lane = threadIdx.x & 31u;
+    const bool split = B.heavy_cap && n > B.coop_lineages;
     const uint32_t stride = gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
     for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
         const uint32_t i = base + lane;
-        bool due = false;
+        bool due = false, heavy = false;
         if (i < n) {
-            const double h = B.S[L.sim[i]].horizon;
-            due = (uint64_t)__double_as_longlong(L.tn[i]) <= (uint64_t)__double_as_longlong(h);
+            const uint32_t si = L.sim[i];
+            const double h = B.S[si].horizon;
+            const double tn = L.tn[i];
+            due = (uint64_t)__double_as_longlong(tn) <= (uint64_t)__double_as_longlong(h);
+            heavy = split && due && (h - tn) * B.P[si].lambda >= HEAVY_EVENTS;
+        }
+        const unsigned mh = __ballot_sync(0xFFFFFFFFu, heavy);
+        if (mh) {
+            uint32_t h0 = 0;
+            if (lane == 0) h0 = atomicAdd(&B.G->n_heavy, (uint32_t)__popc(mh));
+            h0 = __shfl_sync(0xFFFFFFFFu, h0, 0);
+            if (heavy) {
+                const uint32_t pos = h0 + __popc(mh & ((1u << lane) - 1u));
+                if (pos < B.heavy_cap) {
+                    B.heavy[pos] = i;
+                    due = false;  // listed for the warp kernel
+                }
+            }
         }
         const unsigned m = __ballot_sync(0xFFFFFFFFu, due);
         uint32_t p0 = 0;
@@ -62,7 +88,11 @@ template <bool COUNT, int WIDE, bool LOG>
 __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
     if (B.G->n_total <= B.coop_lineages) return;  // a round for k_advance_coop
-    const uint32_t n = B.G->n_work;              // lineages with an event before the horizon (k_filter)
+    // lineages with an event before the horizon (k_filter); those listed for
+    // the warp kernel too when more were listed than its list holds (the
+    // warp kernel then leaves them all here)
+    const uint32_t n_list = B.G->n_work;
+    const uint32_t n = n_list + (B.heavy_cap && B.G->n_heavy > B.heavy_cap ? B.heavy_cap : 0u);
     const uint32_t chunk = 32u * B.lpl;
     // Warps take part in the order warp 0 of every block, then warp 1, ...
     // (the grid is one wave of resident blocks): a round with few lineages
@@ -111,7 +141,8 @@ __global__ void __launch_bounds__(512) k_advance(BatchDev B) {
                 const uint32_t avail = chunk_end - chunk_next;
                 const uint32_t rank = __popc(need & lt_mask);
                 if (!has && rank < avail) {
-                    idx = B.work[chunk_next + rank];
+                    const uint32_t j = chunk_next + rank;
+                    idx = j < n_list ? B.work[j] : B.heavy[j - n_list];
                     gid = L.gid[idx];
                     loc = L.loc[idx];
                     tn = L.tn[idx];
@@ -427,8 +458,14 @@ __global__ void __launch_bounds__(512) k_advance_sm(BatchDev B) {
 template <bool COUNT, int MODE, int KIND, bool LOG = false>
 __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     extern __shared__ __align__(16) unsigned char adv_smem[];
-    if (B.G->n_total > B.coop_lineages) return;  // a round for the one-lane form
-    const uint32_t n = B.G->n_work;             // lineages with an event before the horizon (k_filter)
+    // a round of the warp form: every lineage with an event before the
+    // horizon (k_filter); a round of the one-lane form: the heavy lineages
+    // k_filter listed, when they all fit the list
+    const bool lane_round = B.G->n_total > B.coop_lineages;
+    if (lane_round && (!B.heavy_cap || B.G->n_heavy > B.heavy_cap)) return;
+    const uint32_t n = lane_round ? B.G->n_heavy : B.G->n_work;
+    const uint32_t* const list = lane_round ? B.heavy : B.work;
+    uint32_t* const claims = lane_round ? &B.G->heavy_ctr : &B.G->work_ctr;
     // Warps take part in the order warp 0 of every block, then warp 1 of
     // every block, and so on (the grid is one wave of resident blocks), so
     // that a round with few lineages spreads them over the SMs instead of
@@ -485,10 +522,10 @@ __global__ void __launch_bounds__(512, 1) k_advance_coop(BatchDev B) {
     if (B.stage_bytes) rs = row_stage_init(sbuf, lane);
     for (;;) {
         uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(&B.G->work_ctr, 1u);
+        if (lane == 0) k = atomicAdd(claims, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         if (k >= n) break;
-        const uint32_t idx = B.work[k];
+        const uint32_t idx = list[k];
         const uint32_t gid = L.gid[idx];
         uint64_t loc = L.loc[idx];
         double tn = L.tn[idx];
@@ -827,6 +864,8 @@ __global__ void k_compact(BatchDev B) {
         G->n_total_next = 0;
         G->work_ctr = 0;
         G->n_work = 0;
+        G->n_heavy = 0;
+        G->heavy_ctr = 0;
         G->blocks_done = 0;
         G->used[tp] = 0;
         G->ev_used[tp] = 0;

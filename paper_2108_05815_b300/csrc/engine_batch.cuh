@@ -252,6 +252,17 @@ static cudaError_t set_coop_smem() {
     return cudaSuccess;
 }
 
+// the warp kernel's list of heavy lineages in rounds of the one-lane form:
+// at most one lineage per warp of its grid (more would run one after another
+// on a warp, after the one-lane kernel), none for the convergent one-lane
+// form, which reads only the main list
+constexpr uint32_t HEAVY_LIST_MAX = 16384;
+
+static uint32_t heavy_list_cap(const Batch& b) {
+    if (!b.dev.heavy || b.tun.advance_variant != 1) return 0;
+    return std::min<uint32_t>(b.coop_blocks * (b.adv_threads / 32u), HEAVY_LIST_MAX);
+}
+
 // blocks of the warp kernel an SM holds at once (the fewest over its
 // instantiations), for a block of `threads` with `smem` dynamic bytes
 static uint32_t coop_blocks_per_sm(uint32_t threads, size_t smem) {
@@ -345,6 +356,7 @@ static ind_status batch_build(Batch& b) {
     }
     d.parent = P.get<uint32_t>(n);
     d.work = P.get<uint32_t>(n);
+    d.heavy = P.get<uint32_t>(HEAVY_LIST_MAX);
     d.key_loc = P.get<uint64_t>(n);
     d.key_time = P.get<uint64_t>(n);
     uint32_t cap = 2;
@@ -556,6 +568,7 @@ static ind_status batch_build(Batch& b) {
     b.coop_blocks = std::min(b.adv_blocks, sms * coop_blocks_per_sm(b.adv_threads, b.coop_smem));
     b.lane_blocks = std::min(b.adv_blocks, sms * lane_blocks_per_sm(b.adv_threads, LN_SMEM_BYTES));
     b.cmp_blocks = sms * 4;
+    d.heavy_cap = heavy_list_cap(b);
     // starting states
     k_start<<<1, 256, 0, s>>>(d, b.n_lin);
     CKL();

@@ -373,6 +373,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     }
     d.parent = P.get<uint32_t>(n);
     d.work = P.get<uint32_t>(n);
+    d.heavy = P.get<uint32_t>(HEAVY_LIST_MAX);
     d.key_loc = P.get<uint64_t>(n);
     d.key_time = P.get<uint64_t>(n);
     uint32_t cap = 2;
@@ -443,6 +444,7 @@ ind_status srv_create(uint64_t budget, uint32_t max_sims, const ind_tuning* tuni
     b.coop_blocks = std::min(b.adv_blocks, sms * coop_blocks_per_sm(b.adv_threads, b.coop_smem));
     b.lane_blocks = std::min(b.adv_blocks, sms * lane_blocks_per_sm(b.adv_threads, LN_SMEM_BYTES));
     b.cmp_blocks = sms * 4;
+    d.heavy_cap = heavy_list_cap(b);
     if (b.tun.profile) {
         b.ev_start.resize(b.tun.rounds_per_check);
         b.ev_end.resize(b.tun.rounds_per_check);

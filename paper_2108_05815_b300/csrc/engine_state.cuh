@@ -188,6 +188,10 @@ struct Globals {
     // that another active lane of the same warp inserted in the same
     // instruction (what a warp pre-collapse of equal keys would save)
     unsigned long long ins_total, ins_repeat, ins_warp_repeat;
+    // rounds of the one-lane form: lineages listed for the warp kernel
+    // (k_filter's claims, possibly beyond the list's capacity) and its claim counter
+    uint32_t n_heavy;
+    uint32_t heavy_ctr;
 };
 
 struct __align__(16) EvSlot {
@@ -250,4 +254,9 @@ struct BatchDev {
     uint32_t stage_off;      // warp kernel: shared-memory offset of the per-warp alias-row buffers
     uint32_t stage_bytes;    // bytes of one such buffer (0: map rows are read from global memory)
     EventLog log;            // cap 0: no logging
+    // rounds of the one-lane form: the lineages with many events before the
+    // horizon, run by the warp kernel after the one-lane kernel when they
+    // fit its warps (heavy_cap entries; 0: every lineage on the one-lane list)
+    uint32_t* heavy;
+    uint32_t heavy_cap;
 };
