@@ -191,7 +191,9 @@ typedef struct {
     uint32_t count_unique;      /* 1: count distinct events exactly (slower, for measurement) */
     uint32_t profile;           /* 1: time every advance-kernel launch with CUDA events */
     uint32_t events_per_visit;  /* events a lane runs on its lineage between warp votes, 1..1024 */
-    uint32_t coop_lineages;     /* at most this many active lineages: one warp per lineage (0: never) */
+    uint32_t coop_lineages;     /* at most this many active lineages: one warp per lineage (0: never); with
+                                   more (advance_variant 1), the lineages with 256 or more events before
+                                   the horizon still run one per warp when they fit the warp grid */
     uint32_t advance_variant;   /* more active lineages: 1 (default) = one lineage per lane, events in a
                                    loop; 0 = convergent state machine (one Philox block per lane per step,
                                    kept as an option: slower on B300 on every workload measured) */
