@@ -658,9 +658,10 @@ constexpr double ALONE_STEP_FACTOR = 16.0;
 
 // Relative time of one event per landscape kind in the warp kernel, for
 // pacing rounds that mix kinds: measured on B300 in batches of one kind
-// (config 4's halves), about 0.65 us per critical event non-spatial and
-// 0.84 us on tori; 1.04 us on a habitat map (config 3); the spatially
-// implicit model draws like the non-spatial one.
+// (128 non-spatial demes, or 128 tori, of 10^3 to 10^6 individuals), about
+// 0.65 us per critical event non-spatial and 0.84 us on tori; 1.04 us on a
+// 1024 x 1024 habitat map; the spatially implicit model draws like the
+// non-spatial one.
 __device__ __forceinline__ double kind_event_cost(int kind) {
     return kind == KIND_TORUS ? 0.84 : (kind == KIND_MAP ? 1.04 : 0.65);
 }
