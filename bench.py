@@ -276,7 +276,7 @@ def config4_longest(sampler):
 # DRAM bytes (read + write) of one step's advance launches, from an ncu
 # capture of this build (profiles/k_advance_coop_config3_dram.md): the
 # roofline's traffic, per round like its achieved figure
-DRAM_BYTES_PER_STEP = {("config3", "exp"): 118.25e9}
+DRAM_BYTES_PER_STEP = {("config3", "exp"): 117.74e9}
 
 _floor_cache = {}
 
